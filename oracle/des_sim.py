@@ -1,0 +1,38 @@
+"""Python entry to the discrete-event simulation (``des.c``) -- TEST INFRASTRUCTURE."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+
+def explore(sysd: dict, n_buckets: int = 1, eps: int = 0, kappa: int = 0, all_variants: bool = True,
+            t_limit_extra: int = 200) -> list:
+    """Largest observed response per chain of one tiny system dict over every
+    release-offset vector (and execution-time variant)."""
+    ch, ex = sysd["chains"], sysd["execs"]
+    n = len(ch)
+    T = np.array([c["T"] for c in ch], np.int64)
+    prio = np.array([c["prio"] for c in ch], np.int32)
+    exe = np.array([c["exec"] for c in ch], np.int32)
+    spin = np.array([c["spin"] for c in ch], np.uint8)
+    cb_n = np.array([len(c["cbs"]) for c in ch], np.int32)
+    E = np.array([e for c in ch for (e, _) in c["cbs"]], np.int64)
+    nseg = np.array([len(ss) for c in ch for (_, ss) in c["cbs"]], np.int32)
+    A = np.array([a for c in ch for (_, ss) in c["cbs"] for a in ss] or [0], np.int64)
+    core = np.array([x["core"] for x in ex], np.int32)
+    xprio = np.array([x["prio"] for x in ex], np.int32)
+    out = np.zeros(n, np.int64)
+    f = _lib("des").des_explore
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int32] + [ctypes.c_void_p] * 8 + [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                  ctypes.c_void_p]
+    p = lambda a: a.ctypes.data
+    rc = f(n, p(T), p(prio), p(exe), p(spin), p(cb_n), p(E), p(nseg), p(A), len(ex), p(core), p(xprio),
+           n_buckets, eps, kappa, t_limit_extra, 1 if all_variants else 0, p(out))
+    if rc != 0:
+        raise RuntimeError(f"des_explore failed: {rc}")
+    return out.tolist()
