@@ -1,0 +1,174 @@
+/*
+ * paam_rta.h -- C ABI of the GB300 batched PAAM response-time analysis.
+ *
+ * PAAM (Sec. IV) serves the accelerator segments of ROS 2 callback chains
+ * through a priority-driven server executor and admits a new client only if
+ * every chain's worst-case response time (WCRT) stays within its deadline
+ * (admission control, Sec. IV-A and Sec. IV-F).  This library evaluates that
+ * WCRT bound -- Theorem 1 (Eq. 6) with Eqs. 1-4 and Lemma 4 (Eq. 5) -- for
+ * very many independent systems at once on one GB300 GPU, exactly, in int64
+ * nanoseconds.  Every step of the analysis runs in the library's own CUDA
+ * kernels (sm_103a); there is no CPU fallback.
+ *
+ * Conventions
+ *   - Every call returns PAAM_OK (0) or a negative PAAM_E_* code; nothing
+ *     throws across the ABI.  paam_strerror() names a code.
+ *   - The caller owns every buffer it passes; the library owns contexts,
+ *     batches and models and frees them in the matching *_free / destroy.
+ *   - "device" pointers are CUDA device (or managed) memory of the context's
+ *     GPU; "host" pointers are ordinary or pinned host memory.
+ *   - A stream argument is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls that produce device outputs only enqueue work
+ *     on it, unless stated otherwise.
+ *   - All times are int64 nanoseconds.
+ */
+#ifndef PAAM_RTA_H
+#define PAAM_RTA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define PAAM_OK 0
+#define PAAM_E_INVAL (-1)       /* malformed input: offsets, D > T, T <= 0, negative time,
+                                   duplicate priority, executor index out of range, ... */
+#define PAAM_E_RANGE (-2)       /* a bound could overflow int64 (see paam_rta_load_systems) */
+#define PAAM_E_NOMEM (-3)       /* device or host allocation failed */
+#define PAAM_E_CUDA (-4)        /* a CUDA runtime call failed */
+#define PAAM_E_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define PAAM_E_UNSUPPORTED (-6) /* input outside what this build implements */
+#define PAAM_E_STATE (-7)       /* object used with the wrong context / after free */
+
+/* ---- per-chain status --------------------------------------------------- */
+#define PAAM_ST_SCHED 0   /* R <= D: the chain meets its deadline                    */
+#define PAAM_ST_OVERRUN 1 /* the recurrence exceeded D (Theorem 1 gives no bound <= D) */
+#define PAAM_ST_DEP 2     /* a chain whose H* this chain needs is not schedulable     */
+#define PAAM_ST_ITERCAP 3 /* iteration safety cap hit; unreachable (each step raises a
+                             ceil(t/T)), kept as a guard                              */
+
+#define PAAM_MAX_CHAINS 64        /* chains per system                           */
+#define PAAM_MAX_TIME (1LL << 40) /* largest T, D, E, A accepted (about 18 min)  */
+#define PAAM_MAX_OVERHEAD (1LL << 32) /* largest eps, kappa accepted             */
+
+typedef struct paam_ctx paam_ctx;
+typedef struct paam_batch paam_batch;
+typedef struct paam_model paam_model;
+
+/*
+ * A batch of systems in structure-of-arrays, CSR form (system model of
+ * Sec. II-C).  System s owns chains [sys_chain_off[s], sys_chain_off[s+1])
+ * and executors [sys_exec_off[s], sys_exec_off[s+1]); chain c owns callbacks
+ * [chain_cb_off[c], chain_cb_off[c+1]) executed in order; callback b owns
+ * accelerator segments [cb_seg_off[b], cb_seg_off[b+1]).  Callbacks are not
+ * shared between chains.
+ *
+ *   T[c], D[c]     period and constrained deadline, 0 < D <= T
+ *   prio[c]        chain priority, larger = higher, distinct within a system
+ *   exec[c]        executor of the chain, local index in [0, executors of s)
+ *   spin[c]        1 if the chain busy-waits on accelerator requests, else 0
+ *   E[b]           CPU WCET of callback b (all its CPU segments), >= 0
+ *   A[q]           WCET of accelerator segment q, >= 0
+ *   acc[q]         accelerator of segment q; NULL or all 0 (one accelerator
+ *                  per system in this build, else PAAM_E_UNSUPPORTED)
+ *   exec_core[x]   CPU core of executor x, >= 0
+ *   exec_prio[x]   executor (process) priority, larger = higher, distinct among
+ *                  executors of one core; NULL = derived as the highest chain
+ *                  priority on the executor (criticality-as-priority, Sec. II-C)
+ *
+ * Offsets are non-decreasing, start at 0 and end at the matching count.  All
+ * pointers are host memory (is_device = 0) or device memory of the
+ * context's GPU (is_device = 1).
+ */
+typedef struct {
+    int64_t n_sys, n_chain, n_cb, n_seg, n_exec;
+    const int64_t *sys_chain_off; /* [n_sys + 1]   */
+    const int64_t *chain_cb_off;  /* [n_chain + 1] */
+    const int64_t *cb_seg_off;    /* [n_cb + 1]    */
+    const int64_t *T;             /* [n_chain]     */
+    const int64_t *D;             /* [n_chain]     */
+    const int32_t *prio;          /* [n_chain]     */
+    const int32_t *exec;          /* [n_chain]     */
+    const uint8_t *spin;          /* [n_chain]     */
+    const int64_t *E;             /* [n_cb]        */
+    const int64_t *A;             /* [n_seg]       */
+    const int32_t *acc;           /* [n_seg] or NULL */
+    const int64_t *sys_exec_off;  /* [n_sys + 1]   */
+    const int32_t *exec_core;     /* [n_exec]      */
+    const int32_t *exec_prio;     /* [n_exec] or NULL */
+    int32_t is_device;
+    int32_t reserved_;
+} paam_systems_view;
+
+/*
+ * Analysis parameters (Sec. IV-F).
+ *   n_buckets      n >= 1 worker buckets of the server (rule R2); accelerator
+ *                  users are ranked by descending chain priority and rank r of
+ *                  |U| users goes to bucket floor(r * n / |U|)
+ *   blocking_mode  0: B_c as in Lemma 4 (largest CPU WCET of one callback of
+ *                  a lower-priority chain on the executor); other values
+ *                  PAAM_E_UNSUPPORTED in this build
+ *   eps_ns         per-request server overhead epsilon (Eq. 1), 0..2^32
+ *   kappa_ns       device preemption cost kappa, A* = A + 2 kappa, 0..2^32
+ */
+typedef struct {
+    int32_t n_buckets;
+    int32_t blocking_mode;
+    int64_t eps_ns;
+    int64_t kappa_ns;
+} paam_analysis_opts;
+
+/* Create a context bound to CUDA device `device_ordinal`. */
+int paam_create(paam_ctx **out, int device_ordinal);
+
+/* Release a context (its batches and models must be freed first). */
+void paam_destroy(paam_ctx *ctx);
+
+/* Short English name of a return code. */
+const char *paam_strerror(int code);
+
+/*
+ * Copy a batch of systems into library-owned device memory and validate it on
+ * the GPU.  Blocks until validation finishes (it synchronises `stream`).
+ *
+ * Errors: PAAM_E_INVAL for malformed input (see paam_systems_view), a system
+ * with more than PAAM_MAX_CHAINS chains, or a time above PAAM_MAX_TIME;
+ * PAAM_E_RANGE when N * (ceil(Dmax / Tmin) + 1) * Cmax + Base could exceed
+ * 2^62 for some system (the largest value any fixed-point iterate of Eqs. 3-6
+ * can take with eps, kappa <= PAAM_MAX_OVERHEAD), so that no int64 sum
+ * overflows; PAAM_E_UNSUPPORTED for acc != 0; PAAM_E_NOMEM / PAAM_E_CUDA.
+ * On error *out is NULL and nothing is leaked.
+ */
+int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *view, void *stream,
+                          paam_batch **out);
+
+/* Number of systems / chains of a loaded batch (0 for NULL). */
+int64_t paam_batch_n_sys(const paam_batch *b);
+int64_t paam_batch_n_chain(const paam_batch *b);
+
+/* Free a batch (after the work that uses it has completed). */
+void paam_batch_free(paam_batch *b);
+
+/*
+ * WCRT analysis of every chain of every system (Theorem 1, Eq. 6, with
+ * Eqs. 1-4 and Lemma 4).  Enqueued on `stream`; outputs are device buffers:
+ *   R[n_chain]       int64: the least fixed point of Eq. 6 when the chain is
+ *                    schedulable, else -1
+ *   status[n_chain]  PAAM_ST_* per chain
+ *   verdict[n_sys]   1 if every chain of the system is PAAM_ST_SCHED (the
+ *                    admission test of Sec. IV-A), else 0
+ * verdict may be NULL.  Results are bit-identical to the definition for any
+ * launch configuration.  Errors: PAAM_E_INVAL (NULL outputs, n_buckets < 1),
+ * PAAM_E_RANGE (eps or kappa above PAAM_MAX_OVERHEAD), PAAM_E_UNSUPPORTED
+ * (blocking_mode != 0), PAAM_E_CUDA (launch failure).
+ */
+int paam_rta_analyze_batch(paam_ctx *ctx, const paam_batch *batch, const paam_analysis_opts *opts,
+                           int64_t *R, uint8_t *status, uint8_t *verdict, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAAM_RTA_H */

@@ -1,0 +1,16 @@
+"""GB300-native batched WCRT analysis of PAAM (arxiv 2404.06452, Sec. IV-F).
+
+The compute path is ``libpaam_rta.so`` (hand-written sm_103a CUDA behind the
+C ABI of ``include/paam_rta.h``); this package is its thin Python binding
+plus convenience wrappers that allocate outputs with PyTorch.
+"""
+from ._binding import (PAAM_MAX_CHAINS, PAAM_ST_DEP, PAAM_ST_ITERCAP, PAAM_ST_OVERRUN, PAAM_ST_SCHED,
+                       AnalysisOpts, Batch, Context, PaamError, SystemsView, analysis_opts, lib,
+                       paam_rta_analyze_batch, paam_rta_load_systems, strerror)
+from .api import analyze, to_device
+
+__all__ = [
+    "Context", "Batch", "PaamError", "SystemsView", "AnalysisOpts", "analysis_opts", "lib", "strerror",
+    "paam_rta_load_systems", "paam_rta_analyze_batch", "analyze", "to_device",
+    "PAAM_ST_SCHED", "PAAM_ST_OVERRUN", "PAAM_ST_DEP", "PAAM_ST_ITERCAP", "PAAM_MAX_CHAINS",
+]

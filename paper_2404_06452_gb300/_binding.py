@@ -1,0 +1,207 @@
+"""Thin ctypes binding of ``include/paam_rta.h`` (argument marshalling only).
+
+Every computation runs in ``libpaam_rta.so``.  PyTorch supplies device
+memory and streams.  If the library is missing the import fails loudly; there
+is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpaam_rta.so")
+
+PAAM_OK = 0
+PAAM_ST_SCHED, PAAM_ST_OVERRUN, PAAM_ST_DEP, PAAM_ST_ITERCAP = 0, 1, 2, 3
+PAAM_MAX_CHAINS = 64
+
+_c_void_p = ctypes.c_void_p
+
+
+class SystemsView(ctypes.Structure):
+    _fields_ = [
+        ("n_sys", ctypes.c_int64), ("n_chain", ctypes.c_int64), ("n_cb", ctypes.c_int64),
+        ("n_seg", ctypes.c_int64), ("n_exec", ctypes.c_int64),
+        ("sys_chain_off", _c_void_p), ("chain_cb_off", _c_void_p), ("cb_seg_off", _c_void_p),
+        ("T", _c_void_p), ("D", _c_void_p), ("prio", _c_void_p), ("exec", _c_void_p), ("spin", _c_void_p),
+        ("E", _c_void_p), ("A", _c_void_p), ("acc", _c_void_p), ("sys_exec_off", _c_void_p),
+        ("exec_core", _c_void_p), ("exec_prio", _c_void_p), ("is_device", ctypes.c_int32),
+        ("reserved_", ctypes.c_int32),
+    ]
+
+
+class AnalysisOpts(ctypes.Structure):
+    _fields_ = [("n_buckets", ctypes.c_int32), ("blocking_mode", ctypes.c_int32),
+                ("eps_ns", ctypes.c_int64), ("kappa_ns", ctypes.c_int64)]
+
+
+class PaamError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is not built: run __graft_entry__.build() "
+                              "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        sig = {
+            "paam_create": (ctypes.c_int, [P(_c_void_p), ctypes.c_int]),
+            "paam_destroy": (None, [_c_void_p]),
+            "paam_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "paam_rta_load_systems": (ctypes.c_int, [_c_void_p, P(SystemsView), _c_void_p, P(_c_void_p)]),
+            "paam_batch_n_sys": (ctypes.c_int64, [_c_void_p]),
+            "paam_batch_n_chain": (ctypes.c_int64, [_c_void_p]),
+            "paam_batch_free": (None, [_c_void_p]),
+            "paam_rta_analyze_batch": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
+                                                      _c_void_p, _c_void_p, _c_void_p]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list:
+    """Names this binding expects the library to export."""
+    return ["paam_create", "paam_destroy", "paam_strerror", "paam_rta_load_systems", "paam_batch_n_sys",
+            "paam_batch_n_chain", "paam_batch_free", "paam_rta_analyze_batch"]
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().paam_strerror(code).decode()
+    except ImportError:
+        return str(code)
+
+
+def _check(rc: int, what: str):
+    if rc != PAAM_OK:
+        raise PaamError(rc, what)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _ptr(x) -> int | None:
+    """Address of a numpy array or a torch tensor (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"unsupported buffer {type(x)}")
+
+
+class Context:
+    """A library context bound to one CUDA device (``paam_create``)."""
+
+    def __init__(self, device: int = 0):
+        h = _c_void_p()
+        _check(lib().paam_create(ctypes.byref(h), int(device)), "paam_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().paam_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A validated device copy of systems (``paam_rta_load_systems``)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    @property
+    def n_sys(self) -> int:
+        return int(lib().paam_batch_n_sys(self.handle))
+
+    @property
+    def n_chain(self) -> int:
+        return int(lib().paam_batch_n_chain(self.handle))
+
+    def free(self):
+        if self.handle:
+            lib().paam_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+_VIEW_FIELDS = ["sys_chain_off", "chain_cb_off", "cb_seg_off", "T", "D", "prio", "exec", "spin", "E", "A",
+                "acc", "sys_exec_off", "exec_core", "exec_prio"]
+
+
+def make_view(sy, is_device: bool) -> tuple:
+    """A ``SystemsView`` over the arrays of ``sy`` (attributes named as in the
+    header); returns (view, keepalive)."""
+    v = SystemsView()
+    keep = []
+    for f in _VIEW_FIELDS:
+        a = getattr(sy, f, None)
+        keep.append(a)
+        setattr(v, f, _ptr(a))
+    v.n_sys = len(sy.sys_chain_off) - 1
+    v.n_chain = len(sy.T)
+    v.n_cb = len(sy.E)
+    v.n_seg = len(sy.A)
+    v.n_exec = len(sy.exec_core)
+    v.is_device = 1 if is_device else 0
+    return v, keep
+
+
+def paam_rta_load_systems(ctx: Context, sy, stream=None, is_device: bool | None = None) -> Batch:
+    if is_device is None:
+        is_device = hasattr(sy.T, "is_cuda") and bool(sy.T.is_cuda)
+    v, keep = make_view(sy, is_device)
+    h = _c_void_p()
+    _check(lib().paam_rta_load_systems(ctx.handle, ctypes.byref(v), _stream_ptr(stream), ctypes.byref(h)),
+           "paam_rta_load_systems")
+    del keep
+    return Batch(ctx, h)
+
+
+def analysis_opts(n_buckets: int = 1, eps: int = 0, kappa: int = 0, blocking_mode: int = 0) -> AnalysisOpts:
+    return AnalysisOpts(int(n_buckets), int(blocking_mode), int(eps), int(kappa))
+
+
+def paam_rta_analyze_batch(ctx: Context, batch: Batch, opts: AnalysisOpts, R, status, verdict=None,
+                           stream=None):
+    _check(lib().paam_rta_analyze_batch(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(R), _ptr(status),
+                                        _ptr(verdict), _stream_ptr(stream)), "paam_rta_analyze_batch")

@@ -1,0 +1,40 @@
+"""Convenience wrappers over the C ABI that allocate outputs with PyTorch."""
+from __future__ import annotations
+
+from types import SimpleNamespace
+
+import numpy as np
+
+from . import _binding as B
+
+_FIELDS = ["sys_chain_off", "chain_cb_off", "cb_seg_off", "T", "D", "prio", "exec", "spin", "E", "A", "acc",
+           "sys_exec_off", "exec_core", "exec_prio"]
+
+
+def to_device(sy, device="cuda", pin: bool = False):
+    """Copy the arrays of a host batch to torch tensors on ``device`` (or to
+    pinned host tensors when ``pin``).  Returns an attribute namespace."""
+    import torch
+
+    out = SimpleNamespace()
+    for f in _FIELDS:
+        a = getattr(sy, f, None)
+        if a is None:
+            setattr(out, f, None)
+            continue
+        t = torch.from_numpy(np.ascontiguousarray(a))
+        t = t.pin_memory() if pin else t.to(device)
+        setattr(out, f, t)
+    return out
+
+
+def analyze(ctx: B.Context, batch: B.Batch, n_buckets: int = 1, eps: int = 0, kappa: int = 0, stream=None):
+    """Run ``paam_rta_analyze_batch`` into fresh torch device tensors."""
+    import torch
+
+    dev = torch.device("cuda", ctx.device)
+    R = torch.empty(batch.n_chain, dtype=torch.int64, device=dev)
+    st = torch.empty(batch.n_chain, dtype=torch.uint8, device=dev)
+    v = torch.empty(batch.n_sys, dtype=torch.uint8, device=dev)
+    B.paam_rta_analyze_batch(ctx, batch, B.analysis_opts(n_buckets, eps, kappa), R, st, v, stream=stream)
+    return R, st, v

@@ -1,0 +1,342 @@
+// api.cu -- context, batch loading with on-GPU validation, analysis entry.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+void paam_note_cuda_error(cudaError_t e, const char *expr, const char *file, int line)
+{
+    if (getenv("PAAM_VERBOSE"))
+        fprintf(stderr, "paam: CUDA error %s (%s) at %s:%d: %s\n", cudaGetErrorName(e),
+                cudaGetErrorString(e), file, line, expr);
+}
+
+extern "C" const char *paam_strerror(int code)
+{
+    switch (code) {
+    case PAAM_OK: return "ok";
+    case PAAM_E_INVAL: return "invalid input";
+    case PAAM_E_RANGE: return "values out of the exact int64 range";
+    case PAAM_E_NOMEM: return "out of memory";
+    case PAAM_E_CUDA: return "CUDA runtime error";
+    case PAAM_E_TIMEOUT: return "bounded device wait timed out";
+    case PAAM_E_UNSUPPORTED: return "unsupported input or option";
+    case PAAM_E_STATE: return "object used in the wrong state";
+    default: return "unknown error";
+    }
+}
+
+extern "C" int paam_create(paam_ctx **out, int device_ordinal)
+{
+    if (!out) return PAAM_E_INVAL;
+    *out = nullptr;
+    int n_dev = 0;
+    PAAM_CUDA_TRY(cudaGetDeviceCount(&n_dev));
+    if (device_ordinal < 0 || device_ordinal >= n_dev) return PAAM_E_INVAL;
+    PAAM_CUDA_TRY(cudaSetDevice(device_ordinal));
+    paam_ctx *c = (paam_ctx *)calloc(1, sizeof(paam_ctx));
+    if (!c) return PAAM_E_NOMEM;
+    c->device = device_ordinal;
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device_ordinal) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                               device_ordinal) != cudaSuccess) {
+        free(c);
+        return PAAM_E_CUDA;
+    }
+    if (cudaMalloc(&c->d_err, 4 * sizeof(int32_t)) != cudaSuccess) {
+        free(c);
+        return PAAM_E_NOMEM;
+    }
+    // keep freed batch memory in the device pool so repeated load/free cycles are cheap
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device_ordinal) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    *out = c;
+    return PAAM_OK;
+}
+
+extern "C" void paam_destroy(paam_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaFree(c->d_err);
+    free(c);
+}
+
+// ---------------------------------------------------------------------------
+// validation: one thread per system; the first failing code wins
+// ---------------------------------------------------------------------------
+
+struct ValidateArgs {
+    BatchDev b;
+    int64_t n_chain, n_cb, n_seg, n_exec;
+    const int32_t *acc;
+    int32_t *err; // [0] code, [1] first bad system (min), [2] max chains, [3] max executors
+};
+
+__device__ __forceinline__ void fail(int32_t *err, int32_t code, int64_t sys)
+{
+    atomicCAS(&err[0], 0, code);
+    atomicMin(&err[1], (int32_t)(sys < 0x7fffffff ? sys : 0x7fffffff));
+}
+
+__global__ void validate_kernel(ValidateArgs a)
+{
+    const BatchDev &b = a.b;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < b.n_sys; s += stride) {
+        if (s == 0) { // global sentinels
+            if (b.sys_chain_off[0] != 0 || b.sys_exec_off[0] != 0 || b.chain_cb_off[0] != 0 ||
+                b.cb_seg_off[0] != 0 || b.sys_chain_off[b.n_sys] != a.n_chain ||
+                b.sys_exec_off[b.n_sys] != a.n_exec || b.chain_cb_off[a.n_chain] != a.n_cb ||
+                b.cb_seg_off[a.n_cb] != a.n_seg) {
+                fail(a.err, PAAM_E_INVAL, s);
+                continue;
+            }
+        }
+        const int64_t c0 = b.sys_chain_off[s], c1 = b.sys_chain_off[s + 1];
+        const int64_t x0 = b.sys_exec_off[s], x1 = b.sys_exec_off[s + 1];
+        if (c0 < 0 || c1 < c0 || c1 > a.n_chain || x0 < 0 || x1 < x0 || x1 > a.n_exec) {
+            fail(a.err, PAAM_E_INVAL, s);
+            continue;
+        }
+        const int64_t n = c1 - c0, nx = x1 - x0;
+        if (n > PAAM_MAX_CHAINS || (n > 0 && nx == 0)) {
+            fail(a.err, PAAM_E_INVAL, s);
+            continue;
+        }
+        atomicMax(&a.err[2], (int32_t)n);
+        atomicMax(&a.err[3], (int32_t)(nx < 0x7fffffff ? nx : 0x7fffffff));
+        // executors
+        bool bad = false;
+        for (int64_t x = x0; x < x1 && !bad; ++x) {
+            if (b.exec_core[x] < 0) bad = true;
+            if (b.exec_prio)
+                for (int64_t y = x0; y < x && !bad; ++y)
+                    if (b.exec_core[y] == b.exec_core[x] && b.exec_prio[y] == b.exec_prio[x]) bad = true;
+        }
+        if (bad) {
+            fail(a.err, PAAM_E_INVAL, s);
+            continue;
+        }
+        // chains, callbacks, segments; magnitudes for the range check
+        double Dmax = 0.0, Tmin = 1e300, Cmax = 0.0, Base = 0.0, Emax_sys = 0.0, Mmax_sys = 0.0;
+        const double OV = (double)PAAM_MAX_OVERHEAD;
+        bool unsupported = false;
+        for (int64_t c = c0; c < c1 && !bad; ++c) {
+            const int64_t T = b.T[c], D = b.D[c];
+            if (T <= 0 || T > PAAM_MAX_TIME || D <= 0 || D > T || b.spin[c] > 1 || b.exec[c] < 0 ||
+                b.exec[c] >= nx) {
+                bad = true;
+                break;
+            }
+            for (int64_t k = c0; k < c; ++k)
+                if (b.prio[k] == b.prio[c]) bad = true;
+            const int64_t b0 = b.chain_cb_off[c], b1 = b.chain_cb_off[c + 1];
+            if (b0 < 0 || b1 < b0 || b1 > a.n_cb || (c > c0 && b0 != b.chain_cb_off[c - 1 + 1])) {
+                bad = true;
+                break;
+            }
+            double Ec = 0.0, Sc = 0.0, dc = 0.0;
+            for (int64_t cb = b0; cb < b1 && !bad; ++cb) {
+                const int64_t e = b.E[cb];
+                const int64_t q0 = b.cb_seg_off[cb], q1 = b.cb_seg_off[cb + 1];
+                if (e < 0 || e > PAAM_MAX_TIME || q0 < 0 || q1 < q0 || q1 > a.n_seg) {
+                    bad = true;
+                    break;
+                }
+                Ec += (double)e;
+                if ((double)e > Emax_sys) Emax_sys = (double)e;
+                for (int64_t q = q0; q < q1; ++q) {
+                    const int64_t av = b.A[q];
+                    if (av < 0 || av > PAAM_MAX_TIME) {
+                        bad = true;
+                        break;
+                    }
+                    if (a.acc && a.acc[q] != 0) unsupported = true;
+                    const double as = (double)av + 2.0 * OV;
+                    Sc += as;
+                    dc += 1.0;
+                    if (as > Mmax_sys) Mmax_sys = as;
+                }
+            }
+            if ((double)D > Dmax) Dmax = (double)D;
+            if ((double)T < Tmin) Tmin = (double)T;
+            const double spin_or_d = (double)D > dc * OV ? (double)D : dc * OV;
+            const double C = Ec + spin_or_d + Sc;
+            if (C > Cmax) Cmax = C;
+            const double base = Ec + Sc + dc * OV;
+            if (base > Base) Base = base;
+            (void)Sc;
+            if (dc > 0.0) { // delta * blk contribution to the base
+                const double extra = dc * 1.0;
+                (void)extra;
+            }
+        }
+        if (bad) {
+            fail(a.err, PAAM_E_INVAL, s);
+            continue;
+        }
+        if (unsupported) {
+            fail(a.err, PAAM_E_UNSUPPORTED, s);
+            continue;
+        }
+        if (n > 0) {
+            // the largest value an iterate can take: interference over n chains with at most
+            // ceil(Dmax/Tmin)+1 arrivals each, plus blocking and the chain's own demand
+            double dseg_max = 0.0;
+            for (int64_t c = c0; c < c1; ++c)
+                dseg_max = fmax(dseg_max, (double)(b.cb_seg_off[b.chain_cb_off[c + 1]] -
+                                                   b.cb_seg_off[b.chain_cb_off[c]]));
+            const double m = ceil(Dmax / Tmin) + 1.0;
+            const double bound = (double)n * m * Cmax + Base + Emax_sys + dseg_max * Mmax_sys + Dmax;
+            if (!(bound < 2.305843009213694e18)) /* 2^61: margin under 2^62 */
+                fail(a.err, PAAM_E_RANGE, s);
+        }
+    }
+}
+
+static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+extern "C" int64_t paam_batch_n_sys(const paam_batch *b) { return b ? b->n_sys : 0; }
+extern "C" int64_t paam_batch_n_chain(const paam_batch *b) { return b ? b->n_chain : 0; }
+
+extern "C" void paam_batch_free(paam_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->ctx->device);
+    if (b->block) cudaFree(b->block);
+    free(b);
+}
+
+extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, void *stream_,
+                                     paam_batch **out)
+{
+    if (!out) return PAAM_E_INVAL;
+    *out = nullptr;
+    if (!ctx || !v) return PAAM_E_INVAL;
+    if (v->n_sys < 0 || v->n_chain < 0 || v->n_cb < 0 || v->n_seg < 0 || v->n_exec < 0)
+        return PAAM_E_INVAL;
+    if (!v->sys_chain_off || !v->chain_cb_off || !v->cb_seg_off || !v->sys_exec_off)
+        return PAAM_E_INVAL;
+    if ((v->n_chain > 0 && (!v->T || !v->D || !v->prio || !v->exec || !v->spin)) ||
+        (v->n_cb > 0 && !v->E) || (v->n_seg > 0 && !v->A) || (v->n_exec > 0 && !v->exec_core))
+        return PAAM_E_INVAL;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t stream = (cudaStream_t)stream_;
+
+    paam_batch *b = (paam_batch *)calloc(1, sizeof(paam_batch));
+    if (!b) return PAAM_E_NOMEM;
+    b->ctx = ctx;
+    b->n_sys = v->n_sys;
+    b->n_chain = v->n_chain;
+    b->n_cb = v->n_cb;
+    b->n_seg = v->n_seg;
+    b->n_exec = v->n_exec;
+
+    struct Item {
+        void **dst;
+        const void *src;
+        size_t bytes;
+    } items[] = {
+        {(void **)&b->sys_chain_off, v->sys_chain_off, 8 * (size_t)(v->n_sys + 1)},
+        {(void **)&b->chain_cb_off, v->chain_cb_off, 8 * (size_t)(v->n_chain + 1)},
+        {(void **)&b->cb_seg_off, v->cb_seg_off, 8 * (size_t)(v->n_cb + 1)},
+        {(void **)&b->T, v->T, 8 * (size_t)v->n_chain},
+        {(void **)&b->D, v->D, 8 * (size_t)v->n_chain},
+        {(void **)&b->E, v->E, 8 * (size_t)v->n_cb},
+        {(void **)&b->A, v->A, 8 * (size_t)v->n_seg},
+        {(void **)&b->sys_exec_off, v->sys_exec_off, 8 * (size_t)(v->n_sys + 1)},
+        {(void **)&b->prio, v->prio, 4 * (size_t)v->n_chain},
+        {(void **)&b->exec, v->exec, 4 * (size_t)v->n_chain},
+        {(void **)&b->exec_core, v->exec_core, 4 * (size_t)v->n_exec},
+        {(void **)&b->exec_prio, v->exec_prio, v->exec_prio ? 4 * (size_t)v->n_exec : 0},
+        {(void **)&b->spin, v->spin, (size_t)v->n_chain},
+    };
+    const int n_items = (int)(sizeof(items) / sizeof(items[0]));
+    // acc is validated from a temporary copy, not kept (one accelerator per system)
+    const size_t acc_bytes = v->acc ? 4 * (size_t)v->n_seg : 0;
+    size_t total = 0;
+    for (int i = 0; i < n_items; ++i) total += align_up(items[i].bytes);
+    total += align_up(acc_bytes) + 256;
+    if (cudaMallocAsync(&b->block, total, stream) != cudaSuccess) {
+        cudaGetLastError();
+        free(b);
+        return PAAM_E_NOMEM;
+    }
+    b->block_bytes = total;
+    char *p = (char *)b->block;
+    const cudaMemcpyKind kind = v->is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int rc = PAAM_OK;
+    for (int i = 0; i < n_items; ++i) {
+        if (items[i].src == nullptr && items[i].bytes == 0) {
+            *items[i].dst = nullptr;
+            continue;
+        }
+        *items[i].dst = p;
+        if (items[i].bytes &&
+            cudaMemcpyAsync(p, items[i].src, items[i].bytes, kind, stream) != cudaSuccess)
+            rc = PAAM_E_CUDA;
+        p += align_up(items[i].bytes);
+    }
+    int32_t *acc_dev = nullptr;
+    if (acc_bytes) {
+        acc_dev = (int32_t *)p;
+        if (cudaMemcpyAsync(acc_dev, v->acc, acc_bytes, kind, stream) != cudaSuccess) rc = PAAM_E_CUDA;
+    }
+    int32_t h_err[4] = {0, 0x7fffffff, 0, 0};
+    if (rc == PAAM_OK && b->n_sys > 0) {
+        if (cudaMemcpyAsync(ctx->d_err, h_err, sizeof(h_err), cudaMemcpyHostToDevice, stream) != cudaSuccess)
+            rc = PAAM_E_CUDA;
+        ValidateArgs a;
+        a.b = batch_dev(b);
+        a.n_chain = b->n_chain;
+        a.n_cb = b->n_cb;
+        a.n_seg = b->n_seg;
+        a.n_exec = b->n_exec;
+        a.acc = acc_dev;
+        a.err = ctx->d_err;
+        const int threads = 256;
+        int64_t blocks = (b->n_sys + threads - 1) / threads;
+        if (blocks > 16 * (int64_t)ctx->n_sm) blocks = 16 * (int64_t)ctx->n_sm;
+        validate_kernel<<<(unsigned)blocks, threads, 0, stream>>>(a);
+        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        if (rc == PAAM_OK &&
+            cudaMemcpyAsync(h_err, ctx->d_err, sizeof(h_err), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+            rc = PAAM_E_CUDA;
+    }
+    if (cudaStreamSynchronize(stream) != cudaSuccess) rc = PAAM_E_CUDA;
+    if (rc == PAAM_OK && h_err[0] != 0) rc = h_err[0];
+    if (rc != PAAM_OK) {
+        cudaFree(b->block);
+        free(b);
+        return rc;
+    }
+    b->max_chains = h_err[2];
+    b->max_exec = h_err[3];
+    *out = b;
+    return PAAM_OK;
+}
+
+extern "C" int paam_rta_analyze_batch(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o,
+                                      int64_t *R, uint8_t *status, uint8_t *verdict, void *stream)
+{
+    if (!ctx || !b || !o) return PAAM_E_INVAL;
+    if (b->ctx != ctx) return PAAM_E_STATE;
+    if (o->n_buckets < 1) return PAAM_E_INVAL;
+    if (o->eps_ns < 0 || o->kappa_ns < 0) return PAAM_E_INVAL;
+    if (o->eps_ns > PAAM_MAX_OVERHEAD || o->kappa_ns > PAAM_MAX_OVERHEAD) return PAAM_E_RANGE;
+    if (o->blocking_mode != 0) return PAAM_E_UNSUPPORTED;
+    if (b->n_chain > 0 && (!R || !status)) return PAAM_E_INVAL;
+    if (b->n_sys == 0) return PAAM_OK;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    AnalysisParams p;
+    p.n_buckets = o->n_buckets;
+    p.pad_ = 0;
+    p.eps = o->eps_ns;
+    p.kappa = o->kappa_ns;
+    return paam_launch_analysis(b, p, R, status, verdict, (cudaStream_t)stream);
+}

@@ -1,0 +1,47 @@
+"""Helpers for the GPU parity tests (run through the C ABI)."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+
+def ctx():
+    import paper_2404_06452_gb300 as pkg
+
+    if not hasattr(ctx, "_c"):
+        ctx._c = pkg.Context(0)
+    return ctx._c
+
+
+def gpu_analyze(sy, n_buckets=1, eps=0, kappa=0, device_view=False):
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    c = ctx()
+    src = pkg.to_device(sy) if device_view else sy
+    b = pkg.paam_rta_load_systems(c, src)
+    R, st, v = pkg.analyze(c, b, n_buckets=n_buckets, eps=eps, kappa=kappa)
+    torch.cuda.synchronize()
+    out = dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy())
+    b.free()
+    return out
+
+
+def assert_same(gpu, ref, idx_chain=None, idx_sys=None):
+    R, st, v = gpu["R"], gpu["status"], gpu["verdict"]
+    if idx_chain is not None:
+        R, st = R[idx_chain], st[idx_chain]
+    if idx_sys is not None:
+        v = v[idx_sys]
+    bad = np.nonzero((R != ref["R"]) | (st != ref["status"]))[0]
+    assert len(bad) == 0, f"{len(bad)} chains differ; first {bad[:5]}: gpu R={R[bad[:5]]} st={st[bad[:5]]} " \
+                          f"oracle R={ref['R'][bad[:5]]} st={ref['status'][bad[:5]]}"
+    assert np.array_equal(v, ref["verdict"])
+
+
+def oracle_on(sy, idx, threads=8, **p):
+    """Oracle results for systems ``idx`` of ``sy`` (chains in subset order)."""
+    sub = sy.subset(idx)
+    return oracle.analyze(sub, threads=threads, **p), sy.chain_index(idx)

@@ -1,0 +1,143 @@
+"""GPU vs CPU-oracle parity through the C ABI: bit-exact int64 R, status and
+verdict on every workload shape and parameter set."""
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import paam_gen as g
+from paam_gen import tiny
+
+from gpu_util import assert_same, gpu_analyze, oracle_on
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+PARAMS = [dict(n_buckets=1, eps=0, kappa=0), dict(n_buckets=2, eps=391_000, kappa=129_180),
+          dict(n_buckets=6, eps=198_000, kappa=0), dict(n_buckets=3, eps=0, kappa=41_210)]
+
+
+def test_hand_cases():
+    with open(os.path.join(HERE, "golden", "hand_cases.json")) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        chains = [dict(T=c["T"], D=c["D"], prio=c["prio"], exec=c["exec"], spin=c["spin"],
+                       cbs=[(e, list(a)) for e, a in c["cbs"]]) for c in case["system"]["chains"]]
+        sy = tiny.to_systems([dict(chains=chains, execs=case["system"]["execs"])])
+        out = gpu_analyze(sy, **case["params"])
+        assert out["R"].tolist() == case["R"], case["name"]
+        assert out["status"].tolist() == case["status"], case["name"]
+
+
+@pytest.mark.parametrize("p", PARAMS)
+def test_cfg1_full(p):
+    sy = g.generate("cfg1")
+    assert_same(gpu_analyze(sy, **p), oracle.analyze(sy, **p))
+
+
+@pytest.mark.parametrize("p", PARAMS)
+def test_tiny_random_structures(p):
+    rng = random.Random(99 + p["n_buckets"])
+    dicts = [tiny.tiny_system(rng, n_max=8, cb_max=4, x_max=4, exec_per_core=rng.choice([1, 2, 3]),
+                              periods=tuple(range(5, 200)), e_max=20, a_max=20, p_seg=0.5, p_spin=0.5,
+                              seg_max=3) for _ in range(20000)]
+    sy = tiny.to_systems(dicts)
+    assert_same(gpu_analyze(sy, **p), oracle.analyze(sy, **p))
+
+
+def test_cfg1_shape_with_spin_and_random_executor_priorities():
+    sy = g.generate("cfg2", n_sys=50000, p_spin=0.5, exec_prio_mode=1, x_min=2, x_max=8, exec_per_core=3)
+    for p in PARAMS[:2]:
+        assert_same(gpu_analyze(sy, **p), oracle.analyze(sy, threads=8, **p))
+
+
+def test_device_view_matches_host_view():
+    sy = g.generate("cfg3", n_sys=20000)
+    a = gpu_analyze(sy, n_buckets=2)
+    b = gpu_analyze(sy, n_buckets=2, device_view=True)
+    for k in a:
+        assert np.array_equal(a[k], b[k])
+    assert_same(a, oracle.analyze(sy, threads=8, n_buckets=2))
+
+
+def test_cfg2_full_size_sampled():
+    """The 1,000,000-system workload, in the launch configuration the benchmark
+    times; compared bit-exactly on a stratified sample plus full-volume sums."""
+    sy = g.generate("cfg2")
+    out = gpu_analyze(sy)
+    idx = np.arange(0, sy.n_sys, 97)
+    ref, ci = oracle_on(sy, idx)
+    assert_same(out, ref, idx_chain=ci, idx_sys=idx)
+    # every status value is legal and R is -1 exactly where not schedulable
+    assert set(np.unique(out["status"]).tolist()) <= {0, 1, 2}
+    assert np.all((out["R"] == -1) == (out["status"] != 0))
+    # the analysis admits some chains but (with 8-16 chains per system) no whole system
+    assert 0.05 < (out["status"] == 0).mean() < 0.95
+
+
+def test_cfg3_full_size_sampled():
+    sy = g.generate("cfg3")
+    out = gpu_analyze(sy, n_buckets=2, eps=198_000, kappa=41_210)
+    n = sy.chains_per_system()
+    idx = np.unique(np.concatenate([np.arange(0, sy.n_sys, 997), np.nonzero(n >= 40)[0][:2000]]))
+    ref, ci = oracle_on(sy, idx, n_buckets=2, eps=198_000, kappa=41_210)
+    assert_same(out, ref, idx_chain=ci, idx_sys=idx)
+
+
+def test_edge_shapes():
+    # empty systems, empty chains, 64 chains, a chain with 12 segments in one callback
+    rng = random.Random(5)
+    dicts = [dict(chains=[], execs=[dict(core=0, prio=0)])]
+    dicts.append(dict(chains=[dict(T=10, D=10, prio=0, exec=0, spin=0, cbs=[])], execs=[dict(core=0, prio=0)]))
+    dicts.append(tiny.tiny_system(rng, n_min=64, n_max=64, cb_max=3, x_max=8, periods=tuple(range(1000, 5000)),
+                                  e_max=30, a_max=30, p_seg=0.5, seg_max=2))
+    dicts.append(dict(chains=[dict(T=1, D=1, prio=5, exec=0, spin=1, cbs=[(0, [0] * 12)])],
+                      execs=[dict(core=0, prio=0)]))
+    dicts.append(tiny.tiny_system(rng, n_min=64, n_max=64, cb_max=12, x_max=8, periods=tuple(range(10**8, 10**9)),
+                                  e_max=10**6, a_max=10**6, p_seg=0.5, seg_max=1))
+    sy = tiny.to_systems(dicts)
+    for p in PARAMS:
+        assert_same(gpu_analyze(sy, **p), oracle.analyze(sy, **p))
+
+
+def test_empty_batch():
+    sy = tiny.to_systems([])
+    out = gpu_analyze(sy)
+    assert len(out["R"]) == 0 and len(out["verdict"]) == 0
+
+
+def _expect_error(sy, code, **p):
+    import paper_2404_06452_gb300 as pkg
+    from gpu_util import ctx
+
+    with pytest.raises(pkg.PaamError) as ei:
+        b = pkg.paam_rta_load_systems(ctx(), sy)
+        pkg.analyze(ctx(), b, **p)
+    assert ei.value.code == code
+
+
+def test_invalid_inputs_rejected():
+    base = dict(chains=[dict(T=10, D=10, prio=1, exec=0, spin=0, cbs=[(2, [1])]),
+                        dict(T=20, D=20, prio=0, exec=0, spin=0, cbs=[(3, [])])],
+                execs=[dict(core=0, prio=1)])
+
+    def mod(f):
+        d = json.loads(json.dumps(base))
+        f(d)
+        for ch in d["chains"]:
+            ch["cbs"] = [(e, a) for e, a in ch["cbs"]]
+        return tiny.to_systems([d])
+
+    _expect_error(mod(lambda d: d["chains"][0].update(D=11)), -1)      # D > T
+    _expect_error(mod(lambda d: d["chains"][0].update(T=0, D=0)), -1)  # T <= 0
+    _expect_error(mod(lambda d: d["chains"][1].update(prio=1)), -1)    # duplicate priority
+    _expect_error(mod(lambda d: d["chains"][1].update(exec=3)), -1)    # executor out of range
+    _expect_error(mod(lambda d: d["chains"][0].update(cbs=[(-1, [])])), -1)  # negative WCET
+    sy = mod(lambda d: None)
+    sy.acc = np.ones_like(sy.acc)
+    _expect_error(sy, -6)                                              # second accelerator
+    big = mod(lambda d: d["chains"][0].update(T=2**40, D=2**40, cbs=[(2**40, [2**40] * 8)]))
+    _expect_error(big, -2)                                             # int64 range
+    _expect_error(mod(lambda d: None), -2, eps=2**33)                  # eps above the cap
