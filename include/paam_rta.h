@@ -160,12 +160,41 @@ void paam_batch_free(paam_batch *b);
  *   verdict[n_sys]   1 if every chain of the system is PAAM_ST_SCHED (the
  *                    admission test of Sec. IV-A), else 0
  * verdict may be NULL.  Results are bit-identical to the definition for any
- * launch configuration.  Errors: PAAM_E_INVAL (NULL outputs, n_buckets < 1),
+ * launch configuration.  The first call for a given (outputs, options,
+ * launch configuration) captures the analysis into a CUDA graph owned by the
+ * batch; later calls with the same key replay it on `stream`.  A batch may be
+ * analysed by one host thread at a time.  Errors: PAAM_E_INVAL (NULL outputs, n_buckets < 1),
  * PAAM_E_RANGE (eps or kappa above PAAM_MAX_OVERHEAD), PAAM_E_UNSUPPORTED
  * (blocking_mode != 0), PAAM_E_CUDA (launch failure).
  */
 int paam_rta_analyze_batch(paam_ctx *ctx, const paam_batch *batch, const paam_analysis_opts *opts,
                            int64_t *R, uint8_t *status, uint8_t *verdict, void *stream);
+
+/*
+ * Launch configurations.  The analysis has several built-in launch
+ * configurations (lanes per system, chain-table size of the first pass, lanes
+ * per system for systems with more chains, CTA size); every one produces
+ * bit-identical results.  A batch starts with configuration 0.
+ *
+ * paam_rta_autotune times every configuration on the batch itself (the
+ * analysis is run 4 times per configuration, the first run discarded), keeps
+ * the fastest for later paam_rta_analyze_batch calls on this batch, and
+ * returns its index (>= 0) or a negative error.  times_ms, if not NULL,
+ * receives up to max_out per-configuration times in milliseconds.  It
+ * synchronises `stream` and allocates temporary device outputs.
+ */
+int paam_rta_num_launch_configs(void);
+int paam_rta_autotune(paam_ctx *ctx, paam_batch *batch, const paam_analysis_opts *opts, void *stream,
+                      float *times_ms, int max_out);
+int paam_rta_set_launch_config(paam_batch *batch, int index); /* PAAM_E_INVAL if out of range */
+int paam_rta_get_launch_config(const paam_batch *batch);
+
+/*
+ * Diagnostics: number of CUDA kernels this library has launched in this
+ * process (all contexts).  Not part of the paper; used to report how many
+ * of the library's own kernels ran inside a timed region.
+ */
+uint64_t paam_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -65,6 +65,12 @@ def lib():
             "paam_batch_free": (None, [_c_void_p]),
             "paam_rta_analyze_batch": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
                                                       _c_void_p, _c_void_p, _c_void_p]),
+            "paam_launch_count": (ctypes.c_uint64, []),
+            "paam_rta_num_launch_configs": (ctypes.c_int, []),
+            "paam_rta_autotune": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
+                                                 _c_void_p, ctypes.c_int]),
+            "paam_rta_set_launch_config": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
+            "paam_rta_get_launch_config": (ctypes.c_int, [_c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -76,7 +82,14 @@ def lib():
 def exported_symbols() -> list:
     """Names this binding expects the library to export."""
     return ["paam_create", "paam_destroy", "paam_strerror", "paam_rta_load_systems", "paam_batch_n_sys",
-            "paam_batch_n_chain", "paam_batch_free", "paam_rta_analyze_batch"]
+            "paam_batch_n_chain", "paam_batch_free", "paam_rta_analyze_batch", "paam_launch_count",
+            "paam_rta_num_launch_configs", "paam_rta_autotune", "paam_rta_set_launch_config",
+            "paam_rta_get_launch_config"]
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().paam_launch_count())
 
 
 def strerror(code: int) -> str:
@@ -205,3 +218,26 @@ def paam_rta_analyze_batch(ctx: Context, batch: Batch, opts: AnalysisOpts, R, st
                            stream=None):
     _check(lib().paam_rta_analyze_batch(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(R), _ptr(status),
                                         _ptr(verdict), _stream_ptr(stream)), "paam_rta_analyze_batch")
+
+
+def paam_rta_num_launch_configs() -> int:
+    return int(lib().paam_rta_num_launch_configs())
+
+
+def paam_rta_autotune(ctx: Context, batch: Batch, opts: AnalysisOpts, stream=None) -> tuple:
+    """Time every launch configuration on ``batch``; keep the fastest.
+    Returns (chosen index, list of per-configuration milliseconds)."""
+    n = paam_rta_num_launch_configs()
+    times = (ctypes.c_float * n)()
+    rc = lib().paam_rta_autotune(ctx.handle, batch.handle, ctypes.byref(opts), _stream_ptr(stream), times, n)
+    if rc < 0:
+        raise PaamError(rc, "paam_rta_autotune")
+    return rc, [float(t) for t in times]
+
+
+def paam_rta_set_launch_config(batch: Batch, index: int):
+    _check(lib().paam_rta_set_launch_config(batch.handle, int(index)), "paam_rta_set_launch_config")
+
+
+def paam_rta_get_launch_config(batch: Batch) -> int:
+    return int(lib().paam_rta_get_launch_config(batch.handle))

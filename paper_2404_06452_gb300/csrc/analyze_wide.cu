@@ -1,4 +1,5 @@
-// analyze.cu -- batched WCRT analysis of PAAM (Sec. IV-F, Theorem 1).
+// analyze_wide.cu -- exact int64 analysis of PAAM (Sec. IV-F, Theorem 1) for
+// systems whose times do not fit the 32-bit fast path (analyze_fast.cu).
 //
 // A group of G lanes analyses one system at a time.  The system's chain table
 // lives in shared memory.  Set-up work is spread over chains (lane c handles
@@ -230,9 +231,12 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     __syncwarp(gmask);
 }
 
+// Systems are either all of the batch (list == nullptr) or the list
+// list[0 .. *count).
 template <int G, int MAXN>
-__global__ void __launch_bounds__(256) analyze_kernel(BatchDev b, AnalysisParams p, int64_t *R,
-                                                      uint8_t *st, uint8_t *verdict)
+__global__ void __launch_bounds__(256) analyze_wide_kernel(BatchDev b, AnalysisParams p, int64_t *R,
+                                                           uint8_t *st, uint8_t *verdict,
+                                                           const int32_t *list, const int32_t *count)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int groups = blockDim.x / G;
@@ -240,35 +244,33 @@ __global__ void __launch_bounds__(256) analyze_kernel(BatchDev b, AnalysisParams
     const int lane = threadIdx.x % G;
     SysSmem<MAXN> &s = reinterpret_cast<SysSmem<MAXN> *>(smem_raw)[grp];
     const unsigned gmask = group_mask<G>();
-    for (int64_t sys = (int64_t)blockIdx.x * groups + grp; sys < b.n_sys; sys += (int64_t)gridDim.x * groups)
+    const int64_t n = list ? (int64_t)*count : b.n_sys;
+    for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n; i += (int64_t)gridDim.x * groups) {
+        const int64_t sys = list ? (int64_t)list[i] : i;
         analyze_system<G, MAXN>(b, p, sys, s, lane, gmask, R, st, verdict);
-}
-
-template <int G, int MAXN>
-int launch(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
-           cudaStream_t stream)
-{
-    const int threads = 256;
-    const int groups = threads / G;
-    const size_t smem = sizeof(SysSmem<MAXN>) * groups;
-    auto kern = analyze_kernel<G, MAXN>;
-    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-    if (per_sm < 1) per_sm = 1;
-    int64_t blocks = (bt->n_sys + groups - 1) / groups;
-    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
-    if (blocks > cap) blocks = cap;
-    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict);
-    PAAM_CUDA_TRY(cudaGetLastError());
-    return PAAM_OK;
+    }
 }
 
 } // namespace
 
-int paam_launch_analysis(const paam_batch *b, const AnalysisParams &p, int64_t *R, uint8_t *status,
-                         uint8_t *verdict, cudaStream_t stream)
+int paam_launch_wide(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st,
+                     uint8_t *verdict, const int32_t *list, const int32_t *count, int64_t max_items,
+                     cudaStream_t stream)
 {
-    if (b->max_chains <= 16) return launch<8, 16>(b, p, R, status, verdict, stream);
-    return launch<32, 64>(b, p, R, status, verdict, stream);
+    constexpr int G = 32, MAXN = 64;
+    const int threads = 256;
+    const int groups = threads / G;
+    const size_t smem = sizeof(SysSmem<MAXN>) * groups;
+    auto kern = analyze_wide_kernel<G, MAXN>;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (max_items + groups - 1) / groups;
+    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, list, count);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    return PAAM_OK;
 }

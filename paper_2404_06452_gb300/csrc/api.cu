@@ -3,7 +3,15 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "internal.cuh"
+
+static std::atomic<uint64_t> g_launches{0};
+
+void paam_count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+extern "C" uint64_t paam_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 void paam_note_cuda_error(cudaError_t e, const char *expr, const char *file, int line)
 {
@@ -48,6 +56,17 @@ extern "C" int paam_create(paam_ctx **out, int device_ordinal)
         free(c);
         return PAAM_E_NOMEM;
     }
+    if (cudaMalloc(&c->d_stats, ST_COUNT * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(c->d_err);
+        free(c);
+        return PAAM_E_NOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaFree(c->d_err);
+        cudaFree(c->d_stats);
+        free(c);
+        return PAAM_E_CUDA;
+    }
     // keep freed batch memory in the device pool so repeated load/free cycles are cheap
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, device_ordinal) == cudaSuccess) {
@@ -63,6 +82,8 @@ extern "C" void paam_destroy(paam_ctx *c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaFree(c->d_err);
+    cudaFree(c->d_stats);
+    cudaStreamDestroy(c->capture_stream);
     free(c);
 }
 
@@ -75,6 +96,7 @@ struct ValidateArgs {
     int64_t n_chain, n_cb, n_seg, n_exec;
     const int32_t *acc;
     int32_t *err; // [0] code, [1] first bad system (min), [2] max chains, [3] max executors
+    unsigned long long *stats; // ST_* maxima
 };
 
 __device__ __forceinline__ void fail(int32_t *err, int32_t code, int64_t sys)
@@ -87,6 +109,8 @@ __global__ void validate_kernel(ValidateArgs a)
 {
     const BatchDev &b = a.b;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long lmax[ST_COUNT] = {0, 0, 0, 0, 0};
+    int32_t nmax = 0, xmax = 0;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < b.n_sys; s += stride) {
         if (s == 0) { // global sentinels
             if (b.sys_chain_off[0] != 0 || b.sys_exec_off[0] != 0 || b.chain_cb_off[0] != 0 ||
@@ -108,8 +132,9 @@ __global__ void validate_kernel(ValidateArgs a)
             fail(a.err, PAAM_E_INVAL, s);
             continue;
         }
-        atomicMax(&a.err[2], (int32_t)n);
-        atomicMax(&a.err[3], (int32_t)(nx < 0x7fffffff ? nx : 0x7fffffff));
+        nmax = (int32_t)n > nmax ? (int32_t)n : nmax;
+        const int32_t nx32 = (int32_t)(nx < 0x7fffffff ? nx : 0x7fffffff);
+        xmax = nx32 > xmax ? nx32 : xmax;
         // executors
         bool bad = false;
         for (int64_t x = x0; x < x1 && !bad; ++x) {
@@ -136,11 +161,12 @@ __global__ void validate_kernel(ValidateArgs a)
             for (int64_t k = c0; k < c; ++k)
                 if (b.prio[k] == b.prio[c]) bad = true;
             const int64_t b0 = b.chain_cb_off[c], b1 = b.chain_cb_off[c + 1];
-            if (b0 < 0 || b1 < b0 || b1 > a.n_cb || (c > c0 && b0 != b.chain_cb_off[c - 1 + 1])) {
+            if (b0 < 0 || b1 < b0 || b1 > a.n_cb) {
                 bad = true;
                 break;
             }
             double Ec = 0.0, Sc = 0.0, dc = 0.0;
+            unsigned long long Ei = 0, Si = 0, di = 0;
             for (int64_t cb = b0; cb < b1 && !bad; ++cb) {
                 const int64_t e = b.E[cb];
                 const int64_t q0 = b.cb_seg_off[cb], q1 = b.cb_seg_off[cb + 1];
@@ -149,6 +175,7 @@ __global__ void validate_kernel(ValidateArgs a)
                     break;
                 }
                 Ec += (double)e;
+                Ei += (unsigned long long)e;
                 if ((double)e > Emax_sys) Emax_sys = (double)e;
                 for (int64_t q = q0; q < q1; ++q) {
                     const int64_t av = b.A[q];
@@ -160,21 +187,23 @@ __global__ void validate_kernel(ValidateArgs a)
                     const double as = (double)av + 2.0 * OV;
                     Sc += as;
                     dc += 1.0;
+                    Si += (unsigned long long)av;
+                    di += 1;
                     if (as > Mmax_sys) Mmax_sys = as;
                 }
             }
             if ((double)D > Dmax) Dmax = (double)D;
             if ((double)T < Tmin) Tmin = (double)T;
+            lmax[ST_TMAX] = max(lmax[ST_TMAX], (unsigned long long)T);
+            lmax[ST_DMAX] = max(lmax[ST_DMAX], (unsigned long long)D);
+            lmax[ST_ECMAX] = max(lmax[ST_ECMAX], Ei);
+            lmax[ST_SCMAX] = max(lmax[ST_SCMAX], Si);
+            lmax[ST_DELTAMAX] = max(lmax[ST_DELTAMAX], di);
             const double spin_or_d = (double)D > dc * OV ? (double)D : dc * OV;
             const double C = Ec + spin_or_d + Sc;
             if (C > Cmax) Cmax = C;
             const double base = Ec + Sc + dc * OV;
             if (base > Base) Base = base;
-            (void)Sc;
-            if (dc > 0.0) { // delta * blk contribution to the base
-                const double extra = dc * 1.0;
-                (void)extra;
-            }
         }
         if (bad) {
             fail(a.err, PAAM_E_INVAL, s);
@@ -197,6 +226,19 @@ __global__ void validate_kernel(ValidateArgs a)
                 fail(a.err, PAAM_E_RANGE, s);
         }
     }
+    // one atomic per warp and statistic
+    for (int off = 16; off > 0; off >>= 1) {
+        nmax = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, off));
+        xmax = max(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
+        for (int i = 0; i < ST_COUNT; ++i) lmax[i] = max(lmax[i], __shfl_xor_sync(0xffffffffu, lmax[i], off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (nmax) atomicMax(&a.err[2], nmax);
+        if (xmax) atomicMax(&a.err[3], xmax);
+        for (int i = 0; i < ST_COUNT; ++i)
+            if (lmax[i]) atomicMax(&a.stats[i], lmax[i]);
+    }
+
 }
 
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -208,6 +250,7 @@ extern "C" void paam_batch_free(paam_batch *b)
 {
     if (!b) return;
     cudaSetDevice(b->ctx->device);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->block) cudaFree(b->block);
     free(b);
 }
@@ -262,6 +305,8 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
     size_t total = 0;
     for (int i = 0; i < n_items; ++i) total += align_up(items[i].bytes);
     total += align_up(acc_bytes) + 256;
+    const size_t list_bytes = 4 * (size_t)(v->n_sys > 0 ? v->n_sys : 1);
+    total += 2 * align_up(list_bytes) + 256;
     if (cudaMallocAsync(&b->block, total, stream) != cudaSuccess) {
         cudaGetLastError();
         free(b);
@@ -287,9 +332,16 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
         acc_dev = (int32_t *)p;
         if (cudaMemcpyAsync(acc_dev, v->acc, acc_bytes, kind, stream) != cudaSuccess) rc = PAAM_E_CUDA;
     }
+    p += align_up(acc_bytes);
+    b->list_big = (int32_t *)p;
+    p += align_up(list_bytes);
+    b->list_wide = (int32_t *)p;
+    p += align_up(list_bytes);
+    b->counts = (int32_t *)p;
     int32_t h_err[4] = {0, 0x7fffffff, 0, 0};
     if (rc == PAAM_OK && b->n_sys > 0) {
-        if (cudaMemcpyAsync(ctx->d_err, h_err, sizeof(h_err), cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        if (cudaMemcpyAsync(ctx->d_err, h_err, sizeof(h_err), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            cudaMemsetAsync(ctx->d_stats, 0, ST_COUNT * sizeof(unsigned long long), stream) != cudaSuccess)
             rc = PAAM_E_CUDA;
         ValidateArgs a;
         a.b = batch_dev(b);
@@ -299,13 +351,17 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
         a.n_exec = b->n_exec;
         a.acc = acc_dev;
         a.err = ctx->d_err;
+        a.stats = ctx->d_stats;
         const int threads = 256;
         int64_t blocks = (b->n_sys + threads - 1) / threads;
         if (blocks > 16 * (int64_t)ctx->n_sm) blocks = 16 * (int64_t)ctx->n_sm;
         validate_kernel<<<(unsigned)blocks, threads, 0, stream>>>(a);
+        paam_count_launch();
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
         if (rc == PAAM_OK &&
-            cudaMemcpyAsync(h_err, ctx->d_err, sizeof(h_err), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+            (cudaMemcpyAsync(h_err, ctx->d_err, sizeof(h_err), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+             cudaMemcpyAsync(b->stats, ctx->d_stats, sizeof(b->stats), cudaMemcpyDeviceToHost, stream) !=
+                 cudaSuccess))
             rc = PAAM_E_CUDA;
     }
     if (cudaStreamSynchronize(stream) != cudaSuccess) rc = PAAM_E_CUDA;
@@ -321,22 +377,134 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
     return PAAM_OK;
 }
 
-extern "C" int paam_rta_analyze_batch(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o,
-                                      int64_t *R, uint8_t *status, uint8_t *verdict, void *stream)
+static int check_opts(const paam_analysis_opts *o)
 {
-    if (!ctx || !b || !o) return PAAM_E_INVAL;
-    if (b->ctx != ctx) return PAAM_E_STATE;
     if (o->n_buckets < 1) return PAAM_E_INVAL;
     if (o->eps_ns < 0 || o->kappa_ns < 0) return PAAM_E_INVAL;
     if (o->eps_ns > PAAM_MAX_OVERHEAD || o->kappa_ns > PAAM_MAX_OVERHEAD) return PAAM_E_RANGE;
     if (o->blocking_mode != 0) return PAAM_E_UNSUPPORTED;
-    if (b->n_chain > 0 && (!R || !status)) return PAAM_E_INVAL;
-    if (b->n_sys == 0) return PAAM_OK;
-    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    return PAAM_OK;
+}
+
+static AnalysisParams params_of(const paam_analysis_opts *o)
+{
     AnalysisParams p;
     p.n_buckets = o->n_buckets;
     p.pad_ = 0;
     p.eps = o->eps_ns;
     p.kappa = o->kappa_ns;
-    return paam_launch_analysis(b, p, R, status, verdict, (cudaStream_t)stream);
+    return p;
+}
+
+extern "C" int paam_rta_analyze_batch(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o,
+                                      int64_t *R, uint8_t *status, uint8_t *verdict, void *stream_)
+{
+    if (!ctx || !b || !o) return PAAM_E_INVAL;
+    if (b->ctx != ctx) return PAAM_E_STATE;
+    int rc = check_opts(o);
+    if (rc != PAAM_OK) return rc;
+    if (b->n_chain > 0 && (!R || !status)) return PAAM_E_INVAL;
+    if (b->n_sys == 0) return PAAM_OK;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const AnalysisParams p = params_of(o);
+    paam_batch *bm = const_cast<paam_batch *>(b); // the captured graph is a cache inside the handle
+    const bool same = bm->graph && bm->graph_key.R == R && bm->graph_key.status == status &&
+                      bm->graph_key.verdict == verdict && bm->graph_key.cfg_index == bm->cfg_index &&
+                      bm->graph_key.p.n_buckets == p.n_buckets && bm->graph_key.p.eps == p.eps &&
+                      bm->graph_key.p.kappa == p.kappa;
+    if (!same) {
+        if (bm->graph) {
+            cudaGraphExecDestroy(bm->graph);
+            bm->graph = nullptr;
+        }
+        cudaStream_t cs = ctx->capture_stream;
+        PAAM_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int nk = 0;
+        rc = paam_enqueue_analysis(b, p, kLaunchCfgs[bm->cfg_index], R, status, verdict, cs, &nk);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+        if (rc != PAAM_OK || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc != PAAM_OK ? rc : PAAM_E_CUDA;
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&bm->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            bm->graph = nullptr;
+            return PAAM_E_CUDA;
+        }
+        bm->graph_kernels = nk;
+        bm->graph_key.R = R;
+        bm->graph_key.status = status;
+        bm->graph_key.verdict = verdict;
+        bm->graph_key.p = p;
+        bm->graph_key.cfg_index = bm->cfg_index;
+    }
+    PAAM_CUDA_TRY(cudaGraphLaunch(bm->graph, stream));
+    paam_count_launch((unsigned)bm->graph_kernels);
+    return PAAM_OK;
+}
+
+extern "C" int paam_rta_num_launch_configs(void) { return kNumLaunchCfgs; }
+
+extern "C" int paam_rta_set_launch_config(paam_batch *b, int index)
+{
+    if (!b || index < 0 || index >= kNumLaunchCfgs) return PAAM_E_INVAL;
+    b->cfg_index = index;
+    return PAAM_OK;
+}
+
+extern "C" int paam_rta_get_launch_config(const paam_batch *b) { return b ? b->cfg_index : -1; }
+
+extern "C" int paam_rta_autotune(paam_ctx *ctx, paam_batch *b, const paam_analysis_opts *o, void *stream_,
+                                 float *times_ms, int max_out)
+{
+    if (!ctx || !b || !o) return PAAM_E_INVAL;
+    if (b->ctx != ctx) return PAAM_E_STATE;
+    int rc = check_opts(o);
+    if (rc != PAAM_OK) return rc;
+    if (b->n_sys == 0) return 0;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const AnalysisParams p = params_of(o);
+    void *tmp = nullptr;
+    const size_t rb = 8 * (size_t)b->n_chain, sb = (size_t)b->n_chain, vb = (size_t)b->n_sys;
+    if (cudaMallocAsync(&tmp, rb + sb + vb + 64, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PAAM_E_NOMEM;
+    }
+    int64_t *R = (int64_t *)tmp;
+    uint8_t *st = (uint8_t *)tmp + rb;
+    uint8_t *v = st + sb;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int i = 0; i < kNumLaunchCfgs && rc == PAAM_OK; ++i) {
+        float t_min = 1e30f;
+        for (int rep = 0; rep < 4 && rc == PAAM_OK; ++rep) {
+            cudaEventRecord(e0, stream);
+            rc = paam_enqueue_analysis(b, p, kLaunchCfgs[i], R, st, v, stream, nullptr);
+            cudaEventRecord(e1, stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = PAAM_E_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < t_min) t_min = ms; // the first run warms caches and code
+        }
+        if (times_ms && i < max_out) times_ms[i] = t_min;
+        if (t_min < best_ms) {
+            best_ms = t_min;
+            best = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(tmp, stream);
+    cudaStreamSynchronize(stream);
+    if (rc != PAAM_OK) return rc;
+    b->cfg_index = best;
+    return best;
 }

@@ -17,11 +17,27 @@
 
 void paam_note_cuda_error(cudaError_t e, const char *expr, const char *file, int line);
 
+// Counts kernel launches made by this library (paam_launch_count()).
+void paam_count_launch(unsigned n = 1);
+
+struct AnalysisParams {
+    int32_t n_buckets;
+    int32_t pad_;
+    int64_t eps;
+    int64_t kappa;
+};
+
+// Batch-wide maxima recorded by validation; they decide which kernels an
+// analysis needs (the 32-bit fast path covers every system when they fit).
+enum { ST_TMAX = 0, ST_DMAX, ST_ECMAX, ST_SCMAX, ST_DELTAMAX, ST_COUNT };
+
 struct paam_ctx {
     int device;
     int n_sm;
     int max_smem_optin;
-    int32_t *d_err; // device error word used by validation (first error wins)
+    cudaStream_t capture_stream; // private stream used to capture analysis graphs
+    int32_t *d_err;        // validation: [0] code, [1] first bad system, [2] max chains, [3] max executors
+    unsigned long long *d_stats; // validation: ST_* maxima
 };
 
 // Device copy of a validated batch: the same SoA/CSR arrays as
@@ -34,8 +50,23 @@ struct paam_batch {
     uint8_t *spin;
     int32_t max_chains; // largest chain count of any system
     int32_t max_exec;
+    unsigned long long stats[ST_COUNT];
+    // scratch for one analysis: [0] systems deferred to the wide configuration,
+    // [1] systems deferred to the exact int64 kernel, both n_sys long; counts
+    int32_t *list_big, *list_wide;
+    int32_t *counts; // [0] big, [1] wide
     void *block;
     size_t block_bytes;
+    int cfg_index; // launch configuration (index into kLaunchCfgs)
+    // the analysis captured as a CUDA graph, replayed while its key matches
+    cudaGraphExec_t graph;
+    int graph_kernels;
+    struct {
+        int64_t *R;
+        uint8_t *status, *verdict;
+        AnalysisParams p;
+        int cfg_index;
+    } graph_key;
 };
 
 // Read-only view handed to the kernels.
@@ -54,13 +85,6 @@ struct BatchDev {
     const int32_t *__restrict__ exec_core;
     const int32_t *__restrict__ exec_prio;
     const uint8_t *__restrict__ spin;
-};
-
-struct AnalysisParams {
-    int32_t n_buckets;
-    int32_t pad_;
-    int64_t eps;
-    int64_t kappa;
 };
 
 inline BatchDev batch_dev(const paam_batch *b)
@@ -83,6 +107,21 @@ inline BatchDev batch_dev(const paam_batch *b)
     return d;
 }
 
-// Analysis launcher (analyze.cu).
-int paam_launch_analysis(const paam_batch *b, const AnalysisParams &p, int64_t *R, uint8_t *status,
-                         uint8_t *verdict, cudaStream_t stream);
+// A launch configuration of the analysis: group width and table size of the
+// first pass, group width of the pass over systems with more chains, CTA size.
+struct LaunchCfg {
+    int g_small, maxn_small, g_big, threads;
+};
+extern const LaunchCfg kLaunchCfgs[];
+extern const int kNumLaunchCfgs;
+
+// Enqueue the whole analysis of a batch (analyze_fast.cu); *n_kernels receives
+// the number of kernels it launched.
+int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const LaunchCfg &cfg, int64_t *R,
+                          uint8_t *status, uint8_t *verdict, cudaStream_t stream, int *n_kernels);
+
+// Exact int64 kernel (analyze_wide.cu) over list[0 .. *count) or, with
+// list == nullptr, over every system.
+int paam_launch_wide(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st,
+                     uint8_t *verdict, const int32_t *list, const int32_t *count, int64_t max_items,
+                     cudaStream_t stream);

@@ -1,0 +1,112 @@
+"""Every launch configuration, the int64 fallback and graph replay give the
+oracle's bit-exact results."""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import paam_gen as g
+from paam_gen import tiny
+
+from gpu_util import assert_same, ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_batch():
+    """cfg3-shaped systems (2..64 chains) plus systems whose times exceed the
+    32-bit fast path (periods up to ~34 s), interleaved."""
+    a = g.generate("cfg3", n_sys=6000)
+    rng = random.Random(17)
+    big = [tiny.tiny_system(rng, n_min=2, n_max=40, cb_max=5, x_max=6, periods=tuple(range(2**30, 2**35, 2**27)),
+                            e_max=2**27, a_max=2**26, p_seg=0.5, p_spin=0.5, seg_max=2) for _ in range(300)]
+    b = tiny.to_systems(big)
+    idx_a = np.arange(a.n_sys)
+    parts = []
+    # interleave: 20 fast systems, then 1 wide one
+    out = []
+    k = 0
+    for i in range(b.n_sys):
+        out.append(("a", idx_a[k:k + 20]))
+        out.append(("b", np.array([i])))
+        k += 20
+    out.append(("a", idx_a[k:]))
+    subs = [(a if w == "a" else b).subset(ix) for w, ix in out if len(ix)]
+    return _concat(subs)
+
+
+def _concat(subs):
+    def cat_off(name, count_name):
+        offs, base = [np.zeros(1, np.int64)], 0
+        for s in subs:
+            o = getattr(s, name)
+            offs.append(o[1:] + base)
+            base += o[-1]
+        return np.concatenate(offs)
+
+    cat = lambda f: np.concatenate([getattr(s, f) for s in subs])
+    return g.Systems(cat_off("sys_chain_off", None), cat_off("chain_cb_off", None), cat_off("cb_seg_off", None),
+                     cat("T"), cat("D"), cat("prio"), cat("exec"), cat("spin"), cat("E"), cat("A"), cat("acc"),
+                     cat_off("sys_exec_off", None), cat("exec_core"), cat("exec_prio"))
+
+
+def test_every_launch_config_bit_exact():
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    sy = _mixed_batch()
+    ref = oracle.analyze(sy, threads=8, n_buckets=2, eps=1000, kappa=500)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    for i in range(pkg.paam_rta_num_launch_configs()):
+        pkg.paam_rta_set_launch_config(b, i)
+        R, st, v = pkg.analyze(ctx(), b, n_buckets=2, eps=1000, kappa=500)
+        torch.cuda.synchronize()
+        assert_same(dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy()), ref)
+    b.free()
+
+
+def test_graph_replay_with_changing_outputs_and_options():
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    sy = g.generate("cfg3", n_sys=5000)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    dev = torch.device("cuda", 0)
+    outs = [(torch.empty(b.n_chain, dtype=torch.int64, device=dev), torch.empty(b.n_chain, dtype=torch.uint8, device=dev),
+             torch.empty(b.n_sys, dtype=torch.uint8, device=dev)) for _ in range(2)]
+    plan = [(0, dict(n_buckets=1, eps=0, kappa=0)), (0, dict(n_buckets=1, eps=0, kappa=0)),
+            (1, dict(n_buckets=1, eps=0, kappa=0)), (1, dict(n_buckets=3, eps=200_000, kappa=100_000)),
+            (0, dict(n_buckets=3, eps=200_000, kappa=100_000)), (0, dict(n_buckets=1, eps=0, kappa=0))]
+    refs = {}
+    for which, p in plan:
+        R, st, v = outs[which]
+        R.fill_(123)
+        st.fill_(9)
+        pkg.paam_rta_analyze_batch(ctx(), b, pkg.analysis_opts(**p), R, st, v)
+        torch.cuda.synchronize()
+        key = tuple(sorted(p.items()))
+        if key not in refs:
+            refs[key] = oracle.analyze(sy, threads=8, **p)
+        assert_same(dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy()), refs[key])
+    b.free()
+
+
+def test_autotune_picks_a_valid_config_and_stays_exact():
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    sy = g.generate("cfg2", n_sys=50000)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    best, times = pkg.paam_rta_autotune(ctx(), b, pkg.analysis_opts())
+    assert 0 <= best < pkg.paam_rta_num_launch_configs()
+    assert all(t > 0 for t in times) and times[best] == min(times)
+    assert pkg.paam_rta_get_launch_config(b) == best
+    R, st, v = pkg.analyze(ctx(), b)
+    torch.cuda.synchronize()
+    assert_same(dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy()),
+                oracle.analyze(sy, threads=8))
+    b.free()
