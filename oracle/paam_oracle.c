@@ -45,6 +45,9 @@
 enum { ST_SCHED = 0, ST_OVERRUN = 1, ST_DEP = 2, ST_ITERCAP = 3 };
 
 #define O_INF INT64_MAX
+
+/* diagnostic counters (test infrastructure): fixed-point iterations per system */
+static __thread int64_t g_seg_iters, g_chain_iters;
 #define O_ITER_LIMIT 100000000LL /* never reached: every iteration raises some mu */
 
 typedef struct {
@@ -197,6 +200,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                         work += 1;
                     }
                 }
+                g_seg_iters += 1;
                 if (nh == h) break;
                 h = nh;
                 if (++it > O_ITER_LIMIT) {
@@ -267,6 +271,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                         work += 1;
                     }
                 }
+                g_chain_iters += 1;
                 if (Rn == R) {
                     ch[c].status = ST_SCHED;
                     ch[c].Hstar = hs;
@@ -307,6 +312,26 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
     if (verdict) verdict[s] = ok;
     if (work_out) work_out[s] = work;
     free(ch);
+}
+
+/* per-system iteration counts of the last oracle_analyze_iters call */
+void oracle_analyze_iters(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
+                          const int64_t *chain_cb_off, const int64_t *cb_seg_off, const int64_t *T,
+                          const int64_t *D, const int32_t *prio, const int32_t *exec,
+                          const uint8_t *spin, const int64_t *E, const int64_t *A,
+                          const int64_t *sys_exec_off, const int32_t *exec_core,
+                          const int32_t *exec_prio, int32_t n_buckets, int64_t eps, int64_t kappa,
+                          int64_t *R, uint8_t *status, int64_t *seg_iters, int64_t *chain_iters)
+{
+    for (int64_t s = lo; s < hi; ++s) {
+        g_seg_iters = 0;
+        g_chain_iters = 0;
+        analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A,
+                       sys_exec_off, exec_core, exec_prio, NULL, n_buckets, eps, kappa, R, status,
+                       NULL, NULL, NULL);
+        seg_iters[s] = g_seg_iters;
+        chain_iters[s] = g_chain_iters;
+    }
 }
 
 /*

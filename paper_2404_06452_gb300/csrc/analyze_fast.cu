@@ -449,22 +449,24 @@ using LaunchFn = int (*)(const paam_batch *, const AnalysisParams &, int64_t *, 
                          const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
 
 struct Variant {
-    int G, maxn;
+    int impl, G, maxn;
     LaunchFn fn;
 };
 
-// Every (group width, table size) this build instantiates.
+// Every (family, group width, table size) this build instantiates.
 const Variant kVariants[] = {
-    {1, 16, launch_fast<1, 16>},   {2, 16, launch_fast<2, 16>},   {4, 16, launch_fast<4, 16>},
-    {8, 16, launch_fast<8, 16>},   {2, 32, launch_fast<2, 32>},   {4, 32, launch_fast<4, 32>},
-    {8, 32, launch_fast<8, 32>},   {16, 32, launch_fast<16, 32>}, {4, 64, launch_fast<4, 64>},
-    {8, 64, launch_fast<8, 64>},   {16, 64, launch_fast<16, 64>}, {32, 64, launch_fast<32, 64>},
+    {0, 1, 16, launch_fast<1, 16>},   {0, 2, 16, launch_fast<2, 16>},   {0, 4, 16, launch_fast<4, 16>},
+    {0, 8, 16, launch_fast<8, 16>},   {0, 2, 32, launch_fast<2, 32>},   {0, 4, 32, launch_fast<4, 32>},
+    {0, 8, 32, launch_fast<8, 32>},   {0, 16, 32, launch_fast<16, 32>}, {0, 4, 64, launch_fast<4, 64>},
+    {0, 8, 64, launch_fast<8, 64>},   {0, 16, 64, launch_fast<16, 64>}, {0, 32, 64, launch_fast<32, 64>},
+    {1, 4, 16, launch_reg<4, 4>},     {1, 8, 16, launch_reg<8, 2>},     {1, 16, 16, launch_reg<16, 1>},
+    {1, 16, 32, launch_reg<16, 2>},   {1, 32, 32, launch_reg<32, 1>},   {1, 32, 64, launch_reg<32, 2>},
 };
 
-LaunchFn find_variant(int G, int maxn)
+LaunchFn find_variant(int impl, int G, int maxn)
 {
     for (const Variant &v : kVariants)
-        if (v.G == G && v.maxn == maxn) return v.fn;
+        if (v.impl == impl && v.G == G && v.maxn == maxn) return v.fn;
     return nullptr;
 }
 
@@ -472,17 +474,17 @@ LaunchFn find_variant(int G, int maxn)
 
 // Candidate launch configurations the autotuner times (first = default).
 const LaunchCfg kLaunchCfgs[] = {
-    {4, 16, 16, 256}, {2, 16, 16, 256}, {8, 16, 16, 256}, {1, 16, 16, 128}, {4, 16, 16, 128},
-    {4, 32, 16, 256}, {8, 32, 16, 256}, {4, 16, 8, 256},  {4, 16, 32, 256}, {8, 32, 32, 256},
-    {16, 32, 16, 256}, {2, 32, 16, 128},
+    {1, 8, 16, 0, 16, 256},  {0, 8, 16, 0, 16, 256},  {0, 16, 32, 0, 16, 256}, {1, 16, 16, 0, 16, 256},
+    {1, 4, 16, 0, 16, 256},  {1, 16, 32, 1, 32, 256}, {1, 32, 32, 1, 32, 256}, {1, 8, 16, 1, 32, 256},
+    {0, 4, 16, 0, 16, 256},  {0, 8, 32, 0, 32, 256},  {1, 16, 32, 0, 16, 256}, {1, 4, 16, 1, 32, 128},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
 
 int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const LaunchCfg &cfg, int64_t *R,
                           uint8_t *status, uint8_t *verdict, cudaStream_t stream, int *n_kernels)
 {
-    LaunchFn small = find_variant(cfg.g_small, cfg.maxn_small);
-    LaunchFn bigfn = find_variant(cfg.g_big, 64);
+    LaunchFn small = find_variant(cfg.impl_small, cfg.g_small, cfg.maxn_small);
+    LaunchFn bigfn = find_variant(cfg.impl_big, cfg.g_big, 64);
     if (!small || !bigfn) return PAAM_E_INVAL;
     int k = 0;
     PAAM_CUDA_TRY(cudaMemsetAsync(b->counts, 0, 2 * sizeof(int32_t), stream));

@@ -1,0 +1,494 @@
+// analyze_reg.cu -- register-resident variant of the fast analysis path.
+//
+// Same mathematics and the same 32-bit bound as analyze_fast.cu (see there):
+// arrival counts ceil(t / T) + 1 of Lemma 1 by exact multiply-shift division,
+// interferer sets as bitmasks, the exact skip of Lemma 2's per-segment sum
+// when it cannot beat Eq. 4 at R = D, and the chain recurrences of Theorem 1
+// in an order where every needed H*_h is final.
+//
+// Layout: a group of G lanes owns one system and each lane owns CPL of its
+// chains (chain j lives in lane j % G, slot j / G), held in registers.  Chain
+// relations (hp, hpp, hps, lower-priority same-executor, bucket rank, order)
+// come from O(n) broadcasts of each chain's keys.  Fixed points iterate with
+// every lane adding the terms of its own chains for the chain under analysis;
+// the group combines them with shuffles.  Shared memory only holds each
+// chain's own recurrence terms, read by the whole group as broadcasts.
+#include "internal.cuh"
+
+namespace {
+
+constexpr uint64_t kFitR = 1ull << 30;
+constexpr uint32_t kInfR = 0xFFFFFFFFu;
+
+template <int NMAX>
+struct RegMask {
+    using type = typename std::conditional<(NMAX <= 32), uint32_t, uint64_t>::type;
+};
+
+template <int NMAX>
+struct OwnSmem {
+    using Mask = typename RegMask<NMAX>::type;
+    Mask hp[NMAX], hpp[NMAX], hps[NMAX];
+    uint4 rec[NMAX];  // {D, base = B + E, own = S* + delta blk (capped at D + 1), deps = delta eps}
+    uint4 seg[NMAX];  // {Hseg, limit, blk, delta}
+    uint32_t seg0[NMAX];
+    uint8_t order[NMAX];
+};
+
+// Narrow systems (every deadline below 2^27 - 64) sum per-lane partials capped
+// at 2^27 - 1 in 32 bits (at most 32 lanes: no wrap-around).  A capped partial
+// already exceeds every deadline, so the capped sum decides each comparison
+// with D, and each minimum with a per-segment sum <= D, as the true sum would.
+constexpr uint32_t kNarrow = 1u << 27;
+
+template <int G>
+__device__ __forceinline__ unsigned rgroup_mask()
+{
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        const unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+}
+
+template <int G, typename V>
+__device__ __forceinline__ V rsum(V v, unsigned mask)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off, G);
+    return v;
+}
+
+template <int G, typename V>
+__device__ __forceinline__ V ror(V v, unsigned mask)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v |= __shfl_xor_sync(mask, v, off, G);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ unsigned rand_(unsigned v, unsigned mask)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v &= __shfl_xor_sync(mask, v, off, G);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ uint64_t gsum(uint64_t v, bool narrow, unsigned mask)
+{
+    if (narrow) {
+        uint32_t x = v < kNarrow - 1 ? (uint32_t)v : kNarrow - 1;
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) x += __shfl_xor_sync(mask, x, off, G);
+        return x;
+    }
+    return rsum<G>(v, mask);
+}
+
+template <int G>
+__device__ __forceinline__ uint32_t rmax(uint32_t v, unsigned mask)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(mask, v, off, G));
+    return v;
+}
+
+// value of slot t / G held by lane t % G, broadcast to the group
+template <int G, int CPL, typename V>
+__device__ __forceinline__ V bcast(const V (&a)[CPL], int t, unsigned mask)
+{
+    const int k = t / G;
+    V v = a[0];
+#pragma unroll
+    for (int i = 1; i < CPL; ++i)
+        if (k == i) v = a[i];
+    return __shfl_sync(mask, v, t % G, G);
+}
+
+template <typename Mask>
+__device__ __forceinline__ int rpopc(Mask m)
+{
+    if constexpr (sizeof(Mask) == 8)
+        return __popcll(m);
+    else
+        return __popc(m);
+}
+
+template <typename Mask>
+__device__ __forceinline__ int rlowest(Mask m)
+{
+    if constexpr (sizeof(Mask) == 8)
+        return __ffsll((long long)m) - 1;
+    else
+        return __ffs((int)m) - 1;
+}
+
+// Lemma 1 (Eq. 2): ceil(t / T) + 1 for t, T < 2^30 (magic m, shift sh; see analyze_fast.cu)
+__device__ __forceinline__ uint32_t rarrivals(uint32_t t, uint32_t tm1, uint32_t m, uint32_t sh)
+{
+    return (uint32_t)(((uint64_t)(t + tm1) * m) >> sh) + 1u;
+}
+
+template <int G, int CPL>
+__device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t sys, OwnSmem<G * CPL> &s,
+                           int lane, unsigned gm, int64_t *__restrict__ R_out, uint8_t *__restrict__ st_out,
+                           uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
+                           int32_t *wide_list, int32_t *wide_count)
+{
+    constexpr int NMAX = G * CPL;
+    using Mask = typename RegMask<NMAX>::type;
+    const int64_t c0 = b.sys_chain_off[sys];
+    const int n = (int)(b.sys_chain_off[sys + 1] - c0);
+    if (n > NMAX) {
+        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)sys;
+        return;
+    }
+    const int64_t x0 = b.sys_exec_off[sys];
+    const uint64_t kappa2 = 2 * (uint64_t)p.kappa, eps = (uint64_t)p.eps;
+    const int64_t seg_base = n > 0 ? b.cb_seg_off[b.chain_cb_off[c0]] : 0;
+
+    // ---- per-chain aggregates (Sec. II-C), one chain per slot ---------------
+    uint32_t tm1[CPL], mg[CPL], sh[CPL], Dv[CPL], Ev[CPL], Sv[CPL], Emx[CPL], Mv[CPL], Amn[CPL], dlv[CPL];
+    uint32_t seg0[CPL];
+    int32_t pr[CPL], ep[CPL], ex[CPL], co[CPL];
+    bool sp[CPL], val[CPL];
+    Mask users = 0, spins = 0;
+    unsigned fits = 1;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const int j = lane + G * k;
+        val[k] = j < n;
+        tm1[k] = mg[k] = sh[k] = Dv[k] = Ev[k] = Sv[k] = Emx[k] = Mv[k] = Amn[k] = dlv[k] = seg0[k] = 0;
+        pr[k] = ep[k] = INT32_MIN;
+        ex[k] = co[k] = -1 - j;
+        sp[k] = false;
+        if (!val[k]) continue;
+        const int64_t g = c0 + j;
+        const int64_t T = b.T[g], D = b.D[g];
+        const int x = b.exec[g];
+        pr[k] = b.prio[g];
+        ex[k] = x;
+        co[k] = b.exec_core[x0 + x];
+        ep[k] = b.exec_prio ? b.exec_prio[x0 + x] : INT32_MIN;
+        sp[k] = b.spin[g] != 0;
+        const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
+        uint64_t E = 0, Emax = 0, S = 0, M = 0, Amin = ~0ull;
+        for (int64_t cb = cb0; cb < cb1; ++cb) {
+            const uint64_t e = (uint64_t)b.E[cb];
+            E += e;
+            Emax = e > Emax ? e : Emax;
+        }
+        const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
+        for (int64_t q = q0; q < q1; ++q) {
+            const uint64_t a = (uint64_t)b.A[q] + kappa2; // A* = A + 2 kappa
+            S += a;
+            M = a > M ? a : M;
+            Amin = a < Amin ? a : Amin;
+        }
+        const uint64_t dl = (uint64_t)(q1 - q0);
+        const bool fit = (uint64_t)T < kFitR && (uint64_t)D < kFitR && E < kFitR && S < kFitR && dl < kFitR &&
+                         (eps == 0 || dl <= (kFitR - 1) / eps);
+        fits &= fit ? 1u : 0u;
+        if (fit) {
+            const uint32_t Tu = (uint32_t)T;
+            const uint32_t l = Tu > 1 ? 32u - (uint32_t)__clz(Tu - 1u) : 0u;
+            mg[k] = (uint32_t)(((1ull << (31 + l)) + Tu - 1u) / Tu);
+            sh[k] = 31 + l;
+            tm1[k] = Tu - 1u;
+        }
+        Dv[k] = (uint32_t)D;
+        Ev[k] = (uint32_t)E;
+        Sv[k] = (uint32_t)S;
+        Emx[k] = (uint32_t)Emax;
+        Mv[k] = (uint32_t)M;
+        Amn[k] = dl ? (uint32_t)(Amin < kFitR ? Amin : 0) : 0;
+        dlv[k] = (uint32_t)dl;
+        seg0[k] = (uint32_t)(q0 - seg_base);
+        users |= dl ? (Mask)1 << j : 0;
+        spins |= sp[k] ? (Mask)1 << j : 0;
+    }
+    fits = rand_<G>(fits, gm);
+    users = ror<G>(users, gm);
+    spins = ror<G>(spins, gm);
+    uint32_t dmax = 0;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) dmax = Dv[k] > dmax ? Dv[k] : dmax;
+    const bool narrow = rmax<G>(dmax, gm) < kNarrow - G * CPL;
+    if (!fits) {
+        if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)sys;
+        return;
+    }
+    if (!b.exec_prio) { // criticality-as-priority: highest chain priority on the executor
+        int32_t best[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) best[k] = INT32_MIN;
+        for (int t = 0; t < n; ++t) {
+            const int32_t pt = bcast<G, CPL>(pr, t, gm), xt = bcast<G, CPL>(ex, t, gm);
+#pragma unroll
+            for (int k = 0; k < CPL; ++k)
+                if (xt == ex[k] && pt > best[k]) best[k] = pt;
+        }
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) ep[k] = best[k];
+    }
+
+    // ---- relations, analysis order, CPU blocking (Lemma 4) -------------------
+    Mask higher[CPL], samex[CPL], hppm[CPL];
+    int pos[CPL], rank[CPL];
+    uint32_t Bv[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        higher[k] = samex[k] = hppm[k] = 0;
+        pos[k] = rank[k] = 0;
+        Bv[k] = 0;
+    }
+    for (int t = 0; t < n; ++t) {
+        const int32_t pt = bcast<G, CPL>(pr, t, gm), xt = bcast<G, CPL>(ex, t, gm);
+        const int32_t kt = bcast<G, CPL>(co, t, gm), et = bcast<G, CPL>(ep, t, gm);
+        const uint32_t emt = bcast<G, CPL>(Emx, t, gm);
+        const bool ut = (users >> t) & 1;
+        const Mask bit = (Mask)1 << t;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const bool hi = pt > pr[k];
+            const bool sx = xt == ex[k];
+            higher[k] |= hi ? bit : 0;
+            samex[k] |= sx ? bit : 0;
+            hppm[k] |= (!sx && kt == co[k] && et > ep[k]) ? bit : 0; // hpp, Lemma 4
+            pos[k] += (et > ep[k]) || (et == ep[k] && hi);           // executor, then chain priority
+            rank[k] += (ut && hi) ? 1 : 0;
+            if (sx && pt < pr[k] && emt > Bv[k]) Bv[k] = emt; // one LP callback on the executor
+        }
+    }
+    const int n_users = rpopc(users);
+    int32_t bucket[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) // bucket = floor(rank * n_buckets / |U|) (R2)
+        bucket[k] = (val[k] && dlv[k]) ? (int32_t)((uint32_t)rank[k] * (uint32_t)p.n_buckets / (uint32_t)n_users)
+                                       : -1;
+
+    // ---- same-bucket blocking (R2-R3) and the Lemma 2 skip test -------------
+    uint32_t blk[CPL];
+    uint64_t hchd[CPL], sums[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        blk[k] = 0;
+        hchd[k] = sums[k] = 0;
+    }
+    for (int t = 0; t < n; ++t) {
+        const uint32_t mt = bcast<G, CPL>(Mv, t, gm);
+        const int32_t bt = bcast<G, CPL>(bucket, t, gm);
+        const uint32_t tmt = bcast<G, CPL>(tm1, t, gm), mgt = bcast<G, CPL>(mg, t, gm);
+        const uint32_t sht = bcast<G, CPL>(sh, t, gm), st = bcast<G, CPL>(Sv, t, gm);
+        const bool ut = (users >> t) & 1;
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const bool act = bucket[k] >= 0 && ut;
+            const bool hi = (higher[k] >> t) & 1;
+            const bool same = act && !hi && t != lane + G * k && bt == bucket[k];
+            blk[k] = (same && mt > blk[k]) ? mt : blk[k];
+            const uint32_t sv = (act && hi) ? st : 0u;
+            hchd[k] += (uint64_t)rarrivals(Dv[k], tmt, mgt, sht) * sv;
+            sums[k] += sv;
+        }
+    }
+
+    // ---- own recurrence terms to shared memory ------------------------------
+    Mask need_exact = 0;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        if (!val[k]) continue;
+        const int j = lane + G * k;
+        const uint64_t dl = dlv[k];
+        const uint64_t own = (uint64_t)Sv[k] + dl * blk[k];
+        const uint64_t cap = (uint64_t)Dv[k] + 1; // values above D act the same as D + 1
+        s.hp[j] = higher[k] & samex[k];
+        s.hpp[j] = hppm[k];
+        s.hps[j] = higher[k] & users;
+        s.rec[j] = make_uint4(Dv[k], Bv[k] + Ev[k], (uint32_t)(own < cap ? own : cap), (uint32_t)(dl * eps));
+        const uint64_t lim = own + hchd[k];
+        s.seg[j] = make_uint4(kInfR, (uint32_t)(lim < cap ? lim : cap), blk[k], (uint32_t)dl);
+        s.seg0[j] = seg0[k];
+        s.order[pos[k]] = (uint8_t)j;
+        // Lemma 2's sum is at least sum_j (x_j + f sum_h S_h), x_j = A*_j + blk, f = 2 if x_j >= 1;
+        // Eq. 4 is at most own + sum_h mu_h(D) S_h for every R <= D.  Exact sum only if it can win.
+        const uint64_t f = ((uint64_t)Amn[k] + blk[k]) >= 1 ? 2 : 1;
+        if (dl && f * dl * sums[k] < hchd[k]) need_exact |= (Mask)1 << j;
+    }
+    need_exact = ror<G>(need_exact, gm);
+    __syncwarp(gm);
+
+    // ---- exact per-segment fixed points (Lemma 2), chains one at a time ------
+    for (Mask nm = need_exact; nm; nm &= nm - 1) {
+        const int c = rlowest(nm);
+        const Mask hps = s.hps[c];
+        const uint4 sg = s.seg[c];
+        const uint32_t Dc = s.rec[c].x, lim = sg.y, blkc = sg.z, dl = sg.w;
+        uint32_t acoef[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) acoef[k] = ((hps >> (lane + G * k)) & 1) ? Sv[k] : 0u;
+        uint64_t Hsum = 0;
+        bool inf = false;
+        for (uint32_t q = 0; q < dl && !inf; ++q) {
+            const uint64_t base = (uint64_t)b.A[seg_base + s.seg0[c] + q] + kappa2 + blkc;
+            uint64_t h = base; // the recurrence starts with the first two terms
+            for (;;) {
+                if (h > Dc || Hsum + h >= lim) {
+                    inf = true;
+                    break;
+                }
+                uint64_t part = 0;
+#pragma unroll
+                for (int k = 0; k < CPL; ++k)
+                    part += (uint64_t)rarrivals((uint32_t)h, tm1[k], mg[k], sh[k]) * acoef[k];
+                const uint64_t nh = base + gsum<G>(part, narrow, gm);
+                if (nh == h) break; // strictly increasing until here, bounded by D
+                h = nh;
+            }
+            Hsum += h;
+        }
+        if (lane == 0 && !inf) s.seg[c].x = (uint32_t)Hsum;
+        __syncwarp(gm);
+    }
+
+    // ---- Theorem 1 (Eq. 6), chain by chain ----------------------------------
+    uint32_t Ehp[CPL], Ehpp[CPL], Rv[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        Ehp[k] = Ev[k];
+        Ehpp[k] = Ev[k] + (sp[k] ? 0u : (uint32_t)((uint64_t)dlv[k] * eps));
+        Rv[k] = 0;
+    }
+    Mask sched = 0, dep = 0;
+    for (int step = 0; step < n; ++step) {
+        const int c = s.order[step];
+        const Mask hp = s.hp[c], hpp = s.hpp[c], hps = s.hps[c];
+        const Mask cbit = (Mask)1 << c;
+        if ((hp | (hpp & spins)) & ~sched) { // a needed H*_h is not available
+            dep |= cbit;
+            continue;
+        }
+        uint32_t ccoef[CPL], acoef[CPL];
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const int j = lane + G * k;
+            ccoef[k] = ((hp >> j) & 1) ? Ehp[k] : (((hpp >> j) & 1) ? Ehpp[k] : 0u);
+            acoef[k] = ((hps >> j) & 1) ? Sv[k] : 0u;
+        }
+        const uint4 rc = s.rec[c], sg = s.seg[c];
+        const uint64_t Dc = rc.x, base = rc.y, own = rc.z, deps = rc.w, dl = sg.w;
+        const uint64_t Hseg = sg.x == kInfR ? ~0ull : (uint64_t)sg.x;
+        // start: B + E + H* with the interference part of Eq. 4 empty
+        uint64_t R = base + (dl ? (Hseg < own ? Hseg : own) + deps : 0);
+        uint64_t hs = 0;
+        bool ok = false;
+        while (R <= Dc) {
+            uint64_t cpu = 0, acc = 0;
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                const uint64_t mu = rarrivals((uint32_t)R, tm1[k], mg[k], sh[k]);
+                cpu += mu * ccoef[k];
+                acc += mu * acoef[k];
+            }
+            cpu = gsum<G>(cpu, narrow, gm);
+            acc = gsum<G>(acc, narrow, gm);
+            hs = 0;
+            if (dl) {
+                const uint64_t hch = own + acc; // Eq. 4
+                hs = (Hseg < hch ? Hseg : hch) + deps; // Eq. 1 with min(Eq. 3, Eq. 4)
+            }
+            const uint64_t Rn = base + hs + cpu;
+            if (Rn == R) {
+                ok = true;
+                break;
+            }
+            R = Rn;
+        }
+        if (ok) {
+            sched |= cbit;
+#pragma unroll
+            for (int k = 0; k < CPL; ++k)
+                if (lane + G * k == c) {
+                    Rv[k] = (uint32_t)R;
+                    Ehp[k] = Ev[k] + (uint32_t)hs;
+                    if (sp[k]) Ehpp[k] = Ev[k] + (uint32_t)hs;
+                }
+        }
+    }
+
+    // ---- outputs --------------------------------------------------------------
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        if (!val[k]) continue;
+        const int j = lane + G * k;
+        const bool ok = (sched >> j) & 1;
+        R_out[c0 + j] = ok ? (int64_t)Rv[k] : -1;
+        st_out[c0 + j] = ok ? PAAM_ST_SCHED : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN);
+    }
+    if (lane == 0 && verdict) {
+        const Mask all = n >= (int)(8 * sizeof(Mask)) ? ~(Mask)0 : (((Mask)1 << n) - 1);
+        verdict[sys] = sched == all ? 1 : 0;
+    }
+    __syncwarp(gm);
+}
+
+template <int G, int CPL>
+__global__ void __launch_bounds__(256) analyze_reg_kernel(BatchDev b, AnalysisParams p, int64_t *R, uint8_t *st,
+                                                          uint8_t *verdict, const int32_t *list,
+                                                          const int32_t *count, int32_t *big_list,
+                                                          int32_t *big_count, int32_t *wide_list,
+                                                          int32_t *wide_count)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int groups = blockDim.x / G;
+    const int grp = threadIdx.x / G;
+    const int lane = threadIdx.x % G;
+    OwnSmem<G * CPL> &s = reinterpret_cast<OwnSmem<G * CPL> *>(smem_raw)[grp];
+    const unsigned gm = rgroup_mask<G>();
+    const int64_t n_items = list ? (int64_t)*count : b.n_sys;
+    for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n_items; i += (int64_t)gridDim.x * groups) {
+        const int64_t sys = list ? (int64_t)list[i] : i;
+        reg_system<G, CPL>(b, p, sys, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
+    }
+}
+
+} // namespace
+
+template <int G, int CPL>
+int launch_reg(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+               const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream)
+{
+    if (threads % 32 != 0 || threads > 256) return PAAM_E_INVAL;
+    const int groups = threads / G;
+    const size_t smem = sizeof(OwnSmem<G * CPL>) * groups;
+    auto kern = analyze_reg_kernel<G, CPL>;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (max_items + groups - 1) / groups;
+    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, list, count, bt->list_big,
+                                                      bt->counts, bt->list_wide, bt->counts + 1);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    return PAAM_OK;
+}
+
+// instantiations used by the launch table (analyze_fast.cu)
+template int launch_reg<8, 2>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                              const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_reg<16, 1>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                               const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_reg<4, 4>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                              const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_reg<16, 2>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                               const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_reg<32, 1>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                               const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_reg<32, 2>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                               const int32_t *, const int32_t *, int64_t, int, cudaStream_t);

@@ -107,11 +107,18 @@ inline BatchDev batch_dev(const paam_batch *b)
     return d;
 }
 
-// A launch configuration of the analysis: group width and table size of the
-// first pass, group width of the pass over systems with more chains, CTA size.
+// A launch configuration of the analysis: kernel family (0 = shared-memory
+// tables, analyze_fast.cu; 1 = register tables, analyze_reg.cu), group width
+// and chain-table size of the first pass, family and group width of the pass
+// over systems with more chains (table size 64), CTA size.
 struct LaunchCfg {
-    int g_small, maxn_small, g_big, threads;
+    int impl_small, g_small, maxn_small, impl_big, g_big, threads;
 };
+
+// Register-table kernels (analyze_reg.cu): G lanes per system, CPL chains per lane.
+template <int G, int CPL>
+int launch_reg(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+               const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
 extern const LaunchCfg kLaunchCfgs[];
 extern const int kNumLaunchCfgs;
 
