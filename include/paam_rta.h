@@ -190,6 +190,38 @@ int paam_rta_set_launch_config(paam_batch *batch, int index); /* PAAM_E_INVAL if
 int paam_rta_get_launch_config(const paam_batch *batch);
 
 /*
+ * Allocation-free analysis.  (The paper has no counterpart: this entry point
+ * exists for callers of this library that cannot allocate memory at the time
+ * they need an admission test -- a real-time executor whose control loop
+ * forbids allocation after start-up, a host that has handed its whole device
+ * memory to another allocator, or an integration that must account for all
+ * of its memory before it runs.)
+ *
+ * Same results as paam_rta_load_systems + paam_rta_analyze_batch, but the
+ * call needs no context and allocates nothing: `view` must hold DEVICE
+ * pointers (is_device = 1) to the caller's tables, R / status / verdict are
+ * the caller's device outputs, and the bookkeeping the analysis needs lives in
+ * one fixed device array of the library (PAAM_NOALLOC_MAX_SYS * 8 + 96 bytes,
+ * about 512 KiB), present on every GPU that loads the library until the
+ * process exits.
+ *
+ *   - n_sys above PAAM_NOALLOC_MAX_SYS is rejected with PAAM_E_RANGE (split
+ *     larger batches into several calls);
+ *   - the input is validated exactly as paam_rta_load_systems does, so the
+ *     call synchronises `stream` once (after validation) and returns the
+ *     same error codes; the analysis itself is then enqueued on `stream`;
+ *   - the first call on a device (the current device) looks up the array's
+ *     device address; make that first call before any stream capture;
+ *   - every call shares the array and it keeps the last call's contents
+ *     (each call resets the parts that must start at zero): calls whose work
+ *     overlaps on the GPU -- other streams, other host threads -- race and
+ *     must be serialised by the caller.
+ */
+#define PAAM_NOALLOC_MAX_SYS 65536
+int paam_rta_analyze_noalloc(const paam_systems_view *view, const paam_analysis_opts *opts, int64_t *R,
+                             uint8_t *status, uint8_t *verdict, void *stream);
+
+/*
  * Diagnostics: number of CUDA kernels this library has launched in this
  * process (all contexts).  Not part of the paper; used to report how many
  * of the library's own kernels ran inside a timed region.

@@ -71,6 +71,8 @@ def lib():
                                                  _c_void_p, ctypes.c_int]),
             "paam_rta_set_launch_config": (ctypes.c_int, [_c_void_p, ctypes.c_int]),
             "paam_rta_get_launch_config": (ctypes.c_int, [_c_void_p]),
+            "paam_rta_analyze_noalloc": (ctypes.c_int, [P(SystemsView), P(AnalysisOpts), _c_void_p, _c_void_p,
+                                                        _c_void_p, _c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -84,7 +86,7 @@ def exported_symbols() -> list:
     return ["paam_create", "paam_destroy", "paam_strerror", "paam_rta_load_systems", "paam_batch_n_sys",
             "paam_batch_n_chain", "paam_batch_free", "paam_rta_analyze_batch", "paam_launch_count",
             "paam_rta_num_launch_configs", "paam_rta_autotune", "paam_rta_set_launch_config",
-            "paam_rta_get_launch_config"]
+            "paam_rta_get_launch_config", "paam_rta_analyze_noalloc"]
 
 
 def launch_count() -> int:
@@ -241,3 +243,15 @@ def paam_rta_set_launch_config(batch: Batch, index: int):
 
 def paam_rta_get_launch_config(batch: Batch) -> int:
     return int(lib().paam_rta_get_launch_config(batch.handle))
+
+
+PAAM_NOALLOC_MAX_SYS = 65536
+
+
+def paam_rta_analyze_noalloc(sy, opts: AnalysisOpts, R, status, verdict=None, stream=None):
+    """Allocation-free analysis of device-resident tables ``sy`` (attributes
+    named as in the header, torch CUDA tensors) into caller-owned outputs."""
+    v, keep = make_view(sy, True)
+    _check(lib().paam_rta_analyze_noalloc(ctypes.byref(v), ctypes.byref(opts), _ptr(R), _ptr(status),
+                                          _ptr(verdict), _stream_ptr(stream)), "paam_rta_analyze_noalloc")
+    del keep

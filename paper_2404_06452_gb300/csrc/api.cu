@@ -241,6 +241,28 @@ __global__ void validate_kernel(ValidateArgs a)
 
 }
 
+int paam_launch_validate(const paam_batch *b, const int32_t *acc, int32_t *err, unsigned long long *stats,
+                         cudaStream_t stream)
+{
+    ValidateArgs a;
+    a.b = batch_dev(b);
+    a.n_chain = b->n_chain;
+    a.n_cb = b->n_cb;
+    a.n_seg = b->n_seg;
+    a.n_exec = b->n_exec;
+    a.acc = acc;
+    a.err = err;
+    a.stats = stats;
+    const int threads = 256;
+    int64_t blocks = (b->n_sys + threads - 1) / threads;
+    if (blocks > 16 * (int64_t)b->ctx->n_sm) blocks = 16 * (int64_t)b->ctx->n_sm;
+    if (blocks < 1) blocks = 1;
+    validate_kernel<<<(unsigned)blocks, threads, 0, stream>>>(a);
+    paam_count_launch();
+    PAAM_CUDA_TRY(cudaGetLastError());
+    return PAAM_OK;
+}
+
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 extern "C" int64_t paam_batch_n_sys(const paam_batch *b) { return b ? b->n_sys : 0; }
@@ -343,21 +365,7 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
         if (cudaMemcpyAsync(ctx->d_err, h_err, sizeof(h_err), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemsetAsync(ctx->d_stats, 0, ST_COUNT * sizeof(unsigned long long), stream) != cudaSuccess)
             rc = PAAM_E_CUDA;
-        ValidateArgs a;
-        a.b = batch_dev(b);
-        a.n_chain = b->n_chain;
-        a.n_cb = b->n_cb;
-        a.n_seg = b->n_seg;
-        a.n_exec = b->n_exec;
-        a.acc = acc_dev;
-        a.err = ctx->d_err;
-        a.stats = ctx->d_stats;
-        const int threads = 256;
-        int64_t blocks = (b->n_sys + threads - 1) / threads;
-        if (blocks > 16 * (int64_t)ctx->n_sm) blocks = 16 * (int64_t)ctx->n_sm;
-        validate_kernel<<<(unsigned)blocks, threads, 0, stream>>>(a);
-        paam_count_launch();
-        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        if (paam_launch_validate(b, acc_dev, ctx->d_err, ctx->d_stats, stream) != PAAM_OK) rc = PAAM_E_CUDA;
         if (rc == PAAM_OK &&
             (cudaMemcpyAsync(h_err, ctx->d_err, sizeof(h_err), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
              cudaMemcpyAsync(b->stats, ctx->d_stats, sizeof(b->stats), cudaMemcpyDeviceToHost, stream) !=

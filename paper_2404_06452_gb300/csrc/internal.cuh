@@ -127,6 +127,11 @@ extern const int kNumLaunchCfgs;
 int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const LaunchCfg &cfg, int64_t *R,
                           uint8_t *status, uint8_t *verdict, cudaStream_t stream, int *n_kernels);
 
+// Validation kernel (api.cu): err = {code, first bad system, max chains, max
+// executors} (initialise to {0, INT32_MAX, 0, 0}), stats = ST_* maxima (zeroed).
+int paam_launch_validate(const paam_batch *b, const int32_t *acc, int32_t *err, unsigned long long *stats,
+                         cudaStream_t stream);
+
 // Exact int64 kernel (analyze_wide.cu) over list[0 .. *count) or, with
 // list == nullptr, over every system.
 int paam_launch_wide(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st,
