@@ -171,6 +171,36 @@ int paam_rta_analyze_batch(paam_ctx *ctx, const paam_batch *batch, const paam_an
                            int64_t *R, uint8_t *status, uint8_t *verdict, void *stream);
 
 /*
+ * Exact priority-assignment search.  The paper fixes chain priorities by
+ * criticality (CAPA, Sec. II-C); this call evaluates K candidate chain
+ * priority orders per system with the same exact analysis and reports which
+ * ones pass the admission test (every chain schedulable, Sec. IV-A).
+ *
+ *   ranks[n_sys][K][nmax]  device int16: ranks[s][k][c] is the rank of chain c
+ *                          (local index) of system s in candidate k, 0 =
+ *                          highest priority; each row's first n_s entries
+ *                          must be a permutation of 0..n_s-1 (entries past
+ *                          n_s are ignored); nmax >= the batch's largest chain
+ *                          count.  Executor priorities follow the candidate
+ *                          (highest chain priority on the executor).
+ *   stop_at_first          0: analyse every candidate; 1: candidates above the
+ *                          best schedulable one found for a system may be
+ *                          skipped (their cand_ok entry then reads 0).
+ *   cand_ok[n_sys * K]     device, optional: 1 where candidate k of system s
+ *                          (index s * K + k) is schedulable.
+ *   first_ok[n_sys]        device: smallest schedulable k, or -1.
+ *
+ * The result does not depend on the launch configuration or on the order in
+ * which candidates are processed.  The call synchronises `stream`.  Errors:
+ * PAAM_E_INVAL (a rank row that is not a permutation, bad sizes),
+ * PAAM_E_RANGE (n_sys * K above 2^31 - 1, eps/kappa above the cap),
+ * PAAM_E_UNSUPPORTED, PAAM_E_NOMEM, PAAM_E_CUDA.
+ */
+int paam_rta_search_priorities(paam_ctx *ctx, const paam_batch *batch, const paam_analysis_opts *opts,
+                               const int16_t *ranks, int32_t K, int32_t nmax, int32_t stop_at_first,
+                               uint8_t *cand_ok, int32_t *first_ok, void *stream);
+
+/*
  * Launch configurations.  The analysis has several built-in launch
  * configurations (lanes per system, chain-table size of the first pass, lanes
  * per system for systems with more chains, CTA size); every one produces

@@ -84,6 +84,11 @@ CONFIGS = {
                  cb_min=1, cb_max=12, x_min=2, x_max=8, util_lo=0.2, util_hi=0.95, p_acc=0.5),
     "cfg4": dict(_BASE, n_sys=10_000, seed=0x9AA40004, n_min=16, n_max=16, cb_min=2, cb_max=4,
                  x_min=2, x_max=2, util_lo=0.7, util_hi=0.7, p_acc=0.3),
+    # the search workload with its 16 chains spread over 16 single-executor cores and
+    # 0.05-1 ms segments: here some candidate orders pass the admission test
+    "cfg4s": dict(_BASE, n_sys=10_000, seed=0x9AA40014, n_min=16, n_max=16, cb_min=2, cb_max=4,
+                  x_min=16, x_max=16, exec_per_core=1, util_lo=0.7, util_hi=0.7, p_acc=0.3,
+                  a_min=50_000, a_max=1_000_000),
 }
 
 
@@ -298,6 +303,37 @@ def permutations(seed: int, n_of_sys: np.ndarray, K: int, nmax: int | None = Non
         out = np.zeros((S, K, nmax), np.int16)
     assert out.shape == (S, K, nmax) and out.dtype == np.int16 and out.flags.c_contiguous
     lib.paam_gen_perms(seed, 0, S, K, first_slot, _ptr(n_of_sys), nmax, _ptr(out))
+    return out
+
+
+def candidate_ranks(sy: Systems, K: int, seed: int, nmax: int | None = None) -> np.ndarray:
+    """Candidate chain priority orders for the priority-assignment search.
+
+    ``out[s, k, c]`` is the rank (0 = highest priority) of chain c of system s
+    in candidate k; entries past the system's chain count are -1.  Slot 0 is
+    the system's own order (its given priorities: criticality-as-priority),
+    slot 1 is deadline-monotonic (shorter deadline first, ties by chain index),
+    slots 2.. are seeded random permutations.
+    """
+    n = sy.chains_per_system().astype(np.int32)
+    S = sy.n_sys
+    nmax = int(nmax or (n.max() if S else 1))
+    out = np.full((S, K, nmax), -1, np.int16)
+    if K > 2:
+        permutations(seed, n, K, nmax, first_slot=2, out=out)
+    sysid = np.repeat(np.arange(S), n)
+    local = np.arange(sy.n_chain) - sy.sys_chain_off[sysid]
+
+    def ranks_by(keys):
+        order = np.lexsort(keys + (sysid,))  # within each system, ascending keys
+        r = np.empty(sy.n_chain, np.int64)
+        r[order] = np.arange(sy.n_chain) - sy.sys_chain_off[sysid[order]]
+        return r
+
+    if K > 0:
+        out[sysid, 0, local] = ranks_by((-sy.prio.astype(np.int64),))
+    if K > 1:
+        out[sysid, 1, local] = ranks_by((local, sy.D))
     return out
 
 

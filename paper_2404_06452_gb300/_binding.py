@@ -73,6 +73,9 @@ def lib():
             "paam_rta_get_launch_config": (ctypes.c_int, [_c_void_p]),
             "paam_rta_analyze_noalloc": (ctypes.c_int, [P(SystemsView), P(AnalysisOpts), _c_void_p, _c_void_p,
                                                         _c_void_p, _c_void_p]),
+            "paam_rta_search_priorities": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
+                                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                          _c_void_p, _c_void_p, _c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -86,7 +89,7 @@ def exported_symbols() -> list:
     return ["paam_create", "paam_destroy", "paam_strerror", "paam_rta_load_systems", "paam_batch_n_sys",
             "paam_batch_n_chain", "paam_batch_free", "paam_rta_analyze_batch", "paam_launch_count",
             "paam_rta_num_launch_configs", "paam_rta_autotune", "paam_rta_set_launch_config",
-            "paam_rta_get_launch_config", "paam_rta_analyze_noalloc"]
+            "paam_rta_get_launch_config", "paam_rta_analyze_noalloc", "paam_rta_search_priorities"]
 
 
 def launch_count() -> int:
@@ -255,3 +258,13 @@ def paam_rta_analyze_noalloc(sy, opts: AnalysisOpts, R, status, verdict=None, st
     _check(lib().paam_rta_analyze_noalloc(ctypes.byref(v), ctypes.byref(opts), _ptr(R), _ptr(status),
                                           _ptr(verdict), _stream_ptr(stream)), "paam_rta_analyze_noalloc")
     del keep
+
+
+def paam_rta_search_priorities(ctx: Context, batch: Batch, opts: AnalysisOpts, ranks, stop_at_first: bool,
+                               cand_ok, first_ok, stream=None):
+    """Exact search over candidate rank orders ``ranks`` ([S, K, nmax] int16,
+    device tensor); fills ``first_ok`` [S] and optionally ``cand_ok`` [S, K]."""
+    S, K, nmax = ranks.shape
+    _check(lib().paam_rta_search_priorities(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(ranks), int(K),
+                                            int(nmax), 1 if stop_at_first else 0, _ptr(cand_ok), _ptr(first_ok),
+                                            _stream_ptr(stream)), "paam_rta_search_priorities")

@@ -38,3 +38,18 @@ def analyze(ctx: B.Context, batch: B.Batch, n_buckets: int = 1, eps: int = 0, ka
     v = torch.empty(batch.n_sys, dtype=torch.uint8, device=dev)
     B.paam_rta_analyze_batch(ctx, batch, B.analysis_opts(n_buckets, eps, kappa), R, st, v, stream=stream)
     return R, st, v
+
+
+def search(ctx: B.Context, batch: B.Batch, ranks, n_buckets: int = 1, eps: int = 0, kappa: int = 0,
+           stop_at_first: bool = False, want_cand_ok: bool = True, stream=None):
+    """Run ``paam_rta_search_priorities`` on device rank rows; returns torch
+    tensors (first_ok [S], cand_ok [S, K] or None)."""
+    import torch
+
+    dev = torch.device("cuda", ctx.device)
+    S, K, _ = ranks.shape
+    first_ok = torch.empty(S, dtype=torch.int32, device=dev)
+    cand_ok = torch.empty((S, K), dtype=torch.uint8, device=dev) if want_cand_ok else None
+    B.paam_rta_search_priorities(ctx, batch, B.analysis_opts(n_buckets, eps, kappa), ranks, stop_at_first,
+                                 cand_ok, first_ok, stream=stream)
+    return first_ok, cand_ok

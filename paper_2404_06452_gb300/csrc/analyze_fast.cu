@@ -106,6 +106,21 @@ __device__ __forceinline__ int lowest(Mask m)
         return __ffs((int)m) - 1;
 }
 
+// warp lane of the first lane of this thread's group
+template <int G>
+__device__ __forceinline__ int lane_base_of()
+{
+    return (int)(threadIdx.x & 31u) & ~(G - 1);
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_and(unsigned v, unsigned mask)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v &= __shfl_xor_sync(mask, v, off);
+    return v;
+}
+
 // bits h with h = lane (mod G)
 template <int G, typename Mask>
 __device__ __forceinline__ Mask lane_bits(int lane)
@@ -124,33 +139,52 @@ __device__ __forceinline__ uint32_t arrivals(uint32_t t, uint2 tm, uint32_t sh)
 }
 
 template <int G, int MAXN>
-__device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t sys, FastSmem<MAXN> &s,
+__device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t item, FastSmem<MAXN> &s,
                             int lane, unsigned gmask, int64_t *__restrict__ R_out,
                             uint8_t *__restrict__ st_out, uint8_t *__restrict__ verdict,
                             int32_t *big_list, int32_t *big_count, int32_t *wide_list,
                             int32_t *wide_count)
 {
     using Mask = typename MaskOf<MAXN>::type;
+    int64_t sys;
+    int32_t cand;
+    item_of(p, item, sys, cand);
+    if (p.K > 0 && p.early) { // candidate above the best schedulable one found so far
+        const int pruned = __shfl_sync(gmask, cand_pruned(p, sys, cand) ? 1 : 0, lane_base_of<G>());
+        if (pruned) return;
+    }
     const int64_t c0 = b.sys_chain_off[sys];
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
     if (n > MAXN) { // a wider configuration takes it
-        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)sys;
+        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
         return;
     }
+    const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.K + cand) * p.nmax : nullptr;
+    const int32_t *xprio = p.K > 0 ? nullptr : b.exec_prio; // candidates: criticality-as-priority
     const int64_t x0 = b.sys_exec_off[sys];
     const uint64_t kappa2 = 2 * (uint64_t)p.kappa, eps = (uint64_t)p.eps;
     const int64_t seg_base = n > 0 ? b.cb_seg_off[b.chain_cb_off[c0]] : 0;
 
     // ---- per-chain aggregates (Sec. II-C) and division magics ---------------
     int fits = 1;
-    Mask users = 0, spins = 0;
+    unsigned rank_ok = 1;
+    Mask users = 0, spins = 0, rbits = 0;
     for (int c = lane; c < n; c += G) {
         const int64_t g = c0 + c;
         const int64_t T = b.T[g], D = b.D[g];
         const int x = b.exec[g];
         const uint8_t sp = b.spin[g];
         s.spin[c] = sp;
-        s.pe[c] = make_int2(b.prio[g], b.exec_prio ? b.exec_prio[x0 + x] : 0);
+        int32_t pc;
+        if (rank_row) { // candidate priority order: rank 0 is the highest priority
+            const int r = rank_row[c];
+            rank_ok &= (r >= 0 && r < n) ? 1u : 0u;
+            rbits |= (r >= 0 && r < n) ? (Mask)1 << r : 0;
+            pc = n - 1 - r;
+        } else {
+            pc = b.prio[g];
+        }
+        s.pe[c] = make_int2(pc, xprio ? xprio[x0 + x] : 0);
         s.xk[c] = make_int2(x, b.exec_core[x0 + x]);
         const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
         uint64_t E = 0, Emax = 0, S = 0, M = 0, Amin = ~0ull;
@@ -189,16 +223,29 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         users |= (Mask)(dl > 0 ? 1 : 0) << c;
         spins |= (Mask)(sp ? 1 : 0) << c;
     }
-    fits = __reduce_and_sync(gmask, (unsigned)fits);
+    fits = group_and<G>((unsigned)fits, gmask);
     users = group_or<G>(users, gmask);
     spins = group_or<G>(spins, gmask);
+    const Mask all = n >= (int)(8 * sizeof(Mask)) ? ~(Mask)0 : (((Mask)1 << n) - 1);
+    if (rank_row) { // a candidate must be a permutation of 0..n-1
+        rank_ok = group_and<G>(rank_ok, gmask);
+        rbits = group_or<G>(rbits, gmask);
+        if (!rank_ok || rbits != all) {
+            if (lane == 0) {
+                atomicExch(p.err, PAAM_E_INVAL);
+                if (p.cand_ok) p.cand_ok[sys * p.K + cand] = 0;
+            }
+            __syncwarp(gmask);
+            return;
+        }
+    }
     if (!fits) { // outside the 32-bit bound: the int64 kernel takes it
-        if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)sys;
+        if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)item;
         __syncwarp(gmask);
         return;
     }
     __syncwarp(gmask);
-    if (!b.exec_prio) { // criticality-as-priority: highest chain priority on the executor
+    if (!xprio) { // criticality-as-priority: highest chain priority on the executor
         for (int c = lane; c < n; c += G) {
             const int xc = s.xk[c].x;
             int32_t best = INT32_MIN;
@@ -315,6 +362,7 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         const Mask cbit = (Mask)1 << c;
         if ((hp | (hpp & spins)) & ~sched) { // a needed H*_h is not available
             dep |= cbit;
+            if (rank_row) break; // a candidate fails at its first unschedulable chain
             continue;
         }
         const uint64_t Dc = s.D[c];
@@ -363,19 +411,26 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             }
         }
         __syncwarp(gmask);
+        if (!ok && rank_row) break;
     }
 
     // ---- outputs --------------------------------------------------------------
+    if (rank_row) {
+        if (lane == 0) {
+            const bool ok = sched == all;
+            if (p.cand_ok) p.cand_ok[sys * p.K + cand] = ok ? 1 : 0;
+            if (ok) atomicMin(p.first_ok + sys, cand);
+        }
+        __syncwarp(gmask);
+        return;
+    }
     for (int c = lane; c < n; c += G) {
         const Mask bit = (Mask)1 << c;
         const bool ok = sched & bit;
         R_out[c0 + c] = ok ? (int64_t)s.R[c] : -1;
         st_out[c0 + c] = ok ? PAAM_ST_SCHED : ((dep & bit) ? PAAM_ST_DEP : PAAM_ST_OVERRUN);
     }
-    if (lane == 0 && verdict) {
-        const Mask all = n >= (int)(8 * sizeof(Mask)) ? ~(Mask)0 : (((Mask)1 << n) - 1);
-        verdict[sys] = sched == all ? 1 : 0;
-    }
+    if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
     __syncwarp(gmask);
 }
 
@@ -393,10 +448,10 @@ __global__ void __launch_bounds__(256) analyze_fast_kernel(BatchDev b, AnalysisP
     const int lane = threadIdx.x % G;
     FastSmem<MAXN> &s = reinterpret_cast<FastSmem<MAXN> *>(smem_raw)[grp];
     const unsigned gmask = group_mask<G>();
-    const int64_t n_items = list ? (int64_t)*count : b.n_sys;
+    const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n_items; i += (int64_t)gridDim.x * groups) {
-        const int64_t sys = list ? (int64_t)list[i] : i;
-        fast_system<G, MAXN>(b, p, sys, s, lane, gmask, R, st, verdict, big_list, big_count, wide_list,
+        const int64_t item = list ? (int64_t)list[i] : i;
+        fast_system<G, MAXN>(b, p, item, s, lane, gmask, R, st, verdict, big_list, big_count, wide_list,
                              wide_count);
     }
 }
@@ -487,17 +542,18 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     LaunchFn bigfn = find_variant(cfg.impl_big, cfg.g_big, 64);
     if (!small || !bigfn) return PAAM_E_INVAL;
     int k = 0;
+    const int64_t items = p.K > 0 ? b->n_sys * (int64_t)p.K : b->n_sys;
     PAAM_CUDA_TRY(cudaMemsetAsync(b->counts, 0, 2 * sizeof(int32_t), stream));
-    int rc = small(b, p, R, status, verdict, nullptr, nullptr, b->n_sys, cfg.threads, stream);
+    int rc = small(b, p, R, status, verdict, nullptr, nullptr, items, cfg.threads, stream);
     if (rc != PAAM_OK) return rc;
     ++k;
     if (b->max_chains > cfg.maxn_small) {
-        rc = bigfn(b, p, R, status, verdict, b->list_big, b->counts, b->n_sys, cfg.threads, stream);
+        rc = bigfn(b, p, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
         if (rc != PAAM_OK) return rc;
         ++k;
     }
     if (!batch_fits_32(b, p)) {
-        rc = paam_launch_wide(b, p, R, status, verdict, b->list_wide, b->counts + 1, b->n_sys, stream);
+        rc = paam_launch_wide(b, p, R, status, verdict, b->list_wide, b->counts + 1, items, stream);
         if (rc != PAAM_OK) return rc;
         ++k;
     }

@@ -133,19 +133,28 @@ __device__ __forceinline__ uint32_t rarrivals(uint32_t t, uint32_t tm1, uint32_t
 }
 
 template <int G, int CPL>
-__device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t sys, OwnSmem<G * CPL> &s,
+__device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t item, OwnSmem<G * CPL> &s,
                            int lane, unsigned gm, int64_t *__restrict__ R_out, uint8_t *__restrict__ st_out,
                            uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
                            int32_t *wide_list, int32_t *wide_count)
 {
     constexpr int NMAX = G * CPL;
     using Mask = typename RegMask<NMAX>::type;
+    int64_t sys;
+    int32_t cand;
+    item_of(p, item, sys, cand);
+    if (p.K > 0 && p.early) { // candidate above the best schedulable one found so far
+        const int pruned = __shfl_sync(gm, cand_pruned(p, sys, cand) ? 1 : 0, 0, G);
+        if (pruned) return;
+    }
     const int64_t c0 = b.sys_chain_off[sys];
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
     if (n > NMAX) {
-        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)sys;
+        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
         return;
     }
+    const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.K + cand) * p.nmax : nullptr;
+    const int32_t *xprio = p.K > 0 ? nullptr : b.exec_prio; // candidates: criticality-as-priority
     const int64_t x0 = b.sys_exec_off[sys];
     const uint64_t kappa2 = 2 * (uint64_t)p.kappa, eps = (uint64_t)p.eps;
     const int64_t seg_base = n > 0 ? b.cb_seg_off[b.chain_cb_off[c0]] : 0;
@@ -155,8 +164,8 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t s
     uint32_t seg0[CPL];
     int32_t pr[CPL], ep[CPL], ex[CPL], co[CPL];
     bool sp[CPL], val[CPL];
-    Mask users = 0, spins = 0;
-    unsigned fits = 1;
+    Mask users = 0, spins = 0, rbits = 0;
+    unsigned fits = 1, rank_ok = 1;
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         const int j = lane + G * k;
@@ -169,10 +178,17 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t s
         const int64_t g = c0 + j;
         const int64_t T = b.T[g], D = b.D[g];
         const int x = b.exec[g];
-        pr[k] = b.prio[g];
+        if (rank_row) { // candidate priority order: rank 0 is the highest priority
+            const int r = rank_row[j];
+            rank_ok &= (r >= 0 && r < n) ? 1u : 0u;
+            rbits |= (r >= 0 && r < n) ? (Mask)1 << r : 0;
+            pr[k] = n - 1 - r;
+        } else {
+            pr[k] = b.prio[g];
+        }
         ex[k] = x;
         co[k] = b.exec_core[x0 + x];
-        ep[k] = b.exec_prio ? b.exec_prio[x0 + x] : INT32_MIN;
+        ep[k] = xprio ? xprio[x0 + x] : INT32_MIN;
         sp[k] = b.spin[g] != 0;
         const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
         uint64_t E = 0, Emax = 0, S = 0, M = 0, Amin = ~0ull;
@@ -213,15 +229,27 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t s
     fits = rand_<G>(fits, gm);
     users = ror<G>(users, gm);
     spins = ror<G>(spins, gm);
+    const Mask all = n >= (int)(8 * sizeof(Mask)) ? ~(Mask)0 : (((Mask)1 << n) - 1);
+    if (rank_row) { // a candidate must be a permutation of 0..n-1
+        rank_ok = rand_<G>(rank_ok, gm);
+        rbits = ror<G>(rbits, gm);
+        if (!rank_ok || rbits != all) {
+            if (lane == 0) {
+                atomicExch(p.err, PAAM_E_INVAL);
+                if (p.cand_ok) p.cand_ok[sys * p.K + cand] = 0;
+            }
+            return;
+        }
+    }
     uint32_t dmax = 0;
 #pragma unroll
     for (int k = 0; k < CPL; ++k) dmax = Dv[k] > dmax ? Dv[k] : dmax;
     const bool narrow = rmax<G>(dmax, gm) < kNarrow - G * CPL;
     if (!fits) {
-        if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)sys;
+        if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)item;
         return;
     }
-    if (!b.exec_prio) { // criticality-as-priority: highest chain priority on the executor
+    if (!xprio) { // criticality-as-priority: highest chain priority on the executor
         int32_t best[CPL];
 #pragma unroll
         for (int k = 0; k < CPL; ++k) best[k] = INT32_MIN;
@@ -369,6 +397,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t s
         const Mask cbit = (Mask)1 << c;
         if ((hp | (hpp & spins)) & ~sched) { // a needed H*_h is not available
             dep |= cbit;
+            if (rank_row) break; // a candidate fails at its first unschedulable chain
             continue;
         }
         uint32_t ccoef[CPL], acoef[CPL];
@@ -416,10 +445,21 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t s
                     Ehp[k] = Ev[k] + (uint32_t)hs;
                     if (sp[k]) Ehpp[k] = Ev[k] + (uint32_t)hs;
                 }
+        } else if (rank_row) {
+            break;
         }
     }
 
     // ---- outputs --------------------------------------------------------------
+    if (rank_row) {
+        if (lane == 0) {
+            const bool ok = sched == all;
+            if (p.cand_ok) p.cand_ok[sys * p.K + cand] = ok ? 1 : 0;
+            if (ok) atomicMin(p.first_ok + sys, cand);
+        }
+        __syncwarp(gm);
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         if (!val[k]) continue;
@@ -428,10 +468,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t s
         R_out[c0 + j] = ok ? (int64_t)Rv[k] : -1;
         st_out[c0 + j] = ok ? PAAM_ST_SCHED : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN);
     }
-    if (lane == 0 && verdict) {
-        const Mask all = n >= (int)(8 * sizeof(Mask)) ? ~(Mask)0 : (((Mask)1 << n) - 1);
-        verdict[sys] = sched == all ? 1 : 0;
-    }
+    if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
     __syncwarp(gm);
 }
 
@@ -448,10 +485,10 @@ __global__ void __launch_bounds__(256) analyze_reg_kernel(BatchDev b, AnalysisPa
     const int lane = threadIdx.x % G;
     OwnSmem<G * CPL> &s = reinterpret_cast<OwnSmem<G * CPL> *>(smem_raw)[grp];
     const unsigned gm = rgroup_mask<G>();
-    const int64_t n_items = list ? (int64_t)*count : b.n_sys;
+    const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n_items; i += (int64_t)gridDim.x * groups) {
-        const int64_t sys = list ? (int64_t)list[i] : i;
-        reg_system<G, CPL>(b, p, sys, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
+        const int64_t item = list ? (int64_t)list[i] : i;
+        reg_system<G, CPL>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
     }
 }
 

@@ -54,26 +54,44 @@ __device__ __forceinline__ int group_or(int v, unsigned mask)
 __device__ __forceinline__ int64_t arrivals(int64_t t, int64_t T) { return (t + T - 1) / T + 1; }
 
 template <int G, int MAXN>
-__device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64_t sys,
+__device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64_t item,
                                SysSmem<MAXN> &s, int lane, unsigned gmask, int64_t *__restrict__ R_out,
                                uint8_t *__restrict__ st_out, uint8_t *__restrict__ verdict)
 {
+    int64_t sys;
+    int32_t cand;
+    item_of(p, item, sys, cand);
+    if (p.K > 0 && p.early) { // candidate above the best schedulable one found so far
+        const int base_lane = (int)(threadIdx.x & 31u) & ~(G - 1);
+        if (__shfl_sync(gmask, cand_pruned(p, sys, cand) ? 1 : 0, base_lane)) return;
+    }
     const int64_t c0 = b.sys_chain_off[sys];
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
     const int64_t x0 = b.sys_exec_off[sys];
     const int64_t kappa2 = 2 * p.kappa, eps = p.eps;
+    const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.K + cand) * p.nmax : nullptr;
+    const int32_t *xprio = p.K > 0 ? nullptr : b.exec_prio; // candidates: criticality-as-priority
 
     // ---- chain aggregates (Sec. II-C; A* = A + 2 kappa) -------------------
+    int rank_bad = 0;
+    unsigned long long rbits = 0;
     for (int c = lane; c < n; c += G) {
         const int64_t g = c0 + c;
         s.T[c] = b.T[g];
         s.D[c] = b.D[g];
-        s.prio[c] = b.prio[g];
+        if (rank_row) { // candidate priority order: rank 0 is the highest priority
+            const int r = rank_row[c];
+            if (r < 0 || r >= n) rank_bad = 1;
+            else rbits |= 1ull << r;
+            s.prio[c] = n - 1 - r;
+        } else {
+            s.prio[c] = b.prio[g];
+        }
         const int x = b.exec[g];
         s.exec[c] = x;
         s.spin[c] = b.spin[g];
         s.core[c] = b.exec_core[x0 + x];
-        s.eprio[c] = b.exec_prio ? b.exec_prio[x0 + x] : 0;
+        s.eprio[c] = xprio ? xprio[x0 + x] : 0;
         const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
         int64_t E = 0, Emax = 0, S = 0, M = 0;
         for (int64_t cb = cb0; cb < cb1; ++cb) {
@@ -95,12 +113,25 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
         s.seglo[c] = q0;
     }
     __syncwarp(gmask);
+    if (rank_row) { // a candidate must be a permutation of 0..n-1
+        rank_bad = group_or<G>(rank_bad, gmask);
+        for (int off = G / 2; off > 0; off >>= 1) rbits |= __shfl_xor_sync(gmask, rbits, off);
+        const unsigned long long all = n >= 64 ? ~0ull : ((1ull << n) - 1);
+        if (rank_bad || rbits != all) {
+            if (lane == 0) {
+                atomicExch(p.err, PAAM_E_INVAL);
+                if (p.cand_ok) p.cand_ok[sys * p.K + cand] = 0;
+            }
+            __syncwarp(gmask);
+            return;
+        }
+    }
 
     // ---- executor priorities, buckets (R2), blocking terms ----------------
     int n_users = 0;
     for (int k = 0; k < n; ++k) n_users += s.delta[k] > 0;
     for (int c = lane; c < n; c += G) {
-        if (!b.exec_prio) { // criticality-as-priority: highest chain priority on the executor
+        if (!xprio) { // criticality-as-priority: highest chain priority on the executor
             int32_t best = INT32_MIN;
             for (int k = 0; k < n; ++k)
                 if (s.exec[k] == s.exec[c] && s.prio[k] > best) best = s.prio[k];
@@ -219,7 +250,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
             s.Hs[c] = hs_final;
         }
         __syncwarp(gmask);
-        if (lane == 0) {
+        if (lane == 0 && !rank_row) {
             R_out[c0 + c] = R;
             st_out[c0 + c] = st;
         }
@@ -227,7 +258,14 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     int ok = 1;
     for (int c = lane; c < n; c += G) ok &= s.status[c] == PAAM_ST_SCHED;
     for (int off = G / 2; off > 0; off >>= 1) ok &= __shfl_xor_sync(gmask, ok, off);
-    if (lane == 0 && verdict) verdict[sys] = (uint8_t)ok;
+    if (lane == 0) {
+        if (rank_row) {
+            if (p.cand_ok) p.cand_ok[sys * p.K + cand] = (uint8_t)ok;
+            if (ok) atomicMin(p.first_ok + sys, cand);
+        } else if (verdict) {
+            verdict[sys] = (uint8_t)ok;
+        }
+    }
     __syncwarp(gmask);
 }
 
@@ -244,10 +282,10 @@ __global__ void __launch_bounds__(256) analyze_wide_kernel(BatchDev b, AnalysisP
     const int lane = threadIdx.x % G;
     SysSmem<MAXN> &s = reinterpret_cast<SysSmem<MAXN> *>(smem_raw)[grp];
     const unsigned gmask = group_mask<G>();
-    const int64_t n = list ? (int64_t)*count : b.n_sys;
+    const int64_t n = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n; i += (int64_t)gridDim.x * groups) {
-        const int64_t sys = list ? (int64_t)list[i] : i;
-        analyze_system<G, MAXN>(b, p, sys, s, lane, gmask, R, st, verdict);
+        const int64_t item = list ? (int64_t)list[i] : i;
+        analyze_system<G, MAXN>(b, p, item, s, lane, gmask, R, st, verdict);
     }
 }
 

@@ -396,9 +396,8 @@ static int check_opts(const paam_analysis_opts *o)
 
 static AnalysisParams params_of(const paam_analysis_opts *o)
 {
-    AnalysisParams p;
+    AnalysisParams p = {};
     p.n_buckets = o->n_buckets;
-    p.pad_ = 0;
     p.eps = o->eps_ns;
     p.kappa = o->kappa_ns;
     return p;

@@ -22,10 +22,46 @@ void paam_count_launch(unsigned n = 1);
 
 struct AnalysisParams {
     int32_t n_buckets;
-    int32_t pad_;
+    int32_t K; // 0: analyse every system once; K > 0: candidate mode (below)
     int64_t eps;
     int64_t kappa;
+    // Candidate mode (priority-assignment search): work item i is system
+    // i % n_sys under candidate i / n_sys (candidates in order, so that early
+    // exit prunes well); its chain priorities come from the rank row
+    // ranks[(system * K + candidate) * nmax ..] (0 = highest), executor priorities derived
+    // (criticality-as-priority).  A candidate stops at its first chain that is
+    // not schedulable; results go to cand_ok[i] (optional) and to a running
+    // minimum first_ok[system] of the schedulable candidate indices, cand_ok
+    // indexed system * K + candidate.  early:
+    // skip candidates above the current minimum.  err receives PAAM_E_INVAL
+    // when a rank row is not a permutation of 0..n-1.
+    const int16_t *ranks;
+    int64_t n_sys;
+    int32_t nmax;
+    int32_t early;
+    uint8_t *cand_ok;
+    int32_t *first_ok;
+    int32_t *err;
 };
+
+// Item i of a launch: system index and candidate index (0 outside candidate mode).
+__device__ __forceinline__ void item_of(const AnalysisParams &p, int64_t i, int64_t &sys, int32_t &cand)
+{
+    if (p.K > 0) {
+        cand = (int32_t)(i / p.n_sys);
+        sys = i - (int64_t)cand * p.n_sys;
+    } else {
+        sys = i;
+        cand = 0;
+    }
+}
+
+// Early exit of the search: is candidate `cand` of `sys` above the best one found so far?
+__device__ __forceinline__ bool cand_pruned(const AnalysisParams &p, int64_t sys, int32_t cand)
+{
+    if (p.K == 0 || !p.early) return false;
+    return cand > *(volatile const int32_t *)(p.first_ok + sys);
+}
 
 // Batch-wide maxima recorded by validation; they decide which kernels an
 // analysis needs (the 32-bit fast path covers every system when they fit).

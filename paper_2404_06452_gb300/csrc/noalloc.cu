@@ -126,9 +126,8 @@ extern "C" int paam_rta_analyze_noalloc(const paam_systems_view *v, const paam_a
     b.max_exec = herr[3];
     for (int i = 0; i < ST_COUNT; ++i) b.stats[i] = hstats[i];
 
-    AnalysisParams p;
+    AnalysisParams p = {};
     p.n_buckets = o->n_buckets;
-    p.pad_ = 0;
     p.eps = o->eps_ns;
     p.kappa = o->kappa_ns;
     int nk = 0;

@@ -1,0 +1,95 @@
+// search.cu -- exact priority-assignment search over candidate orders.
+//
+// Every (system, candidate) pair is one exact analysis (Sec. IV-F) with the
+// candidate's chain priorities and criticality-as-priority executor
+// priorities (Sec. II-C); a candidate is schedulable when every chain is
+// (the admission test of Sec. IV-A).  The analysis kernels run in candidate
+// mode (see AnalysisParams): candidates are visited in order and each stops
+// at its first unschedulable chain; with stop_at_first a candidate above the
+// best one already found for its system is skipped.
+#include "internal.cuh"
+
+namespace {
+
+__global__ void search_init(int32_t *first_ok, int64_t n_sys, int32_t K, uint8_t *cand_ok, int64_t n_cand)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sys; i += stride) first_ok[i] = K;
+    if (cand_ok)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_cand; i += stride) cand_ok[i] = 0;
+}
+
+__global__ void search_final(int32_t *first_ok, int64_t n_sys, int32_t K)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sys; i += stride)
+        if (first_ok[i] >= K) first_ok[i] = -1;
+}
+
+} // namespace
+
+extern "C" int paam_rta_search_priorities(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o,
+                                          const int16_t *ranks, int32_t K, int32_t nmax, int32_t stop_at_first,
+                                          uint8_t *cand_ok, int32_t *first_ok, void *stream_)
+{
+    if (!ctx || !b || !o || !first_ok) return PAAM_E_INVAL;
+    if (b->ctx != ctx) return PAAM_E_STATE;
+    if (o->n_buckets < 1 || o->eps_ns < 0 || o->kappa_ns < 0) return PAAM_E_INVAL;
+    if (o->eps_ns > PAAM_MAX_OVERHEAD || o->kappa_ns > PAAM_MAX_OVERHEAD) return PAAM_E_RANGE;
+    if (o->blocking_mode != 0) return PAAM_E_UNSUPPORTED;
+    if (K < 1 || nmax < b->max_chains || nmax < 1 || (b->n_sys > 0 && !ranks)) return PAAM_E_INVAL;
+    if (b->n_sys * (int64_t)K > (int64_t)INT32_MAX) return PAAM_E_RANGE;
+    if (b->n_sys == 0) return PAAM_OK;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const int64_t items = b->n_sys * (int64_t)K;
+
+    // per-call scratch: the two deferral lists over items, their counts, an error word
+    void *tmp = nullptr;
+    const size_t list_bytes = 4 * (size_t)items;
+    if (cudaMallocAsync(&tmp, 2 * list_bytes + 64, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PAAM_E_NOMEM;
+    }
+    paam_batch bs = *b; // same tables, item-sized lists
+    bs.list_big = (int32_t *)tmp;
+    bs.list_wide = (int32_t *)((char *)tmp + list_bytes);
+    bs.counts = (int32_t *)((char *)tmp + 2 * list_bytes);
+    int32_t *err = bs.counts + 4;
+    bs.graph = nullptr;
+
+    int rc = PAAM_OK;
+    const int threads = 256;
+    int blocks = (int)((items + threads - 1) / threads);
+    if (blocks > 8 * ctx->n_sm) blocks = 8 * ctx->n_sm;
+    if (cudaMemsetAsync(err, 0, sizeof(int32_t), stream) != cudaSuccess) rc = PAAM_E_CUDA;
+    search_init<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K, cand_ok, items);
+    if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+
+    AnalysisParams p = {};
+    p.n_buckets = o->n_buckets;
+    p.eps = o->eps_ns;
+    p.kappa = o->kappa_ns;
+    p.K = K;
+    p.ranks = ranks;
+    p.n_sys = b->n_sys;
+    p.nmax = nmax;
+    p.early = stop_at_first ? 1 : 0;
+    p.cand_ok = cand_ok;
+    p.first_ok = first_ok;
+    p.err = err;
+    int nk = 0;
+    if (rc == PAAM_OK) rc = paam_enqueue_analysis(&bs, p, kLaunchCfgs[b->cfg_index], nullptr, nullptr, nullptr,
+                                                  stream, &nk);
+    if (rc == PAAM_OK) {
+        search_final<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K);
+        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        paam_count_launch((unsigned)nk + 2);
+    }
+    int32_t herr = 0;
+    if (cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, stream) != cudaSuccess) rc = PAAM_E_CUDA;
+    cudaFreeAsync(tmp, stream);
+    if (cudaStreamSynchronize(stream) != cudaSuccess) rc = PAAM_E_CUDA;
+    if (rc == PAAM_OK && herr != 0) rc = herr;
+    return rc;
+}

@@ -65,3 +65,23 @@ def test_permutations():
         for k in range(2, 5):
             assert sorted(p[s, k, : n[s]].tolist()) == list(range(n[s]))
             assert np.all(p[s, k, n[s]:] == -1)
+
+
+def test_candidate_ranks():
+    import oracle
+
+    sy = g.generate("cfg3", n_sys=300)
+    r = g.candidate_ranks(sy, 6, 9, nmax=64)
+    n = sy.chains_per_system()
+    for s in range(0, 300, 37):
+        c0 = sy.sys_chain_off[s]
+        for k in range(6):
+            assert sorted(r[s, k, : n[s]].tolist()) == list(range(n[s]))
+            assert np.all(r[s, k, n[s]:] == -1)
+        # slot 0 follows the given priorities, slot 1 the deadlines
+        assert np.all(np.argsort(r[s, 0, : n[s]]) == np.argsort(-sy.prio[c0:c0 + n[s]], kind="stable"))
+        assert np.all(np.diff(sy.D[c0:c0 + n[s]][np.argsort(r[s, 1, : n[s]])]) >= 0)
+    # slot 0 is the plain analysis with criticality-as-priority executor priorities
+    ref = oracle.search(sy, r[:, :1], threads=4)
+    a = oracle.analyze(sy, derive_exec_prio=True, threads=4)
+    assert np.array_equal(ref["cand_ok"][:, 0], a["verdict"])
