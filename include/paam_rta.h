@@ -252,6 +252,16 @@ int paam_rta_analyze_noalloc(const paam_systems_view *view, const paam_analysis_
                              uint8_t *status, uint8_t *verdict, void *stream);
 
 /*
+ * Tensor-core GEMM used by the surrogate network, exposed for testing:
+ * C[M, N] (fp32, row-major) = A[M, K] * B[N, K]^T with A and B bf16 row-major
+ * device matrices (leading dimension K), fp32 accumulation.  K must be a
+ * multiple of 64 and N of 64.  Enqueued on `stream`; *err (device int32,
+ * zeroed by the caller) receives PAAM_E_TIMEOUT if a bounded device wait
+ * expired.  Not part of the paper.
+ */
+int paam_tc_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int32_t *err, void *stream);
+
+/*
  * Diagnostics: number of CUDA kernels this library has launched in this
  * process (all contexts).  Not part of the paper; used to report how many
  * of the library's own kernels ran inside a timed region.

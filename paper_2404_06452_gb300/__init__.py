@@ -8,7 +8,7 @@ from ._binding import (PAAM_MAX_CHAINS, PAAM_ST_DEP, PAAM_ST_ITERCAP, PAAM_ST_OV
                        AnalysisOpts, Batch, Context, PaamError, SystemsView, analysis_opts, launch_count, lib,
                        paam_rta_analyze_batch, paam_rta_autotune, paam_rta_get_launch_config,
                        paam_rta_load_systems, paam_rta_num_launch_configs, paam_rta_set_launch_config,
-                       PAAM_NOALLOC_MAX_SYS, paam_rta_analyze_noalloc, paam_rta_search_priorities, strerror)
+                       PAAM_NOALLOC_MAX_SYS, paam_rta_analyze_noalloc, paam_rta_search_priorities, paam_tc_gemm_bf16, strerror)
 from .api import analyze, search, to_device
 
 __all__ = [
@@ -16,6 +16,6 @@ __all__ = [
     "paam_rta_load_systems", "paam_rta_analyze_batch", "analyze", "to_device", "launch_count",
     "paam_rta_autotune", "paam_rta_num_launch_configs", "paam_rta_set_launch_config",
     "paam_rta_get_launch_config", "paam_rta_analyze_noalloc", "PAAM_NOALLOC_MAX_SYS",
-    "paam_rta_search_priorities", "search",
+    "paam_rta_search_priorities", "search", "paam_tc_gemm_bf16",
     "PAAM_ST_SCHED", "PAAM_ST_OVERRUN", "PAAM_ST_DEP", "PAAM_ST_ITERCAP", "PAAM_MAX_CHAINS",
 ]

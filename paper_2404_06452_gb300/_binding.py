@@ -73,6 +73,8 @@ def lib():
             "paam_rta_get_launch_config": (ctypes.c_int, [_c_void_p]),
             "paam_rta_analyze_noalloc": (ctypes.c_int, [P(SystemsView), P(AnalysisOpts), _c_void_p, _c_void_p,
                                                         _c_void_p, _c_void_p]),
+            "paam_tc_gemm_bf16": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, _c_void_p, _c_void_p]),
             "paam_rta_search_priorities": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
                                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                           _c_void_p, _c_void_p, _c_void_p]),
@@ -89,7 +91,8 @@ def exported_symbols() -> list:
     return ["paam_create", "paam_destroy", "paam_strerror", "paam_rta_load_systems", "paam_batch_n_sys",
             "paam_batch_n_chain", "paam_batch_free", "paam_rta_analyze_batch", "paam_launch_count",
             "paam_rta_num_launch_configs", "paam_rta_autotune", "paam_rta_set_launch_config",
-            "paam_rta_get_launch_config", "paam_rta_analyze_noalloc", "paam_rta_search_priorities"]
+            "paam_rta_get_launch_config", "paam_rta_analyze_noalloc", "paam_rta_search_priorities",
+            "paam_tc_gemm_bf16"]
 
 
 def launch_count() -> int:
@@ -268,3 +271,11 @@ def paam_rta_search_priorities(ctx: Context, batch: Batch, opts: AnalysisOpts, r
     _check(lib().paam_rta_search_priorities(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(ranks), int(K),
                                             int(nmax), 1 if stop_at_first else 0, _ptr(cand_ok), _ptr(first_ok),
                                             _stream_ptr(stream)), "paam_rta_search_priorities")
+
+
+def paam_tc_gemm_bf16(A, B, C, err, stream=None):
+    """C = A @ B^T on the tensor cores (A [M, K], B [N, K] bf16; C [M, N] fp32)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().paam_tc_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), _ptr(err),
+                                   _stream_ptr(stream)), "paam_tc_gemm_bf16")

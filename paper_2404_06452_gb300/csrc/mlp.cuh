@@ -1,0 +1,46 @@
+// mlp.cuh -- shared declarations of the surrogate network's GPU code.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+// Epilogue applied to each fp32 accumulator tile of the tensor-core GEMM.
+enum TcEpiMode {
+    TC_EPI_STORE_F32 = 0,  // C = acc
+    TC_EPI_BIAS_GELU = 1,  // Z = bf16(acc + bias); H = bf16(gelu(Z)); HT = H^T (optional)
+    TC_EPI_BIAS_F32 = 2,   // C = acc + bias
+    TC_EPI_DGELU = 3,      // H = bf16(acc * gelu'(Zin)); HT = H^T (optional)
+    TC_EPI_ATOMIC_F32 = 4, // C += acc (split-K partial sums)
+};
+
+struct TcEpilogue {
+    int mode, M, N;                // valid output rows and columns
+    float *C;
+    int ldc;
+    const float *bias;             // [N]
+    const __nv_bfloat16 *Zin;      // pre-activation read by TC_EPI_DGELU
+    int ldzin;
+    __nv_bfloat16 *Z;              // pre-activation written by TC_EPI_BIAS_GELU
+    int ldz;
+    __nv_bfloat16 *H;              // activation (BIAS_GELU) or input gradient (DGELU), row-major
+    int ldh;
+    __nv_bfloat16 *HT;             // H transposed ([N][M]), optional
+    int ldht;
+};
+
+// C[M, N] (epilogue) = A[M, K] * B[N, K]^T with A, B bf16 row-major, lda/ldb in
+// elements; a_rows / b_rows are the allocated rows of A and B (tiles past them
+// read zeros).  K must be a multiple of 64, lda and ldb multiples of 8, the
+// output N a multiple of 64.  splits > 1 divides K over grid z and needs
+// TC_EPI_ATOMIC_F32.  err receives PAAM_E_TIMEOUT if a bounded wait expired.
+struct TcGemm {
+    const __nv_bfloat16 *A;
+    int lda, a_rows;
+    const __nv_bfloat16 *B;
+    int ldb, b_rows;
+    int K, splits;
+    TcEpilogue ep;
+};
+
+int tc_gemm(const TcGemm &g, int32_t *err, cudaStream_t stream);
