@@ -201,6 +201,95 @@ int paam_rta_search_priorities(paam_ctx *ctx, const paam_batch *batch, const paa
                                uint8_t *cand_ok, int32_t *first_ok, void *stream);
 
 /*
+ * The same search over an ordered subset of each system's candidates:
+ * ranks holds Kc candidates per system ([n_sys][Kc][nmax]); slot j of system
+ * s visits candidate order[s * K + j] (device int32 in [0, Kc)), so K slots
+ * are analysed per system in that order.  first_ok[s] is the candidate index
+ * (not the slot) of the first admitted slot, or -1; cand_ok is indexed
+ * s * Kc + candidate and reads 0 for candidates not visited.  A surrogate
+ * ranking plus this call is the guided search: only candidates it visits
+ * can be admitted, and every admission is exact.
+ */
+int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *batch, const paam_analysis_opts *opts,
+                            const int16_t *ranks, int32_t Kc, int32_t nmax, const int32_t *order, int32_t K,
+                            int32_t stop_at_first, uint8_t *cand_ok, int32_t *first_ok, void *stream);
+
+/*
+ * Surrogate ranking model (not in the paper: it serves the priority search).
+ * A multilayer perceptron 1024 -> 256 -> 256 -> 256 -> 64 (GELU hidden
+ * layers, bf16 weights for bf16 tensor-core GEMMs with fp32 accumulation,
+ * fp32 master weights and AdamW moments) maps 16 features of each of up to
+ * 64 chains of a system under one priority order to each chain's predicted
+ * exact R / D (clipped to [0, 2]; 2 for an unschedulable chain).  The model
+ * only orders candidates: admission always comes from the exact analysis.
+ *
+ * paam_surrogate_train: trains on every system of `batch` with their own
+ * priorities; R / status are that batch's exact analysis outputs (device).
+ * *model NULL creates a model (initialised from opts->seed); otherwise the
+ * given model keeps training.  Synchronous.  opts->epoch_loss (host,
+ * optional) receives the mean minibatch loss of each epoch.
+ *
+ * paam_surrogate_infer: scores candidate k of system s (same ranks layout as
+ * paam_rta_search_priorities) by its largest predicted R / D and writes the
+ * top_k candidate indices per system in increasing score to ranked
+ * ([n_sys][top_k] device int32); scores ([n_sys][K] device float) optional.
+ * Synchronises `stream`.
+ *
+ * paam_surrogate_predict: per-chain predictions ([n_sys][64] device float) of
+ * the batch's own priority orders.
+ *
+ * paam_surrogate_grad: loss and gradients (host, paam_model_num_params()
+ * floats, parameter order as paam_model_get_params) of one minibatch X
+ * ([rows][1024] device bf16), L ([rows][64] device float, < 0 = no chain),
+ * rows a multiple of 128; the model is not updated.  For testing.
+ *
+ * Parameter order (get / set): per layer the weights [out][in] row-major,
+ * then the biases.  paam_model_save / load write and read a checkpoint
+ * (weights, biases, AdamW moments and step count).
+ */
+typedef struct {
+    int32_t epochs;        /* passes over the batch                              */
+    int32_t batch_rows;    /* minibatch size, a multiple of 128                   */
+    float lr, weight_decay, beta1, beta2, adam_eps;
+    uint64_t seed;         /* initialisation of a new model and minibatch order  */
+    int32_t n_buckets;     /* analysis parameters of the labels (features use    */
+    int32_t reserved_;     /*   the bucket count and kappa)                      */
+    int64_t kappa_ns;
+    float *epoch_loss;     /* host, optional, [epochs]                           */
+} paam_train_opts;
+
+int paam_model_create(paam_ctx *ctx, uint64_t seed, paam_model **out);
+void paam_model_free(paam_model *model);
+int64_t paam_model_num_params(void);
+int paam_model_get_params(const paam_model *model, float *host);
+int paam_model_set_params(paam_model *model, const float *host);
+int paam_model_save(const paam_model *model, const char *path);
+int paam_model_load(paam_ctx *ctx, const char *path, paam_model **out);
+int paam_surrogate_train(paam_ctx *ctx, const paam_batch *batch, const int64_t *R, const uint8_t *status,
+                         const paam_train_opts *opts, paam_model **model);
+int paam_surrogate_infer(paam_ctx *ctx, const paam_model *model, const paam_batch *batch, const int16_t *ranks,
+                         int32_t K, int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t top_k,
+                         int32_t *ranked, float *scores, void *stream);
+int paam_surrogate_predict(paam_ctx *ctx, const paam_model *model, const paam_batch *batch, int32_t n_buckets,
+                           int64_t kappa_ns, float *pred, void *stream);
+int paam_surrogate_grad(paam_ctx *ctx, paam_model *model, const void *X, const float *L, int32_t rows,
+                        float *grads_host, float *loss_host);
+
+/*
+ * The network's inputs: for item = system * K + candidate, 64 chain slots x
+ * 16 features (bf16, device, [n_sys * K][1024]); slots past the system's
+ * chains are zero.  Per chain: E / T, S* / T, D / T, log2(T / Tmin) / 4,
+ * rank / n, min(delta, 16) / 16, Emax / D, M* / D, sum over hp of (E + S*) / T,
+ * sum over hpp of E / T, sum over hps of S* / T, B / D, blk / D, (E + S*) / D,
+ * sum over hp and hpp of (E + S*) / D, 1 -- each clipped to [0, 8] (E, S*,
+ * M*, B, blk, hp, hpp, hps as
+ * in the analysis, under the candidate's priorities).  ranks NULL and K = 1
+ * take the batch's own priorities.  Enqueued on `stream`.
+ */
+int paam_surrogate_features(paam_ctx *ctx, const paam_batch *batch, const int16_t *ranks, int32_t K,
+                            int32_t nmax, int32_t n_buckets, int64_t kappa_ns, void *X, void *stream);
+
+/*
  * Launch configurations.  The analysis has several built-in launch
  * configurations (lanes per system, chain-table size of the first pass, lanes
  * per system for systems with more chains, CTA size); every one produces

@@ -1,0 +1,71 @@
+"""Float64 forward and backward of the surrogate network -- TEST INFRASTRUCTURE ONLY.
+
+Layers 1024 -> 256 -> 256 -> 256 -> 64; hidden activation GELU(z) =
+z * Phi(z) with the exact normal CDF; output linear; loss = mean over the
+valid (label >= 0) entries of (y - label)^2.  Parameters are one flat vector:
+per layer the weights [out][in] row-major, then the biases.  Gradients by
+hand-written backpropagation in numpy; shares no code with the CUDA path.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import erf
+
+SIZES = [(1024, 256), (256, 256), (256, 256), (256, 64)]
+
+
+def unpack(params):
+    params = np.asarray(params, np.float64)
+    out, o = [], 0
+    for fin, fout in SIZES:
+        W = params[o:o + fin * fout].reshape(fout, fin)
+        o += fin * fout
+        b = params[o:o + fout]
+        o += fout
+        out.append((W, b))
+    assert o == params.size
+    return out
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+
+
+def forward(params, X):
+    layers = unpack(params)
+    h = np.asarray(X, np.float64)
+    cache = []
+    for i, (W, b) in enumerate(layers):
+        z = h @ W.T + b
+        cache.append((h, z))
+        h = gelu(z) if i < len(layers) - 1 else z
+    return h, cache
+
+
+def loss_and_grad(params, X, L):
+    """Masked mean-squared error and its gradient with respect to params."""
+    layers = unpack(params)
+    Y, cache = forward(params, X)
+    L = np.asarray(L, np.float64)
+    mask = L >= 0
+    cnt = max(int(mask.sum()), 1)
+    d = np.where(mask, Y - L, 0.0)
+    loss = float((d * d).sum() / cnt)
+    g = 2.0 * d / cnt  # dLoss / dY
+    grads = []
+    for i in range(len(layers) - 1, -1, -1):
+        W, b = layers[i]
+        h_in, z = cache[i]
+        if i < len(layers) - 1:
+            g = g * gelu_grad(z)  # through the GELU of layer i
+        grads.append((g.T @ h_in, g.sum(axis=0)))
+        g = g @ W
+    flat = []
+    for gW, gb in reversed(grads):
+        flat.append(gW.ravel())
+        flat.append(gb)
+    return loss, np.concatenate(flat)

@@ -38,6 +38,14 @@ class AnalysisOpts(ctypes.Structure):
                 ("eps_ns", ctypes.c_int64), ("kappa_ns", ctypes.c_int64)]
 
 
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch_rows", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("weight_decay", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("adam_eps", ctypes.c_float), ("seed", ctypes.c_uint64), ("n_buckets", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32), ("kappa_ns", ctypes.c_int64),
+                ("epoch_loss", ctypes.POINTER(ctypes.c_float))]
+
+
 class PaamError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
@@ -73,6 +81,28 @@ def lib():
             "paam_rta_get_launch_config": (ctypes.c_int, [_c_void_p]),
             "paam_rta_analyze_noalloc": (ctypes.c_int, [P(SystemsView), P(AnalysisOpts), _c_void_p, _c_void_p,
                                                         _c_void_p, _c_void_p]),
+            "paam_rta_search_ordered": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
+                                                       ctypes.c_int32, ctypes.c_int32, _c_void_p, ctypes.c_int32,
+                                                       ctypes.c_int32, _c_void_p, _c_void_p, _c_void_p]),
+            "paam_model_create": (ctypes.c_int, [_c_void_p, ctypes.c_uint64, P(_c_void_p)]),
+            "paam_model_free": (None, [_c_void_p]),
+            "paam_model_num_params": (ctypes.c_int64, []),
+            "paam_model_get_params": (ctypes.c_int, [_c_void_p, _c_void_p]),
+            "paam_model_set_params": (ctypes.c_int, [_c_void_p, _c_void_p]),
+            "paam_model_save": (ctypes.c_int, [_c_void_p, ctypes.c_char_p]),
+            "paam_model_load": (ctypes.c_int, [_c_void_p, ctypes.c_char_p, P(_c_void_p)]),
+            "paam_surrogate_train": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, P(TrainOpts),
+                                                    P(_c_void_p)]),
+            "paam_surrogate_infer": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
+                                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                                    _c_void_p, _c_void_p, _c_void_p]),
+            "paam_surrogate_predict": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
+                                                      ctypes.c_int64, _c_void_p, _c_void_p]),
+            "paam_surrogate_grad": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
+                                                   _c_void_p, _c_void_p]),
+            "paam_surrogate_features": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
+                                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _c_void_p,
+                                                       _c_void_p]),
             "paam_tc_gemm_bf16": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _c_void_p, _c_void_p]),
             "paam_rta_search_priorities": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
@@ -92,7 +122,10 @@ def exported_symbols() -> list:
             "paam_batch_n_chain", "paam_batch_free", "paam_rta_analyze_batch", "paam_launch_count",
             "paam_rta_num_launch_configs", "paam_rta_autotune", "paam_rta_set_launch_config",
             "paam_rta_get_launch_config", "paam_rta_analyze_noalloc", "paam_rta_search_priorities",
-            "paam_tc_gemm_bf16"]
+            "paam_tc_gemm_bf16", "paam_rta_search_ordered", "paam_model_create", "paam_model_free",
+            "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
+            "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
+            "paam_surrogate_grad", "paam_surrogate_features"]
 
 
 def launch_count() -> int:
@@ -279,3 +312,107 @@ def paam_tc_gemm_bf16(A, B, C, err, stream=None):
     N = B.shape[0]
     _check(lib().paam_tc_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), _ptr(err),
                                    _stream_ptr(stream)), "paam_tc_gemm_bf16")
+
+
+def paam_rta_search_ordered(ctx: Context, batch: Batch, opts: AnalysisOpts, ranks, order, stop_at_first: bool,
+                            cand_ok, first_ok, stream=None):
+    """Search visiting candidates ``order[s, j]`` (device int32 [S, K]) of
+    ``ranks`` ([S, Kc, nmax] int16) in that order."""
+    S, Kc, nmax = ranks.shape
+    K = order.shape[1]
+    _check(lib().paam_rta_search_ordered(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(ranks), int(Kc),
+                                         int(nmax), _ptr(order), int(K), 1 if stop_at_first else 0, _ptr(cand_ok),
+                                         _ptr(first_ok), _stream_ptr(stream)), "paam_rta_search_ordered")
+
+
+class Model:
+    """A surrogate ranking model (``paam_model_*``)."""
+
+    def __init__(self, ctx: Context, handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    @staticmethod
+    def create(ctx: Context, seed: int = 0) -> "Model":
+        h = _c_void_p()
+        _check(lib().paam_model_create(ctx.handle, ctypes.c_uint64(seed), ctypes.byref(h)), "paam_model_create")
+        return Model(ctx, h)
+
+    @staticmethod
+    def load(ctx: Context, path: str) -> "Model":
+        h = _c_void_p()
+        _check(lib().paam_model_load(ctx.handle, path.encode(), ctypes.byref(h)), "paam_model_load")
+        return Model(ctx, h)
+
+    def save(self, path: str):
+        _check(lib().paam_model_save(self.handle, path.encode()), "paam_model_save")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(int(lib().paam_model_num_params()), np.float32)
+        _check(lib().paam_model_get_params(self.handle, out.ctypes.data), "paam_model_get_params")
+        return out
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == int(lib().paam_model_num_params())
+        _check(lib().paam_model_set_params(self.handle, p.ctypes.data), "paam_model_set_params")
+
+    def free(self):
+        if self.handle:
+            lib().paam_model_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def train_opts(epochs=1, batch_rows=8192, lr=1e-3, weight_decay=1e-4, beta1=0.9, beta2=0.999, adam_eps=1e-8,
+               seed=0, n_buckets=1, kappa=0, epoch_loss=None) -> TrainOpts:
+    o = TrainOpts(int(epochs), int(batch_rows), float(lr), float(weight_decay), float(beta1), float(beta2),
+                  float(adam_eps), ctypes.c_uint64(seed).value, int(n_buckets), 0, int(kappa), None)
+    if epoch_loss is not None:
+        o.epoch_loss = epoch_loss.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    return o
+
+
+def paam_surrogate_train(ctx: Context, batch: Batch, R, status, opts: TrainOpts, model: "Model | None" = None):
+    h = _c_void_p(model.handle.value if model is not None else None)
+    _check(lib().paam_surrogate_train(ctx.handle, batch.handle, _ptr(R), _ptr(status), ctypes.byref(opts),
+                                      ctypes.byref(h)), "paam_surrogate_train")
+    return model if model is not None else Model(ctx, h)
+
+
+def paam_surrogate_infer(ctx: Context, model: Model, batch: Batch, ranks, top_k: int, ranked, scores=None,
+                         n_buckets: int = 1, kappa: int = 0, stream=None):
+    S, K, nmax = ranks.shape
+    _check(lib().paam_surrogate_infer(ctx.handle, model.handle, batch.handle, _ptr(ranks), int(K), int(nmax),
+                                      int(n_buckets), int(kappa), int(top_k), _ptr(ranked), _ptr(scores),
+                                      _stream_ptr(stream)), "paam_surrogate_infer")
+
+
+def paam_surrogate_predict(ctx: Context, model: Model, batch: Batch, pred, n_buckets: int = 1, kappa: int = 0,
+                           stream=None):
+    _check(lib().paam_surrogate_predict(ctx.handle, model.handle, batch.handle, int(n_buckets), int(kappa),
+                                        _ptr(pred), _stream_ptr(stream)), "paam_surrogate_predict")
+
+
+def paam_surrogate_grad(ctx: Context, model: Model, X, L) -> tuple:
+    rows = X.shape[0]
+    g = np.empty(int(lib().paam_model_num_params()), np.float32)
+    loss = ctypes.c_float(0.0)
+    _check(lib().paam_surrogate_grad(ctx.handle, model.handle, _ptr(X), _ptr(L), int(rows), g.ctypes.data,
+                                     ctypes.byref(loss)), "paam_surrogate_grad")
+    return g, float(loss.value)
+
+
+def paam_surrogate_features(ctx: Context, batch: Batch, X, ranks=None, n_buckets: int = 1, kappa: int = 0,
+                            stream=None):
+    if ranks is None:
+        K, nmax = 1, 0
+    else:
+        _, K, nmax = ranks.shape
+    _check(lib().paam_surrogate_features(ctx.handle, batch.handle, _ptr(ranks), int(K), int(nmax), int(n_buckets),
+                                         int(kappa), _ptr(X), _stream_ptr(stream)), "paam_surrogate_features")

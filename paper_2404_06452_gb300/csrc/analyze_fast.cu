@@ -159,7 +159,7 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
         return;
     }
-    const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.K + cand) * p.nmax : nullptr;
+    const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.Kc + cand_of(p, sys, cand)) * p.nmax : nullptr;
     const int32_t *xprio = p.K > 0 ? nullptr : b.exec_prio; // candidates: criticality-as-priority
     const int64_t x0 = b.sys_exec_off[sys];
     const uint64_t kappa2 = 2 * (uint64_t)p.kappa, eps = (uint64_t)p.eps;
@@ -233,7 +233,7 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         if (!rank_ok || rbits != all) {
             if (lane == 0) {
                 atomicExch(p.err, PAAM_E_INVAL);
-                if (p.cand_ok) p.cand_ok[sys * p.K + cand] = 0;
+                if (p.cand_ok) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = 0;
             }
             __syncwarp(gmask);
             return;
@@ -418,7 +418,7 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     if (rank_row) {
         if (lane == 0) {
             const bool ok = sched == all;
-            if (p.cand_ok) p.cand_ok[sys * p.K + cand] = ok ? 1 : 0;
+            if (p.cand_ok) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = ok ? 1 : 0;
             if (ok) atomicMin(p.first_ok + sys, cand);
         }
         __syncwarp(gmask);

@@ -69,7 +69,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
     const int64_t x0 = b.sys_exec_off[sys];
     const int64_t kappa2 = 2 * p.kappa, eps = p.eps;
-    const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.K + cand) * p.nmax : nullptr;
+    const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.Kc + cand_of(p, sys, cand)) * p.nmax : nullptr;
     const int32_t *xprio = p.K > 0 ? nullptr : b.exec_prio; // candidates: criticality-as-priority
 
     // ---- chain aggregates (Sec. II-C; A* = A + 2 kappa) -------------------
@@ -120,7 +120,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
         if (rank_bad || rbits != all) {
             if (lane == 0) {
                 atomicExch(p.err, PAAM_E_INVAL);
-                if (p.cand_ok) p.cand_ok[sys * p.K + cand] = 0;
+                if (p.cand_ok) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = 0;
             }
             __syncwarp(gmask);
             return;
@@ -260,7 +260,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     for (int off = G / 2; off > 0; off >>= 1) ok &= __shfl_xor_sync(gmask, ok, off);
     if (lane == 0) {
         if (rank_row) {
-            if (p.cand_ok) p.cand_ok[sys * p.K + cand] = (uint8_t)ok;
+            if (p.cand_ok) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = (uint8_t)ok;
             if (ok) atomicMin(p.first_ok + sys, cand);
         } else if (verdict) {
             verdict[sys] = (uint8_t)ok;

@@ -38,6 +38,8 @@ struct AnalysisParams {
     const int16_t *ranks;
     int64_t n_sys;
     int32_t nmax;
+    int32_t Kc;           // candidates per system in ranks / cand_ok (K = slots visited)
+    const int32_t *order; // optional [n_sys][K]: candidate visited in slot j (else slot j = candidate j)
     int32_t early;
     uint8_t *cand_ok;
     int32_t *first_ok;
@@ -56,7 +58,13 @@ __device__ __forceinline__ void item_of(const AnalysisParams &p, int64_t i, int6
     }
 }
 
-// Early exit of the search: is candidate `cand` of `sys` above the best one found so far?
+// Candidate index visited in slot `slot` of system `sys`.
+__device__ __forceinline__ int32_t cand_of(const AnalysisParams &p, int64_t sys, int32_t slot)
+{
+    return p.order ? p.order[sys * p.K + slot] : slot;
+}
+
+// Early exit of the search: is slot `cand` of `sys` above the best one found so far?
 __device__ __forceinline__ bool cand_pruned(const AnalysisParams &p, int64_t sys, int32_t cand)
 {
     if (p.K == 0 || !p.early) return false;

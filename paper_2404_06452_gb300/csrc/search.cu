@@ -19,11 +19,21 @@ __global__ void search_init(int32_t *first_ok, int64_t n_sys, int32_t K, uint8_t
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_cand; i += stride) cand_ok[i] = 0;
 }
 
-__global__ void search_final(int32_t *first_ok, int64_t n_sys, int32_t K)
+// slot of the first admitted candidate -> its candidate index (or -1)
+__global__ void search_final(int32_t *first_ok, int64_t n_sys, int32_t K, const int32_t *order)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sys; i += stride)
-        if (first_ok[i] >= K) first_ok[i] = -1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sys; i += stride) {
+        const int32_t v = first_ok[i];
+        first_ok[i] = v >= K ? -1 : (order ? order[i * K + v] : v);
+    }
+}
+
+__global__ void check_order(const int32_t *order, int64_t n, int32_t Kc, int32_t *err)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        if (order[i] < 0 || order[i] >= Kc) atomicExch(err, PAAM_E_INVAL);
 }
 
 } // namespace
@@ -32,12 +42,23 @@ extern "C" int paam_rta_search_priorities(paam_ctx *ctx, const paam_batch *b, co
                                           const int16_t *ranks, int32_t K, int32_t nmax, int32_t stop_at_first,
                                           uint8_t *cand_ok, int32_t *first_ok, void *stream_)
 {
+    return paam_rta_search_ordered(ctx, b, o, ranks, K, nmax, nullptr, K, stop_at_first, cand_ok, first_ok,
+                                   stream_);
+}
+
+extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o,
+                                       const int16_t *ranks, int32_t Kc, int32_t nmax, const int32_t *order,
+                                       int32_t K, int32_t stop_at_first, uint8_t *cand_ok, int32_t *first_ok,
+                                       void *stream_)
+{
     if (!ctx || !b || !o || !first_ok) return PAAM_E_INVAL;
     if (b->ctx != ctx) return PAAM_E_STATE;
     if (o->n_buckets < 1 || o->eps_ns < 0 || o->kappa_ns < 0) return PAAM_E_INVAL;
     if (o->eps_ns > PAAM_MAX_OVERHEAD || o->kappa_ns > PAAM_MAX_OVERHEAD) return PAAM_E_RANGE;
     if (o->blocking_mode != 0) return PAAM_E_UNSUPPORTED;
-    if (K < 1 || nmax < b->max_chains || nmax < 1 || (b->n_sys > 0 && !ranks)) return PAAM_E_INVAL;
+    if (Kc < 1 || K < 1 || (!order && K != Kc) || nmax < b->max_chains || nmax < 1 || (b->n_sys > 0 && !ranks))
+        return PAAM_E_INVAL;
+    if (b->n_sys * (int64_t)Kc > (int64_t)INT32_MAX) return PAAM_E_RANGE;
     if (b->n_sys * (int64_t)K > (int64_t)INT32_MAX) return PAAM_E_RANGE;
     if (b->n_sys == 0) return PAAM_OK;
     PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -63,14 +84,25 @@ extern "C" int paam_rta_search_priorities(paam_ctx *ctx, const paam_batch *b, co
     int blocks = (int)((items + threads - 1) / threads);
     if (blocks > 8 * ctx->n_sm) blocks = 8 * ctx->n_sm;
     if (cudaMemsetAsync(err, 0, sizeof(int32_t), stream) != cudaSuccess) rc = PAAM_E_CUDA;
-    search_init<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K, cand_ok, items);
+    search_init<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K, cand_ok, b->n_sys * (int64_t)Kc);
+    if (order) check_order<<<blocks, threads, 0, stream>>>(order, items, Kc, err);
     if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+    if (order && rc == PAAM_OK) { // an out-of-range slot must not reach the analysis kernels
+        int32_t herr = 0;
+        if (cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess)
+            rc = PAAM_E_CUDA;
+        else if (herr != 0)
+            rc = herr;
+    }
 
     AnalysisParams p = {};
     p.n_buckets = o->n_buckets;
     p.eps = o->eps_ns;
     p.kappa = o->kappa_ns;
     p.K = K;
+    p.Kc = Kc;
+    p.order = order;
     p.ranks = ranks;
     p.n_sys = b->n_sys;
     p.nmax = nmax;
@@ -82,9 +114,9 @@ extern "C" int paam_rta_search_priorities(paam_ctx *ctx, const paam_batch *b, co
     if (rc == PAAM_OK) rc = paam_enqueue_analysis(&bs, p, kLaunchCfgs[b->cfg_index], nullptr, nullptr, nullptr,
                                                   stream, &nk);
     if (rc == PAAM_OK) {
-        search_final<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K);
+        search_final<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K, order);
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-        paam_count_launch((unsigned)nk + 2);
+        paam_count_launch((unsigned)nk + (order ? 3 : 2));
     }
     int32_t herr = 0;
     if (cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, stream) != cudaSuccess) rc = PAAM_E_CUDA;

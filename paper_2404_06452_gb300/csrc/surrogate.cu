@@ -1,0 +1,840 @@
+// surrogate.cu -- the learned ranking model of the priority-assignment search.
+//
+// A multilayer perceptron 1024 -> 256 -> 256 -> 256 -> 64 with GELU hidden
+// layers reads the 64 x 16 chain features of one (system, candidate) and
+// predicts, per chain, the exact analysis' response time relative to the
+// deadline (clip(R / D, 0, 2); 2 when not schedulable).  Weights are kept in
+// fp32 (with AdamW moments) and used as bf16 copies by the tensor-core GEMMs
+// (mlp_gemm.cu), which accumulate in fp32.  Training labels come from the
+// exact analysis kernels; a candidate's score is its largest predicted
+// R / D, and candidates are confirmed in increasing score by the exact search
+// (paam_rta_search_ordered), so every admission stays exact.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mlp.cuh"
+
+struct paam_model {
+    paam_ctx *ctx;
+    int64_t step;
+    void *block;
+    size_t block_bytes;
+    float *W[4], *bias[4], *mW[4], *vW[4], *mb[4], *vb[4], *gW[4], *gb[4];
+    __nv_bfloat16 *Wb[4], *WbT[4];
+};
+
+namespace {
+
+constexpr int NL = 4;
+constexpr int IN[NL] = {1024, 256, 256, 256};
+constexpr int OUT[NL] = {256, 256, 256, 64};
+constexpr int NCH = 64, NF = 16, XW = NCH * NF;
+
+size_t n_params()
+{
+    size_t n = 0;
+    for (int l = 0; l < NL; ++l) n += (size_t)IN[l] * OUT[l] + OUT[l];
+    return n;
+}
+
+// ---- labels: clip(R / D, 0, 2) for schedulable chains, 2 otherwise, -1 for padding
+__global__ void labels_kernel(BatchDev b, const int64_t *R, const uint8_t *status, float *L)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b.n_sys * NCH; i += stride) {
+        const int64_t sys = i / NCH;
+        const int c = (int)(i % NCH);
+        const int64_t c0 = b.sys_chain_off[sys];
+        const int n = (int)(b.sys_chain_off[sys + 1] - c0);
+        float y = -1.0f;
+        if (c < n) {
+            const int64_t g = c0 + c;
+            y = status[g] == PAAM_ST_SCHED ? fminf((float)((double)R[g] / (double)b.D[g]), 2.0f) : 2.0f;
+        }
+        L[i] = y;
+    }
+}
+
+// ---- minibatch gather: rows idx[r] (-1 = padding) of X, L into Xb, XbT, Lb;
+// counts the valid labels into *count
+__global__ void gather_kernel(const __nv_bfloat16 *X, const float *L, const int64_t *idx, int rows,
+                              __nv_bfloat16 *Xb, __nv_bfloat16 *XbT, float *Lb, float *count)
+{
+    const int r = blockIdx.x;
+    if (r >= rows) return;
+    const int64_t src = idx[r];
+    for (int k = threadIdx.x; k < XW; k += blockDim.x) {
+        const __nv_bfloat16 v = src >= 0 ? X[src * XW + k] : __float2bfloat16_rn(0.0f);
+        Xb[(int64_t)r * XW + k] = v;
+        XbT[(int64_t)k * rows + r] = v;
+    }
+    float cnt = 0.0f;
+    for (int c = threadIdx.x; c < NCH; c += blockDim.x) {
+        const float y = src >= 0 ? L[src * NCH + c] : -1.0f;
+        Lb[(int64_t)r * NCH + c] = y;
+        cnt += y >= 0.0f ? 1.0f : 0.0f;
+    }
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if ((threadIdx.x & 31) == 0 && cnt > 0.0f) atomicAdd(count, cnt);
+}
+
+// ---- masked mean-squared error and its gradient
+__global__ void loss_kernel(const float *Y, const float *Lb, int rows, const float *count, __nv_bfloat16 *dY,
+                            __nv_bfloat16 *dYT, float *loss_sum)
+{
+    const float inv = 1.0f / fmaxf(*count, 1.0f);
+    float acc = 0.0f;
+    const int64_t n = (int64_t)rows * NCH;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float y = Lb[i];
+        const float d = y >= 0.0f ? Y[i] - y : 0.0f;
+        acc += d * d;
+        const __nv_bfloat16 g = __float2bfloat16_rn(2.0f * d * inv);
+        const int64_t r = i / NCH, c = i % NCH;
+        dY[i] = g;
+        dYT[c * rows + r] = g;
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, acc * inv);
+}
+
+// ---- bias gradients: row sums of a [rows][cols] bf16 matrix (one block per row)
+__global__ void rowsum_kernel(const __nv_bfloat16 *A, int cols, float *out)
+{
+    __shared__ float part[8];
+    float acc = 0.0f;
+    const __nv_bfloat16 *a = A + (int64_t)blockIdx.x * cols;
+    for (int k = threadIdx.x; k < cols; k += blockDim.x) acc += __bfloat162float(a[k]);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+        out[blockIdx.x] += s;
+    }
+}
+
+// ---- AdamW (decoupled weight decay on weights only); refreshes the bf16 copies
+__global__ void adamw_kernel(float *W, float *m, float *v, float *g, int64_t n, int rows, int cols, float lr,
+                             float b1, float b2, float eps, float wd, float c1, float c2, __nv_bfloat16 *Wb,
+                             __nv_bfloat16 *WbT)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        float w = W[i];
+        w -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w);
+        W[i] = w;
+        g[i] = 0.0f;
+        if (Wb) {
+            const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+            Wb[i] = wb;
+            if (WbT) WbT[(i % cols) * rows + i / cols] = wb;
+        }
+    }
+}
+
+__global__ void to_bf16_kernel(const float *W, int64_t n, int rows, int cols, __nv_bfloat16 *Wb,
+                               __nv_bfloat16 *WbT)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const __nv_bfloat16 wb = __float2bfloat16_rn(W[i]);
+        Wb[i] = wb;
+        if (WbT) WbT[(i % cols) * rows + i / cols] = wb;
+    }
+}
+
+// ---- inference: score = largest predicted R / D over the system's chains
+__global__ void score_kernel(const float *Y, BatchDev b, int64_t sys0, int32_t K, int64_t items, float *score)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items; i += stride) {
+        const int64_t sys = sys0 + i / K;
+        const int n = (int)(b.sys_chain_off[sys + 1] - b.sys_chain_off[sys]);
+        float s = 0.0f;
+        for (int c = 0; c < n && c < NCH; ++c) s = fmaxf(s, Y[i * NCH + c]);
+        score[i] = s;
+    }
+}
+
+// ---- per system: the top_k candidates in increasing score (ties: lower index)
+__global__ void topk_kernel(const float *score, int64_t n_sys, int32_t K, int32_t top_k, int32_t *ranked)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t sys = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (sys >= n_sys) return;
+    const float *s = score + sys * K;
+    int32_t *out = ranked + sys * top_k;
+    // pick repeatedly the smallest (score, index) above the previous pick
+    float last_s = -INFINITY;
+    int last_i = -1;
+    for (int t = 0; t < top_k; ++t) {
+        float best_s = INFINITY;
+        int best_i = 0x7fffffff;
+        for (int k = lane; k < K; k += 32) {
+            const float v = isnan(s[k]) ? INFINITY : s[k];
+            const bool after = v > last_s || (v == last_s && k > last_i);
+            if (after && (v < best_s || (v == best_s && k < best_i))) {
+                best_s = v;
+                best_i = k;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const float os = __shfl_xor_sync(0xffffffffu, best_s, off);
+            const int oi = __shfl_xor_sync(0xffffffffu, best_i, off);
+            if (os < best_s || (os == best_s && oi < best_i)) {
+                best_s = os;
+                best_i = oi;
+            }
+        }
+        if (lane == 0) out[t] = best_i;
+        last_s = best_s;
+        last_i = best_i;
+    }
+}
+
+unsigned grid_for(int64_t n, int threads, int n_sm)
+{
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = 16 * (int64_t)n_sm;
+    if (b > cap) b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// model lifecycle
+// ---------------------------------------------------------------------------
+namespace {
+
+int model_alloc(paam_ctx *ctx, paam_model **out)
+{
+    paam_model *m = (paam_model *)calloc(1, sizeof(paam_model));
+    if (!m) return PAAM_E_NOMEM;
+    m->ctx = ctx;
+    size_t bytes = 0;
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)IN[l] * OUT[l], nb = OUT[l];
+        bytes += 4 * (4 * nw + 4 * nb) + 2 * 2 * nw + 8 * 256;
+    }
+    if (cudaMalloc(&m->block, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        free(m);
+        return PAAM_E_NOMEM;
+    }
+    m->block_bytes = bytes;
+    cudaMemset(m->block, 0, bytes);
+    char *p = (char *)m->block;
+    auto take = [&](size_t n) {
+        char *q = p;
+        p += (n + 255) & ~(size_t)255;
+        return q;
+    };
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)IN[l] * OUT[l], nb = OUT[l];
+        m->W[l] = (float *)take(4 * nw);
+        m->mW[l] = (float *)take(4 * nw);
+        m->vW[l] = (float *)take(4 * nw);
+        m->gW[l] = (float *)take(4 * nw);
+        m->bias[l] = (float *)take(4 * nb);
+        m->mb[l] = (float *)take(4 * nb);
+        m->vb[l] = (float *)take(4 * nb);
+        m->gb[l] = (float *)take(4 * nb);
+        m->Wb[l] = (__nv_bfloat16 *)take(2 * nw);
+        m->WbT[l] = (__nv_bfloat16 *)take(2 * nw);
+    }
+    *out = m;
+    return PAAM_OK;
+}
+
+int refresh_bf16(paam_model *m, cudaStream_t s)
+{
+    for (int l = 0; l < NL; ++l) {
+        const int64_t nw = (int64_t)IN[l] * OUT[l];
+        to_bf16_kernel<<<grid_for(nw, 256, m->ctx->n_sm), 256, 0, s>>>(m->W[l], nw, OUT[l], IN[l], m->Wb[l],
+                                                                       m->WbT[l]);
+        PAAM_CUDA_TRY(cudaGetLastError());
+    }
+    paam_count_launch(NL);
+    return PAAM_OK;
+}
+
+// splitmix64-driven uniform in [-1, 1)
+double unif_pm1(uint64_t *x)
+{
+    uint64_t z = (*x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-52 - 1.0;
+}
+
+} // namespace
+
+extern "C" int paam_model_create(paam_ctx *ctx, uint64_t seed, paam_model **out)
+{
+    if (!ctx || !out) return PAAM_E_INVAL;
+    *out = nullptr;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    paam_model *m = nullptr;
+    int rc = model_alloc(ctx, &m);
+    if (rc != PAAM_OK) return rc;
+    uint64_t x = seed;
+    for (int l = 0; l < NL; ++l) { // uniform(-a, a), a = sqrt(6 / fan_in): keeps GELU activations in range
+        const size_t nw = (size_t)IN[l] * OUT[l];
+        const double a = sqrt(6.0 / IN[l]);
+        std::vector<float> w(nw);
+        for (size_t i = 0; i < nw; ++i) w[i] = (float)(a * unif_pm1(&x));
+        if (cudaMemcpy(m->W[l], w.data(), 4 * nw, cudaMemcpyHostToDevice) != cudaSuccess) rc = PAAM_E_CUDA;
+    }
+    if (rc == PAAM_OK) rc = refresh_bf16(m, 0);
+    if (rc == PAAM_OK && cudaDeviceSynchronize() != cudaSuccess) rc = PAAM_E_CUDA;
+    if (rc != PAAM_OK) {
+        cudaFree(m->block);
+        free(m);
+        return rc;
+    }
+    *out = m;
+    return PAAM_OK;
+}
+
+extern "C" void paam_model_free(paam_model *m)
+{
+    if (!m) return;
+    cudaSetDevice(m->ctx->device);
+    cudaFree(m->block);
+    free(m);
+}
+
+extern "C" int64_t paam_model_num_params(void) { return (int64_t)n_params(); }
+
+// host copy of the fp32 parameters: per layer W [out][in] row-major, then bias [out]
+extern "C" int paam_model_get_params(const paam_model *m, float *host)
+{
+    if (!m || !host) return PAAM_E_INVAL;
+    PAAM_CUDA_TRY(cudaSetDevice(m->ctx->device));
+    size_t o = 0;
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)IN[l] * OUT[l];
+        PAAM_CUDA_TRY(cudaMemcpy(host + o, m->W[l], 4 * nw, cudaMemcpyDeviceToHost));
+        o += nw;
+        PAAM_CUDA_TRY(cudaMemcpy(host + o, m->bias[l], 4 * (size_t)OUT[l], cudaMemcpyDeviceToHost));
+        o += OUT[l];
+    }
+    return PAAM_OK;
+}
+
+extern "C" int paam_model_set_params(paam_model *m, const float *host)
+{
+    if (!m || !host) return PAAM_E_INVAL;
+    PAAM_CUDA_TRY(cudaSetDevice(m->ctx->device));
+    size_t o = 0;
+    for (int l = 0; l < NL; ++l) {
+        const size_t nw = (size_t)IN[l] * OUT[l];
+        PAAM_CUDA_TRY(cudaMemcpy(m->W[l], host + o, 4 * nw, cudaMemcpyHostToDevice));
+        o += nw;
+        PAAM_CUDA_TRY(cudaMemcpy(m->bias[l], host + o, 4 * (size_t)OUT[l], cudaMemcpyHostToDevice));
+        o += OUT[l];
+    }
+    int rc = refresh_bf16(m, 0);
+    if (rc == PAAM_OK && cudaDeviceSynchronize() != cudaSuccess) rc = PAAM_E_CUDA;
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// one minibatch: forward, masked MSE, backward, AdamW
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Work {
+    int rows;
+    void *block;
+    __nv_bfloat16 *Xb, *XbT, *Z[3], *H[3], *HT[3], *dY, *dYT, *dZ[3], *dZT[3];
+    float *Lb, *Y, *count, *loss;
+    int32_t *err;
+};
+
+int work_alloc(Work &w, int rows, bool train, cudaStream_t s)
+{
+    w = Work{};
+    w.rows = rows;
+    const size_t r = (size_t)rows;
+    size_t bytes = 2 * r * XW * (train ? 2 : 1) + 3 * 2 * r * 256 * (train ? 6 : 1) + 4 * r * 64 * (train ? 2 : 1) +
+                   2 * 2 * r * 64 + 64 * 256;
+    if (cudaMallocAsync(&w.block, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PAAM_E_NOMEM;
+    }
+    char *p = (char *)w.block;
+    auto take = [&](size_t n) {
+        char *q = p;
+        p += (n + 255) & ~(size_t)255;
+        return q;
+    };
+    w.Xb = (__nv_bfloat16 *)take(2 * r * XW);
+    if (train) w.XbT = (__nv_bfloat16 *)take(2 * r * XW);
+    for (int l = 0; l < 3; ++l) {
+        w.H[l] = (__nv_bfloat16 *)take(2 * r * 256);
+        if (train) {
+            w.Z[l] = (__nv_bfloat16 *)take(2 * r * 256);
+            w.HT[l] = (__nv_bfloat16 *)take(2 * r * 256);
+            w.dZ[l] = (__nv_bfloat16 *)take(2 * r * 256);
+            w.dZT[l] = (__nv_bfloat16 *)take(2 * r * 256);
+        }
+    }
+    w.Y = (float *)take(4 * r * 64);
+    if (train) {
+        w.Lb = (float *)take(4 * r * 64);
+        w.dY = (__nv_bfloat16 *)take(2 * r * 64);
+        w.dYT = (__nv_bfloat16 *)take(2 * r * 64);
+    }
+    w.count = (float *)take(4);
+    w.loss = (float *)take(4);
+    w.err = (int32_t *)take(4);
+    return PAAM_OK;
+}
+
+TcGemm gemm(const __nv_bfloat16 *A, int lda, int a_rows, const __nv_bfloat16 *B, int ldb, int b_rows, int K)
+{
+    TcGemm g = {};
+    g.A = A;
+    g.lda = lda;
+    g.a_rows = a_rows;
+    g.B = B;
+    g.ldb = ldb;
+    g.b_rows = b_rows;
+    g.K = K;
+    g.splits = 1;
+    return g;
+}
+
+// X (rows of w.Xb) through the network into w.Y; keeps Z, H, H^T when training
+int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, bool train, cudaStream_t s)
+{
+    const int rows = w.rows;
+    for (int l = 0; l < 3; ++l) {
+        TcGemm g = gemm(l == 0 ? X : w.H[l - 1], IN[l], rows, m->Wb[l], IN[l], OUT[l], IN[l]);
+        g.ep.mode = TC_EPI_BIAS_GELU;
+        g.ep.M = rows;
+        g.ep.N = OUT[l];
+        g.ep.bias = m->bias[l];
+        g.ep.Z = train ? w.Z[l] : nullptr;
+        g.ep.ldz = OUT[l];
+        g.ep.H = w.H[l];
+        g.ep.ldh = OUT[l];
+        g.ep.HT = train ? w.HT[l] : nullptr;
+        g.ep.ldht = rows;
+        int rc = tc_gemm(g, w.err, s);
+        if (rc != PAAM_OK) return rc;
+    }
+    TcGemm g = gemm(w.H[2], IN[3], rows, m->Wb[3], IN[3], OUT[3], IN[3]);
+    g.ep.mode = TC_EPI_BIAS_F32;
+    g.ep.M = rows;
+    g.ep.N = OUT[3];
+    g.ep.bias = m->bias[3];
+    g.ep.C = w.Y;
+    g.ep.ldc = OUT[3];
+    return tc_gemm(g, w.err, s);
+}
+
+int splits_for(int tiles, int kb, int n_sm)
+{
+    int sp = (2 * n_sm + tiles - 1) / tiles;
+    if (sp > kb) sp = kb;
+    return sp < 1 ? 1 : sp;
+}
+
+// gradients of the masked MSE into m->gW, m->gb (accumulated)
+int backward(paam_model *m, Work &w, cudaStream_t s)
+{
+    const int rows = w.rows, kb = rows / 64, sm = m->ctx->n_sm;
+    loss_kernel<<<grid_for((int64_t)rows * 64, 256, sm), 256, 0, s>>>(w.Y, w.Lb, rows, w.count, w.dY, w.dYT,
+                                                                       w.loss);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    paam_count_launch();
+    // output layer: dW4 = dY^T H3, db4 = column sums of dY, dH3 = dY W4 (then the GELU derivative)
+    const __nv_bfloat16 *dT = w.dYT; // [OUT[l]][rows]
+    const __nv_bfloat16 *d = w.dY;   // [rows][OUT[l]]
+    for (int l = 3; l >= 0; --l) {
+        const __nv_bfloat16 *inT = l == 0 ? w.XbT : w.HT[l - 1];
+        TcGemm g = gemm(dT, rows, OUT[l], inT, rows, IN[l], rows);
+        g.ep.mode = TC_EPI_ATOMIC_F32;
+        g.ep.M = OUT[l];
+        g.ep.N = IN[l];
+        g.ep.C = m->gW[l];
+        g.ep.ldc = IN[l];
+        const int tiles = ((OUT[l] + 127) / 128) * (IN[l] % 256 == 0 ? IN[l] / 256 : IN[l] / 64);
+        g.splits = splits_for(tiles, kb, sm);
+        int rc = tc_gemm(g, w.err, s);
+        if (rc != PAAM_OK) return rc;
+        rowsum_kernel<<<OUT[l], 256, 0, s>>>(dT, rows, m->gb[l]);
+        PAAM_CUDA_TRY(cudaGetLastError());
+        paam_count_launch();
+        if (l == 0) break;
+        TcGemm h = gemm(d, OUT[l], rows, m->WbT[l], OUT[l], IN[l], OUT[l]);
+        h.ep.mode = TC_EPI_DGELU;
+        h.ep.M = rows;
+        h.ep.N = IN[l];
+        h.ep.Zin = w.Z[l - 1];
+        h.ep.ldzin = IN[l];
+        h.ep.H = w.dZ[l - 1];
+        h.ep.ldh = IN[l];
+        h.ep.HT = w.dZT[l - 1];
+        h.ep.ldht = rows;
+        rc = tc_gemm(h, w.err, s);
+        if (rc != PAAM_OK) return rc;
+        dT = w.dZT[l - 1];
+        d = w.dZ[l - 1];
+    }
+    return PAAM_OK;
+}
+
+int adamw(paam_model *m, const paam_train_opts *o, cudaStream_t s)
+{
+    m->step += 1;
+    const float c1 = 1.0f - powf(o->beta1, (float)m->step), c2 = 1.0f - powf(o->beta2, (float)m->step);
+    for (int l = 0; l < NL; ++l) {
+        const int64_t nw = (int64_t)IN[l] * OUT[l];
+        adamw_kernel<<<grid_for(nw, 256, m->ctx->n_sm), 256, 0, s>>>(
+            m->W[l], m->mW[l], m->vW[l], m->gW[l], nw, OUT[l], IN[l], o->lr, o->beta1, o->beta2, o->adam_eps,
+            o->weight_decay, c1, c2, m->Wb[l], m->WbT[l]);
+        adamw_kernel<<<1, 256, 0, s>>>(m->bias[l], m->mb[l], m->vb[l], m->gb[l], OUT[l], 1, OUT[l], o->lr, o->beta1,
+                                       o->beta2, o->adam_eps, 0.0f, c1, c2, nullptr, nullptr);
+        PAAM_CUDA_TRY(cudaGetLastError());
+    }
+    paam_count_launch(2 * NL);
+    return PAAM_OK;
+}
+
+int check_train_opts(const paam_train_opts *o)
+{
+    if (!o || o->epochs < 0 || o->batch_rows < 128 || o->batch_rows % 128 || o->n_buckets < 1 || o->kappa_ns < 0 ||
+        o->kappa_ns > PAAM_MAX_OVERHEAD || !(o->lr > 0.0f) || !(o->beta1 >= 0.0f && o->beta1 < 1.0f) ||
+        !(o->beta2 >= 0.0f && o->beta2 < 1.0f) || !(o->adam_eps > 0.0f) || !(o->weight_decay >= 0.0f))
+        return PAAM_E_INVAL;
+    return PAAM_OK;
+}
+
+} // namespace
+
+extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const int64_t *R, const uint8_t *status,
+                                    const paam_train_opts *o, paam_model **model)
+{
+    if (!ctx || !b || !model || (b->n_chain > 0 && (!R || !status))) return PAAM_E_INVAL;
+    if (b->ctx != ctx) return PAAM_E_STATE;
+    int rc = check_train_opts(o);
+    if (rc != PAAM_OK) return rc;
+    if (b->max_chains > NCH) return PAAM_E_UNSUPPORTED;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    bool created = false;
+    if (!*model) {
+        rc = paam_model_create(ctx, o->seed, model);
+        if (rc != PAAM_OK) return rc;
+        created = true;
+    } else if ((*model)->ctx != ctx) {
+        return PAAM_E_STATE;
+    }
+    paam_model *m = *model;
+    cudaStream_t s = ctx->capture_stream;
+    const int64_t n = b->n_sys;
+    const int rows = o->batch_rows;
+    const int64_t steps = (n + rows - 1) / rows;
+    void *data = nullptr;
+    Work w;
+    if (cudaMallocAsync(&data, (size_t)n * (2 * XW + 4 * NCH) + 8 * (size_t)steps * rows + 1024, s) != cudaSuccess) {
+        cudaGetLastError();
+        rc = PAAM_E_NOMEM;
+    }
+    if (rc == PAAM_OK) rc = work_alloc(w, rows, true, s);
+    __nv_bfloat16 *X = (__nv_bfloat16 *)data;
+    float *L = (float *)((char *)data + (size_t)n * 2 * XW);
+    int64_t *idx_dev = (int64_t *)((char *)L + (size_t)n * 4 * NCH);
+    if (rc == PAAM_OK) rc = paam_launch_features(b, nullptr, 1, 0, 0, n, o->n_buckets, o->kappa_ns, X, s);
+    if (rc == PAAM_OK) {
+        labels_kernel<<<grid_for(n * NCH, 256, ctx->n_sm), 256, 0, s>>>(batch_dev(b), R, status, L);
+        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        paam_count_launch();
+        if (cudaMemsetAsync(w.err, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
+    }
+    std::vector<int64_t> idx((size_t)(steps * rows));
+    uint64_t rng = o->seed ^ 0x5DEECE66DULL ^ (uint64_t)m->step;
+    for (int e = 0; e < o->epochs && rc == PAAM_OK; ++e) {
+        // minibatch order: a fresh permutation of the systems, padded with -1
+        for (int64_t i = 0; i < (int64_t)idx.size(); ++i) idx[i] = i < n ? i : -1;
+        for (int64_t i = n - 1; i > 0; --i) {
+            const int64_t j = (int64_t)((unif_pm1(&rng) * 0.5 + 0.5) * (double)(i + 1)) % (i + 1);
+            const int64_t t = idx[i];
+            idx[i] = idx[j];
+            idx[j] = t;
+        }
+        if (cudaMemcpyAsync(idx_dev, idx.data(), 8 * idx.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(w.loss, 0, 4, s) != cudaSuccess)
+            rc = PAAM_E_CUDA;
+        for (int64_t st = 0; st < steps && rc == PAAM_OK; ++st) {
+            if (cudaMemsetAsync(w.count, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
+            gather_kernel<<<rows, 128, 0, s>>>(X, L, idx_dev + st * rows, rows, w.Xb, w.XbT, w.Lb, w.count);
+            if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+            paam_count_launch();
+            if (rc == PAAM_OK) rc = forward(m, w, w.Xb, true, s);
+            if (rc == PAAM_OK) rc = backward(m, w, s);
+            if (rc == PAAM_OK) rc = adamw(m, o, s);
+        }
+        float loss = 0.0f;
+        if (rc == PAAM_OK && (cudaMemcpyAsync(&loss, w.loss, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                              cudaStreamSynchronize(s) != cudaSuccess))
+            rc = PAAM_E_CUDA;
+        if (rc == PAAM_OK && o->epoch_loss) o->epoch_loss[e] = loss / (float)steps;
+    }
+    int32_t herr = 0;
+    if (w.block) cudaMemcpyAsync(&herr, w.err, 4, cudaMemcpyDeviceToHost, s);
+    if (w.block) cudaFreeAsync(w.block, s);
+    if (data) cudaFreeAsync(data, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == PAAM_OK) rc = PAAM_E_CUDA;
+    if (rc == PAAM_OK && herr != 0) rc = herr;
+    if (rc != PAAM_OK && created) {
+        paam_model_free(m);
+        *model = nullptr;
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// inference
+// ---------------------------------------------------------------------------
+extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const paam_batch *b, const int16_t *ranks,
+                                    int32_t K, int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t top_k,
+                                    int32_t *ranked, float *scores, void *stream_)
+{
+    if (!ctx || !m || !b || (b->n_sys > 0 && (!ranks || !ranked))) return PAAM_E_INVAL;
+    if (m->ctx != ctx || b->ctx != ctx) return PAAM_E_STATE;
+    if (K < 1 || top_k < 1 || top_k > K || nmax < b->max_chains || n_buckets < 1 || kappa_ns < 0 ||
+        kappa_ns > PAAM_MAX_OVERHEAD)
+        return PAAM_E_INVAL;
+    if (b->max_chains > NCH) return PAAM_E_UNSUPPORTED;
+    if (b->n_sys == 0) return PAAM_OK;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream_;
+    // candidates are scored in chunks of whole systems, at most ~256k rows at a time
+    int64_t chunk = (262144 + K - 1) / K;
+    if (chunk > b->n_sys) chunk = b->n_sys;
+    const int rows = (int)(chunk * K);
+    Work w;
+    int rc = work_alloc(w, rows, false, s);
+    if (rc != PAAM_OK) return rc;
+    float *sc = scores;
+    void *tmp = nullptr;
+    if (!sc) {
+        if (cudaMallocAsync(&tmp, 4 * (size_t)b->n_sys * K, s) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeAsync(w.block, s);
+            return PAAM_E_NOMEM;
+        }
+        sc = (float *)tmp;
+    }
+    if (cudaMemsetAsync(w.err, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
+    for (int64_t s0 = 0; s0 < b->n_sys && rc == PAAM_OK; s0 += chunk) {
+        const int64_t ns = (s0 + chunk <= b->n_sys) ? chunk : b->n_sys - s0;
+        const int64_t items = ns * K;
+        Work wc = w;
+        wc.rows = (int)items;
+        rc = paam_launch_features(b, ranks, K, nmax, s0, items, n_buckets, kappa_ns, wc.Xb, s);
+        if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, false, s);
+        if (rc == PAAM_OK) {
+            score_kernel<<<grid_for(items, 256, ctx->n_sm), 256, 0, s>>>(wc.Y, batch_dev(b), s0, K, items,
+                                                                         sc + s0 * K);
+            if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+            paam_count_launch();
+        }
+    }
+    if (rc == PAAM_OK) {
+        topk_kernel<<<(unsigned)((b->n_sys + 7) / 8), 256, 0, s>>>(sc, b->n_sys, K, top_k, ranked);
+        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        paam_count_launch();
+    }
+    int32_t herr = 0;
+    if (cudaMemcpyAsync(&herr, w.err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = PAAM_E_CUDA;
+    cudaFreeAsync(w.block, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = PAAM_E_CUDA;
+    if (rc == PAAM_OK && herr != 0) rc = herr;
+    return rc;
+}
+
+extern "C" int paam_surrogate_predict(paam_ctx *ctx, const paam_model *m, const paam_batch *b, int32_t n_buckets,
+                                      int64_t kappa_ns, float *pred, void *stream_)
+{
+    if (!ctx || !m || !b || (b->n_sys > 0 && !pred)) return PAAM_E_INVAL;
+    if (m->ctx != ctx || b->ctx != ctx) return PAAM_E_STATE;
+    if (n_buckets < 1 || kappa_ns < 0 || kappa_ns > PAAM_MAX_OVERHEAD) return PAAM_E_INVAL;
+    if (b->max_chains > NCH) return PAAM_E_UNSUPPORTED;
+    if (b->n_sys == 0) return PAAM_OK;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream_;
+    const int64_t chunk = b->n_sys < 262144 ? b->n_sys : 262144;
+    Work w;
+    int rc = work_alloc(w, (int)chunk, false, s);
+    if (rc != PAAM_OK) return rc;
+    if (cudaMemsetAsync(w.err, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
+    for (int64_t s0 = 0; s0 < b->n_sys && rc == PAAM_OK; s0 += chunk) {
+        Work wc = w;
+        wc.rows = (int)((s0 + chunk <= b->n_sys) ? chunk : b->n_sys - s0);
+        wc.Y = pred + s0 * NCH;
+        rc = paam_launch_features(b, nullptr, 1, 0, s0, wc.rows, n_buckets, kappa_ns, wc.Xb, s);
+        if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, false, s);
+    }
+    int32_t herr = 0;
+    if (cudaMemcpyAsync(&herr, w.err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = PAAM_E_CUDA;
+    cudaFreeAsync(w.block, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = PAAM_E_CUDA;
+    if (rc == PAAM_OK && herr != 0) rc = herr;
+    return rc;
+}
+
+// Loss and gradients of one minibatch (rows a multiple of 128), no update.
+extern "C" int paam_surrogate_grad(paam_ctx *ctx, paam_model *m, const void *X, const float *L, int32_t rows,
+                                   float *grads_host, float *loss_host)
+{
+    if (!ctx || !m || !X || !L || !grads_host || rows < 128 || rows % 128) return PAAM_E_INVAL;
+    if (m->ctx != ctx) return PAAM_E_STATE;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->capture_stream;
+    Work w;
+    int rc = work_alloc(w, rows, true, s);
+    if (rc != PAAM_OK) return rc;
+    int64_t *idx = nullptr;
+    if (cudaMallocAsync((void **)&idx, 8 * (size_t)rows, s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(w.block, s);
+        return PAAM_E_NOMEM;
+    }
+    std::vector<int64_t> id(rows);
+    for (int i = 0; i < rows; ++i) id[i] = i;
+    if (cudaMemcpyAsync(idx, id.data(), 8 * (size_t)rows, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(w.err, 0, 4, s) != cudaSuccess || cudaMemsetAsync(w.count, 0, 4, s) != cudaSuccess ||
+        cudaMemsetAsync(w.loss, 0, 4, s) != cudaSuccess)
+        rc = PAAM_E_CUDA;
+    for (int l = 0; l < NL && rc == PAAM_OK; ++l)
+        if (cudaMemsetAsync(m->gW[l], 0, 4 * (size_t)IN[l] * OUT[l], s) != cudaSuccess ||
+            cudaMemsetAsync(m->gb[l], 0, 4 * (size_t)OUT[l], s) != cudaSuccess)
+            rc = PAAM_E_CUDA;
+    if (rc == PAAM_OK) {
+        gather_kernel<<<rows, 128, 0, s>>>((const __nv_bfloat16 *)X, L, idx, rows, w.Xb, w.XbT, w.Lb, w.count);
+        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        paam_count_launch();
+    }
+    if (rc == PAAM_OK) rc = forward(m, w, w.Xb, true, s);
+    if (rc == PAAM_OK) rc = backward(m, w, s);
+    size_t o = 0;
+    for (int l = 0; l < NL && rc == PAAM_OK; ++l) {
+        const size_t nw = (size_t)IN[l] * OUT[l];
+        if (cudaMemcpyAsync(grads_host + o, m->gW[l], 4 * nw, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = PAAM_E_CUDA;
+        o += nw;
+        if (cudaMemcpyAsync(grads_host + o, m->gb[l], 4 * (size_t)OUT[l], cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            rc = PAAM_E_CUDA;
+        o += OUT[l];
+    }
+    float loss = 0.0f;
+    int32_t herr = 0;
+    cudaMemcpyAsync(&loss, w.loss, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&herr, w.err, 4, cudaMemcpyDeviceToHost, s);
+    for (int l = 0; l < NL; ++l) { // leave no gradient behind for a later training step
+        cudaMemsetAsync(m->gW[l], 0, 4 * (size_t)IN[l] * OUT[l], s);
+        cudaMemsetAsync(m->gb[l], 0, 4 * (size_t)OUT[l], s);
+    }
+    cudaFreeAsync(idx, s);
+    cudaFreeAsync(w.block, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = PAAM_E_CUDA;
+    if (rc == PAAM_OK && herr != 0) rc = herr;
+    if (loss_host) *loss_host = loss;
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoints: magic, version, step, parameter count, then per layer the fp32
+// weights, biases and both AdamW moments
+// ---------------------------------------------------------------------------
+extern "C" int paam_model_save(const paam_model *m, const char *path)
+{
+    if (!m || !path) return PAAM_E_INVAL;
+    PAAM_CUDA_TRY(cudaSetDevice(m->ctx->device));
+    FILE *f = fopen(path, "wb");
+    if (!f) return PAAM_E_INVAL;
+    const char magic[8] = {'P', 'A', 'A', 'M', 'S', 'U', 'R', '1'};
+    const int64_t hdr[2] = {m->step, (int64_t)n_params()};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, 8, 2, f) == 2;
+    for (int l = 0; l < NL && ok; ++l) {
+        const size_t nw = (size_t)IN[l] * OUT[l], nb = OUT[l];
+        const float *parts[6] = {m->W[l], m->bias[l], m->mW[l], m->vW[l], m->mb[l], m->vb[l]};
+        const size_t sizes[6] = {nw, nb, nw, nw, nb, nb};
+        for (int k = 0; k < 6 && ok; ++k) {
+            std::vector<float> h(sizes[k]);
+            ok = cudaMemcpy(h.data(), parts[k], 4 * sizes[k], cudaMemcpyDeviceToHost) == cudaSuccess &&
+                 fwrite(h.data(), 4, sizes[k], f) == sizes[k];
+        }
+    }
+    ok = (fclose(f) == 0) && ok;
+    return ok ? PAAM_OK : PAAM_E_CUDA;
+}
+
+extern "C" int paam_model_load(paam_ctx *ctx, const char *path, paam_model **out)
+{
+    if (!ctx || !path || !out) return PAAM_E_INVAL;
+    *out = nullptr;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    FILE *f = fopen(path, "rb");
+    if (!f) return PAAM_E_INVAL;
+    char magic[8];
+    int64_t hdr[2];
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "PAAMSUR1", 8) == 0 && fread(hdr, 8, 2, f) == 2 &&
+              hdr[1] == (int64_t)n_params();
+    paam_model *m = nullptr;
+    if (ok && model_alloc(ctx, &m) != PAAM_OK) ok = false;
+    for (int l = 0; l < NL && ok; ++l) {
+        const size_t nw = (size_t)IN[l] * OUT[l], nb = OUT[l];
+        float *parts[6] = {m->W[l], m->bias[l], m->mW[l], m->vW[l], m->mb[l], m->vb[l]};
+        const size_t sizes[6] = {nw, nb, nw, nw, nb, nb};
+        for (int k = 0; k < 6 && ok; ++k) {
+            std::vector<float> h(sizes[k]);
+            ok = fread(h.data(), 4, sizes[k], f) == sizes[k] &&
+                 cudaMemcpy(parts[k], h.data(), 4 * sizes[k], cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+    }
+    fclose(f);
+    if (ok) {
+        m->step = hdr[0];
+        ok = refresh_bf16(m, 0) == PAAM_OK && cudaDeviceSynchronize() == cudaSuccess;
+    }
+    if (!ok) {
+        if (m) paam_model_free(m);
+        return PAAM_E_INVAL;
+    }
+    *out = m;
+    return PAAM_OK;
+}
+
+// Surrogate input features of every (system, candidate) into X ([n_sys * K][1024] bf16, device);
+// ranks NULL (K = 1) takes the systems' own priorities.
+extern "C" int paam_surrogate_features(paam_ctx *ctx, const paam_batch *b, const int16_t *ranks, int32_t K,
+                                       int32_t nmax, int32_t n_buckets, int64_t kappa_ns, void *X, void *stream)
+{
+    if (!ctx || !b || (b->n_sys > 0 && !X) || n_buckets < 1 || kappa_ns < 0 || kappa_ns > PAAM_MAX_OVERHEAD)
+        return PAAM_E_INVAL;
+    if (b->ctx != ctx) return PAAM_E_STATE;
+    if (b->max_chains > NCH) return PAAM_E_UNSUPPORTED;
+    if (ranks ? (K < 1 || nmax < b->max_chains) : K != 1) return PAAM_E_INVAL;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    return paam_launch_features(b, ranks, K, nmax, 0, b->n_sys * (int64_t)K, n_buckets, kappa_ns,
+                                (__nv_bfloat16 *)X, (cudaStream_t)stream);
+}

@@ -69,3 +69,44 @@ def test_search_rejects_non_permutation():
     with pytest.raises(pkg.PaamError) as ei:
         _run(sy, ranks)
     assert ei.value.code == -1
+
+
+def test_ordered_search_subset():
+    """Visiting a permuted subset of candidates admits exactly those the full
+    search admits among them; first_ok is the first admitted in visit order."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    sy = g.generate("cfg4s", n_sys=800)
+    Kc, K = 64, 20
+    ranks = g.candidate_ranks(sy, Kc, 21)
+    ref = oracle.search(sy, ranks, threads=8)
+    rng = np.random.default_rng(3)
+    order = np.stack([rng.permutation(Kc)[:K] for _ in range(sy.n_sys)]).astype(np.int32)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    r = torch.from_numpy(ranks).cuda()
+    o = torch.from_numpy(order).cuda()
+    for early in (False, True):
+        first = torch.empty(sy.n_sys, dtype=torch.int32, device="cuda")
+        cand = torch.empty((sy.n_sys, Kc), dtype=torch.uint8, device="cuda")
+        pkg.paam_rta_search_ordered(ctx(), b, pkg.analysis_opts(), r, o, early, cand, first)
+        torch.cuda.synchronize()
+        first, cand = first.cpu().numpy(), cand.cpu().numpy()
+        want_first = np.full(sy.n_sys, -1)
+        for s in range(sy.n_sys):
+            ok = [k for k in order[s] if ref["cand_ok"][s, k]]
+            want_first[s] = ok[0] if ok else -1
+        assert np.array_equal(first, want_first)
+        visited = np.zeros_like(ref["cand_ok"])
+        np.put_along_axis(visited, order.astype(np.int64), 1, axis=1)
+        if not early:
+            assert np.array_equal(cand, ref["cand_ok"] & visited)
+        else:
+            assert np.all(cand <= (ref["cand_ok"] & visited))
+    bad = o.clone()
+    bad[3, 2] = Kc
+    with pytest.raises(pkg.PaamError):
+        pkg.paam_rta_search_ordered(ctx(), b, pkg.analysis_opts(), r, bad, False, None,
+                                    torch.empty(sy.n_sys, dtype=torch.int32, device="cuda"))
+    b.free()

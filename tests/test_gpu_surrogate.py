@@ -1,0 +1,191 @@
+"""The surrogate network's GPU kernels against float64 oracles, and what the
+trained network does for the priority search.
+
+Tolerances: features are fp32 ratios stored as bf16 (relative 2^-8); the
+network runs bf16 weights and activations with fp32 accumulation through four
+layers, so gradients are compared in relative L2 norm within 3e-2."""
+import numpy as np
+import pytest
+
+import oracle
+import paam_gen as g
+from oracle import features as ofeat
+from oracle import mlp
+
+from gpu_util import ctx
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16_to_f64(t):
+    import torch
+
+    return t.to(torch.float32).cpu().numpy().astype(np.float64)
+
+
+def _features(sy, ranks=None, n_buckets=1, kappa=0):
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    K = 1 if ranks is None else ranks.shape[1]
+    X = torch.empty((sy.n_sys * K, 1024), dtype=torch.bfloat16, device="cuda")
+    r = None if ranks is None else torch.from_numpy(ranks).cuda()
+    pkg.paam_surrogate_features(ctx(), b, X, ranks=r, n_buckets=n_buckets, kappa=kappa)
+    torch.cuda.synchronize()
+    b.free()
+    return _bf16_to_f64(X)
+
+
+def test_features_match_oracle():
+    sy = g.generate("cfg3", n_sys=150)
+    got = _features(sy, n_buckets=2, kappa=30_000)
+    ref = ofeat.features(sy, n_buckets=2, kappa=30_000)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 2e-3)
+    assert np.all(got[ref == 0] == 0)
+    sy4 = g.generate("cfg4s", n_sys=40)
+    ranks = g.candidate_ranks(sy4, 6, 4)
+    got = _features(sy4, ranks)
+    ref = ofeat.features(sy4, ranks)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 2e-3)
+
+
+def _random_params(seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for fin, fout in mlp.SIZES:
+        out.append(rng.uniform(-1, 1, fin * fout) * np.sqrt(6.0 / fin))
+        out.append(rng.uniform(-0.1, 0.1, fout))
+    return np.concatenate(out).astype(np.float32)
+
+
+def test_gradients_match_oracle():
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    p = _random_params(5)
+    m = pkg.Model.create(ctx(), 1)
+    m.set_params(p)
+    rng = np.random.default_rng(6)
+    rows = 256
+    X = torch.from_numpy(rng.uniform(0, 1.5, (rows, 1024)).astype(np.float32)).to(torch.bfloat16)
+    L = rng.uniform(0, 2, (rows, 64)).astype(np.float32)
+    L[rng.uniform(size=L.shape) < 0.3] = -1.0
+    grads, loss = pkg.paam_surrogate_grad(ctx(), m, X.cuda(), torch.from_numpy(L).cuda())
+    # the oracle sees the same bf16 inputs and the fp32 parameters
+    ref_loss, ref = mlp.loss_and_grad(p.astype(np.float64), X.to(torch.float32).numpy().astype(np.float64), L)
+    assert abs(loss - ref_loss) <= 1e-2 * ref_loss
+    o = 0
+    for fin, fout in mlp.SIZES:
+        for size in (fin * fout, fout):
+            a, b = grads[o:o + size].astype(np.float64), ref[o:o + size]
+            assert np.linalg.norm(a - b) <= 3e-2 * np.linalg.norm(b) + 1e-7, (o, np.linalg.norm(a - b) / np.linalg.norm(b))
+            o += size
+    m.free()
+
+
+def _trained_model(cfg="cfg4s", n_sys=20000, epochs=6, seed=1):
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    sy = g.generate(cfg, n_sys=n_sys, seed=12345)
+    # vary the priority orders the network sees: random permutations per system
+    rng = np.random.default_rng(seed)
+    for s in range(sy.n_sys):
+        c0, c1 = sy.sys_chain_off[s], sy.sys_chain_off[s + 1]
+        sy.prio[c0:c1] = rng.permutation(c1 - c0)
+    sy.exec_prio = None
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    R, st, _ = pkg.analyze(ctx(), b)
+    losses = np.zeros(epochs, np.float32)
+    m = pkg.paam_surrogate_train(ctx(), b, R, st, pkg.train_opts(epochs=epochs, batch_rows=2048, lr=2e-3, seed=seed,
+                                                                    epoch_loss=losses))
+    torch.cuda.synchronize()
+    return m, b, sy, R, st, losses
+
+
+def test_training_reduces_loss_and_predicts():
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    m, b, sy, R, st, losses = _trained_model()
+    assert np.all(np.isfinite(losses)) and losses[-1] < 0.6 * losses[0], losses
+    pred = torch.empty((sy.n_sys, 64), dtype=torch.float32, device="cuda")
+    pkg.paam_surrogate_predict(ctx(), m, b, pred)
+    torch.cuda.synchronize()
+    Rn, stn, D = R.cpu().numpy(), st.cpu().numpy(), sy.D
+    y = np.where(stn == 0, np.minimum(Rn / D, 2.0), 2.0)
+    n = sy.chains_per_system()
+    p = pred.cpu().numpy()[np.repeat(np.arange(sy.n_sys), n), np.arange(sy.n_chain) - np.repeat(sy.sys_chain_off[:-1], n)]
+    mae = np.abs(p - y).mean()
+    assert mae < 0.7 * np.abs(y - y.mean()).mean(), mae
+    m.free()
+    b.free()
+
+
+def test_infer_ranks_by_score_and_guided_search_is_exact():
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    m, btrain, *_ = _trained_model()
+    btrain.free()
+    sy = g.generate("cfg4s", n_sys=400)
+    K, top = 64, 8
+    ranks = g.candidate_ranks(sy, K, 9)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    r = torch.from_numpy(ranks).cuda()
+    ranked = torch.empty((sy.n_sys, top), dtype=torch.int32, device="cuda")
+    scores = torch.empty((sy.n_sys, K), dtype=torch.float32, device="cuda")
+    pkg.paam_surrogate_infer(ctx(), m, b, r, top, ranked, scores)
+    torch.cuda.synchronize()
+    sc = scores.cpu().numpy()
+    want = np.argsort(sc, axis=1, kind="stable")[:, :top]
+    assert np.array_equal(ranked.cpu().numpy(), want)
+    # guided search: confirm the top candidates exactly
+    first = torch.empty(sy.n_sys, dtype=torch.int32, device="cuda")
+    cand = torch.empty((sy.n_sys, K), dtype=torch.uint8, device="cuda")
+    pkg.paam_rta_search_ordered(ctx(), b, pkg.analysis_opts(), r, ranked, False, cand, first)
+    torch.cuda.synchronize()
+    ex = oracle.search(sy, ranks, threads=8)
+    guided_ok = cand.cpu().numpy()
+    assert not np.any(guided_ok & (ex["cand_ok"] == 0))  # zero false accepts
+    found = (first.cpu().numpy() >= 0)
+    has = ex["first_ok"] >= 0
+    assert not np.any(found & ~has)
+    recall = found[has].mean()
+    # the same budget spent on a random order of the candidates
+    rng = np.random.default_rng(2)
+    rand_order = np.stack([rng.permutation(K)[:top] for _ in range(sy.n_sys)])
+    rand_found = np.array([ex["cand_ok"][s, rand_order[s]].any() for s in range(sy.n_sys)])
+    assert recall >= rand_found[has].mean(), (recall, rand_found[has].mean())
+    m.free()
+    b.free()
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    m = pkg.Model.create(ctx(), 3)
+    m.set_params(_random_params(8))
+    path = str(tmp_path / "model.bin")
+    m.save(path)
+    m2 = pkg.Model.load(ctx(), path)
+    assert np.array_equal(m.get_params(), m2.get_params())
+    sy = g.generate("cfg2", n_sys=300)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    p1 = torch.empty((sy.n_sys, 64), dtype=torch.float32, device="cuda")
+    p2 = torch.empty_like(p1)
+    pkg.paam_surrogate_predict(ctx(), m, b, p1)
+    pkg.paam_surrogate_predict(ctx(), m2, b, p2)
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2)
+    m.free()
+    m2.free()
+    b.free()
