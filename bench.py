@@ -39,6 +39,14 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-sys", type=int, default=None, help="override the workload size (testing)")
+    ap.add_argument("--no-search", action="store_true", help="skip the priority-search measurements")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurements")
+    ap.add_argument("--search-sys", type=int, default=10_000)
+    ap.add_argument("--train-sys", type=int, default=10_000_000, help="systems the surrogate trains on")
+    ap.add_argument("--top-k", type=int, default=16)
+    ap.add_argument("--gemm", type=int, nargs=3, default=None, metavar=("M", "N", "K"),
+                    help="time only the tensor-core GEMM C[M,N] = A[M,K] B[N,K]^T")
+    ap.add_argument("--launch-config", type=int, default=None, help="fixed launch configuration (no autotune)")
     return ap.parse_args()
 
 
@@ -108,6 +116,10 @@ def peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
 
 
+# launch configurations whose main kernel is the register-table family
+REG_CONFIGS = {0, 3, 4, 5, 6, 7, 10, 11}
+
+
 def algorithmic_bytes(sy) -> int:
     """Bytes one analysis must move: every input table read once (the
     accelerator index is not kept: one accelerator) plus R, status, verdict."""
@@ -167,6 +179,223 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# priority search (256 candidate orders per system) and the surrogate
+# ---------------------------------------------------------------------------
+SEARCH_K = 256
+
+
+def _timed(fn, reps=1):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps, out
+
+
+def search_bench(pkg, ctx, n_sys):
+    """Exhaustive and early-exit exact search on the specified search workload
+    (cfg4) and on its sparse-executor variant (cfg4s)."""
+    import torch
+
+    import paam_gen
+
+    out = {}
+    for cfg in ("cfg4", "cfg4s"):
+        sy = paam_gen.generate(cfg, n_sys=n_sys)
+        ranks = paam_gen.candidate_ranks(sy, SEARCH_K, paam_gen.CONFIGS[cfg]["seed"] + 7)
+        b = pkg.paam_rta_load_systems(ctx, sy)
+        r = torch.from_numpy(ranks).cuda()
+        pkg.search(ctx, b, r)  # warm-up
+        t_x, (first, cand) = _timed(lambda: pkg.search(ctx, b, r), 3)
+        t_e, (first_e, _) = _timed(lambda: pkg.search(ctx, b, r, stop_at_first=True, want_cand_ok=False), 3)
+        cand_np = cand.cpu().numpy()
+        assert np.array_equal(first.cpu().numpy(), first_e.cpu().numpy())
+        out[cfg] = {
+            "systems": sy.n_sys, "candidates_per_system": SEARCH_K,
+            "exhaustive_systems_per_s": sy.n_sys / t_x, "exhaustive_ms": t_x * 1e3,
+            "early_exit_systems_per_s": sy.n_sys / t_e, "early_exit_ms": t_e * 1e3,
+            "candidate_analyses_per_s": sy.n_sys * SEARCH_K / t_x,
+            "systems_with_schedulable_order": float((first.cpu().numpy() >= 0).mean()),
+            "schedulable_candidates": float(cand_np.mean()),
+        }
+        b.free()
+    return out
+
+
+def _random_orders(sy, seed):
+    """The systems' priorities replaced by seeded random permutations (CAPA executor priorities)."""
+    rng = np.random.default_rng(seed)
+    n = sy.chains_per_system()
+    keys = rng.random(sy.n_chain) + np.repeat(np.arange(sy.n_sys), n)  # sort within each system
+    order = np.argsort(keys, kind="stable")
+    local = np.empty(sy.n_chain, np.int64)
+    local[order] = np.arange(sy.n_chain) - np.repeat(sy.sys_chain_off[:-1], n)
+    sy.prio = local.astype(np.int32)
+    sy.exec_prio = None
+    return sy
+
+
+def surrogate_bench(pkg, ctx, train_sys, n_search, top_k):
+    """Train the ranking network on exactly analysed systems, then compare the
+    guided search (network ranking + exact confirmation of the top-k) with the
+    exhaustive exact search on the same candidates."""
+    import torch
+
+    import paam_gen
+
+    flops_row = 2.0 * (1024 * 256 + 256 * 256 + 256 * 256 + 256 * 64)  # one forward pass, one row
+    sources = ("cfg2", "cfg3", "cfg4s")
+    chunk = 1_000_000
+    model, t_train, t_label, losses, rows = None, 0.0, 0.0, [], 0
+    for i, lo in enumerate(range(0, train_sys, chunk)):
+        n = min(chunk, train_sys - lo)
+        cfg = sources[i % len(sources)]
+        sy = paam_gen.generate(cfg, n_sys=n, seed=paam_gen.CONFIGS[cfg]["seed"] + 1000 + i)
+        if cfg == "cfg4s":
+            sy = _random_orders(sy, i)
+        b = pkg.paam_rta_load_systems(ctx, sy)
+        dt, (R, st, _) = _timed(lambda: pkg.analyze(ctx, b))
+        t_label += dt
+        loss = np.zeros(1, np.float32)
+        opts = pkg.train_opts(epochs=1, batch_rows=8192, lr=1e-3, seed=i, epoch_loss=loss)
+        dt, model = _timed(lambda: pkg.paam_surrogate_train(ctx, b, R, st, opts, model))
+        t_train += dt
+        losses.append(round(float(loss[0]), 5))
+        rows += n
+        b.free()
+    # held-out error of the predicted R/D on each training source
+    mae = {}
+    for cfg in sources:
+        sy = paam_gen.generate(cfg, n_sys=50_000, seed=paam_gen.CONFIGS[cfg]["seed"] + 999)
+        if cfg == "cfg4s":
+            sy = _random_orders(sy, 999)
+        b = pkg.paam_rta_load_systems(ctx, sy)
+        R, st, _ = pkg.analyze(ctx, b)
+        pred = torch.empty((sy.n_sys, 64), dtype=torch.float32, device="cuda")
+        pkg.paam_surrogate_predict(ctx, model, b, pred)
+        torch.cuda.synchronize()
+        Rn, stn = R.cpu().numpy(), st.cpu().numpy()
+        y = np.where(stn == 0, np.minimum(np.maximum(Rn, 0) / sy.D, 2.0), 2.0)
+        n = sy.chains_per_system()
+        sysid = np.repeat(np.arange(sy.n_sys), n)
+        p = pred.cpu().numpy()[sysid, np.arange(sy.n_chain) - sy.sys_chain_off[sysid]]
+        mae[cfg] = round(float(np.abs(p - y).mean()), 5)
+        b.free()
+
+    # the search workload: SEARCH_K candidate orders per system
+    K = SEARCH_K
+    sy = paam_gen.generate("cfg4s", n_sys=n_search)
+    ranks = paam_gen.candidate_ranks(sy, K, paam_gen.CONFIGS["cfg4s"]["seed"] + 7)
+    b = pkg.paam_rta_load_systems(ctx, sy)
+    r = torch.from_numpy(ranks).cuda()
+    opts = pkg.analysis_opts()
+    pkg.search(ctx, b, r)
+    t_ex, (first_x, cand_x) = _timed(lambda: pkg.search(ctx, b, r), 3)
+    t_ee, _ = _timed(lambda: pkg.search(ctx, b, r, stop_at_first=True, want_cand_ok=False), 3)
+    S = sy.n_sys
+    order_k = torch.empty((S, top_k), dtype=torch.int32, device="cuda")
+    order_all = torch.empty((S, K), dtype=torch.int32, device="cuda")
+    first = torch.empty(S, dtype=torch.int32, device="cuda")
+    cand = torch.empty((S, K), dtype=torch.uint8, device="cuda")
+
+    def infer(order):
+        pkg.paam_surrogate_infer(ctx, model, b, r, order.shape[1], order)
+
+    def guided(order, stop_at_first, cand_ok):
+        infer(order)
+        pkg.paam_rta_search_ordered(ctx, b, opts, r, order, stop_at_first, cand_ok, first)
+        return first
+
+    # top-k: every one of the k best-scored candidates is confirmed exactly
+    guided(order_k, False, cand)
+    t_inf, _ = _timed(lambda: infer(order_k), 3)
+    t_g, _ = _timed(lambda: guided(order_k, False, cand), 3)
+    fx, cx = first_x.cpu().numpy(), cand_x.cpu().numpy().astype(bool)
+    guided(order_k, False, cand)
+    fg, cg = first.cpu().numpy(), cand.cpu().numpy().astype(bool)
+    has = fx >= 0
+    false_accepts = int(np.sum(cg & ~cx))
+    recall = float((fg[has] >= 0).mean()) if has.any() else None
+    # the same confirmation budget spent on the first k slots, and on k random slots
+    slot_recall = float(cx[:, :top_k][has].any(axis=1).mean()) if has.any() else None
+    rng = np.random.default_rng(3)
+    pick = np.argsort(rng.random((S, K)), axis=1)[:, :top_k]
+    rand_recall = float(np.take_along_axis(cx, pick, 1)[has].any(axis=1).mean()) if has.any() else None
+    # with fallback: every candidate, best-scored first, stopping at the first admitted one
+    guided(order_all, True, None)
+    t_fb, _ = _timed(lambda: guided(order_all, True, None), 3)
+    fb_same = bool(np.array_equal(first.cpu().numpy() >= 0, has))
+    b.free()
+    model.free()
+    return {
+        "train": {"systems": rows, "sources": list(sources), "epochs": 1, "minibatch": 8192,
+                  "label_analysis_s": round(t_label, 4), "train_s": round(t_train, 4),
+                  "train_tflops": 3 * flops_row * rows / t_train / 1e12, "chunk_loss": losses,
+                  "heldout_mae_R_over_D": mae},
+        "workload": f"cfg4s: {S} systems x {K} candidate orders",
+        "exhaustive_systems_per_s": S / t_ex, "exhaustive_ms": t_ex * 1e3,
+        "early_exit_systems_per_s": S / t_ee, "early_exit_ms": t_ee * 1e3,
+        "top_k": top_k, "guided_systems_per_s": S / t_g, "guided_ms": t_g * 1e3,
+        "speedup_vs_exhaustive": t_ex / t_g, "speedup_vs_early_exit": t_ee / t_g,
+        "infer_ms": t_inf * 1e3, "infer_tflops": flops_row * S * K / t_inf / 1e12,
+        "false_accepts": false_accepts, "recall": recall, "recall_first_k_slots": slot_recall,
+        "recall_random_k": rand_recall,
+        "fallback": {"systems_per_s": S / t_fb, "ms": t_fb * 1e3, "same_verdicts_as_exhaustive": fb_same,
+                     "speedup_vs_exhaustive": t_ex / t_fb, "speedup_vs_early_exit": t_ee / t_fb},
+    }
+
+
+def gemm_bench(pkg, M, N, K, steps, warmup):
+    """The network's tensor-core GEMM alone, fp32 output: TFLOP/s against the
+    measured bf16 peak (first-layer shape of a 262,144-row inference chunk)."""
+    import torch
+
+    g = torch.Generator().manual_seed(5)
+    A = torch.randn((M, K), generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn((N, K), generator=g).to(torch.bfloat16).cuda()
+    C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        pkg.paam_tc_gemm_bf16(A, B, C, err, stream=stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        pkg.paam_tc_gemm_bf16(A, B, C, err, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # spot check against a float32 product of the same bf16 operands
+    rows = torch.arange(0, M, max(1, M // 64), device="cuda")
+    ref = A[rows].float() @ B.float().t()
+    rel = float(((C[rows] - ref).abs().max() / ref.abs().max()).item())
+    tf = 2.0 * M * N * K / (ms / 1e3) / 1e12
+    pk = peaks()
+    return {"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "peak_tflops": pk["bf16_tflops"],
+            "frac": tf / pk["bf16_tflops"], "peak_src": pk["src"], "max_rel_err_vs_fp32": rel,
+            "err_flag": int(err.item())}
+
+
+def search_cpu_baseline(n_sys):
+    import oracle
+    import paam_gen
+
+    sy = paam_gen.generate("cfg4s", n_sys=n_sys)
+    ranks = paam_gen.candidate_ranks(sy, SEARCH_K, paam_gen.CONFIGS["cfg4s"]["seed"] + 7)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.search(sy, ranks, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_sys / dt, "unit": "systems/s (exhaustive, 256 candidates)", "cores": cores, "kind": "oracle",
+            "sample": f"{n_sys} systems of the sparse-executor search workload"}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -186,6 +415,11 @@ def run_ours(args):
     import paam_gen
     import paper_2404_06452_gb300 as pkg
 
+    if args.gemm:
+        if rank == 0:
+            print(json.dumps({"gemm": gemm_bench(pkg, *args.gemm, args.steps, args.warmup)}), flush=True)
+        return
+
     n_sys = args.n_sys or paam_gen.CONFIGS[WORKLOAD]["n_sys"]
     seed = paam_gen.CONFIGS[WORKLOAD]["seed"] + 1_000_003 * rank
     sy = paam_gen.generate(WORKLOAD, n_sys=n_sys, seed=seed)
@@ -198,7 +432,11 @@ def run_ours(args):
     verdict = torch.empty(batch.n_sys, dtype=torch.uint8, device=dev)
     opts = pkg.analysis_opts(1, 0, 0)
     # pick the launch configuration on this batch (untimed; results are identical for all)
-    cfg_index, cfg_times = pkg.paam_rta_autotune(ctx, batch, opts, stream=stream)
+    if args.launch_config is None:
+        cfg_index, cfg_times = pkg.paam_rta_autotune(ctx, batch, opts, stream=stream)
+    else:
+        cfg_index, cfg_times = args.launch_config, []
+        pkg.paam_rta_set_launch_config(batch, cfg_index)
 
     def step():
         pkg.paam_rta_analyze_batch(ctx, batch, opts, R, st, verdict, stream=stream)
@@ -241,7 +479,8 @@ def run_ours(args):
     achieved = alg / (kern_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"],
-                "kernel": "analyze_fast_kernel", "algorithmic_bytes_per_launch": alg}
+                "kernel": "analyze_reg_kernel" if cfg_index in REG_CONFIGS else "analyze_fast_kernel",
+                "algorithmic_bytes_per_launch": alg}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
@@ -291,6 +530,15 @@ def run_ours(args):
         same = bool(np.array_equal(ref["R"], R.cpu().numpy()) and np.array_equal(ref["status"], st.cpu().numpy()))
         cpu["bit_exact_vs_gpu"] = same
 
+    # ---- priority search and surrogate (single GPU, rank 0) -------------------
+    search = surrogate = None
+    if rank == 0 and world == 1 and not args.no_search:
+        search = search_bench(pkg, ctx, args.search_sys)
+        if not args.no_cpu_baseline:
+            search["cpu_baseline"] = search_cpu_baseline(min(args.search_sys, 2000))
+    if rank == 0 and world == 1 and not args.no_surrogate:
+        surrogate = surrogate_bench(pkg, ctx, args.train_sys, args.search_sys, args.top_k)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "chains/s", "n_gpus": world, "steps": args.steps,
@@ -303,7 +551,7 @@ def run_ours(args):
                        "autotune_ms": [round(t, 4) for t in cfg_times]},
             "systems_per_s": total_sys * args.steps / (elapsed_ms / 1e3),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks,
+            "clocks": clocks, "search": search, "surrogate": surrogate,
         }
         print(json.dumps(line), flush=True)
     batch.free()
