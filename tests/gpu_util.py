@@ -14,7 +14,9 @@ def ctx():
     return ctx._c
 
 
-def gpu_analyze(sy, n_buckets=1, eps=0, kappa=0, device_view=False):
+def gpu_analyze(sy, n_buckets=1, eps=0, kappa=0, device_view=False, autotune=False):
+    """Analyse ``sy`` through the C ABI; with ``autotune`` in the launch
+    configuration the autotuner picks (as the benchmark does)."""
     import torch
 
     import paper_2404_06452_gb300 as pkg
@@ -22,6 +24,8 @@ def gpu_analyze(sy, n_buckets=1, eps=0, kappa=0, device_view=False):
     c = ctx()
     src = pkg.to_device(sy) if device_view else sy
     b = pkg.paam_rta_load_systems(c, src)
+    if autotune:
+        pkg.paam_rta_autotune(c, b, pkg.analysis_opts(n_buckets, eps, kappa))
     R, st, v = pkg.analyze(c, b, n_buckets=n_buckets, eps=eps, kappa=kappa)
     torch.cuda.synchronize()
     out = dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy())
