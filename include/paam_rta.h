@@ -351,6 +351,16 @@ int paam_rta_analyze_noalloc(const paam_systems_view *view, const paam_analysis_
 int paam_tc_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int32_t *err, void *stream);
 
 /*
+ * The network's activation as its GEMM epilogues compute it, exposed for
+ * testing: for i < n, gelu[i] = z Phi(z) and grad[i] = Phi(z) + z phi(z) at
+ * z = z[i] (fp32 device arrays; either output may be NULL).  Phi is evaluated
+ * with the Abramowitz-Stegun 7.1.26 form of erf (|error| <= 1.5e-7).
+ * Enqueued on `stream`.  PAAM_E_INVAL for n < 0 or a NULL z with n > 0.
+ * Not part of the paper.
+ */
+int paam_diag_gelu(const float *z, float *gelu, float *grad, int64_t n, void *stream);
+
+/*
  * Diagnostics: number of CUDA kernels this library has launched in this
  * process (all contexts).  Not part of the paper; used to report how many
  * of the library's own kernels ran inside a timed region.

@@ -105,6 +105,7 @@ def lib():
                                                        _c_void_p]),
             "paam_tc_gemm_bf16": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _c_void_p, _c_void_p]),
+            "paam_diag_gelu": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int64, _c_void_p]),
             "paam_rta_search_priorities": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
                                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                           _c_void_p, _c_void_p, _c_void_p]),
@@ -125,7 +126,7 @@ def exported_symbols() -> list:
             "paam_tc_gemm_bf16", "paam_rta_search_ordered", "paam_model_create", "paam_model_free",
             "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
             "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
-            "paam_surrogate_grad", "paam_surrogate_features"]
+            "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu"]
 
 
 def launch_count() -> int:
@@ -312,6 +313,12 @@ def paam_tc_gemm_bf16(A, B, C, err, stream=None):
     N = B.shape[0]
     _check(lib().paam_tc_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), _ptr(err),
                                    _stream_ptr(stream)), "paam_tc_gemm_bf16")
+
+
+def paam_diag_gelu(z, gelu=None, grad=None, stream=None):
+    """The network's activation and its derivative at device fp32 ``z``."""
+    _check(lib().paam_diag_gelu(_ptr(z), _ptr(gelu), _ptr(grad), int(z.numel()), _stream_ptr(stream)),
+           "paam_diag_gelu")
 
 
 def paam_rta_search_ordered(ctx: Context, batch: Batch, opts: AnalysisOpts, ranks, order, stop_at_first: bool,

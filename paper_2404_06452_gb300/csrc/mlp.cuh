@@ -47,6 +47,10 @@ int tc_gemm(const TcGemm &g, int32_t *err, cudaStream_t stream);
 
 // Surrogate input features (features.cu): rows item = (system - sys0) * K +
 // candidate for items [0, n_items) of systems starting at sys0; ranks NULL =
-// the systems' own priorities (K = 1).  X is [n_items][1024] bf16.
+// the systems' own priorities (K = 1).  X is [n_items][width] bf16 with width =
+// 16 x (chain slots), a multiple of 16 of at least 16 x the batch's largest
+// chain count and at most 1024; slots past a system's chains are zero, so a
+// first layer may read only the first width columns of its 1024-wide input.
 int paam_launch_features(const paam_batch *b, const int16_t *ranks, int32_t K, int32_t nmax, int64_t sys0,
-                         int64_t n_items, int32_t n_buckets, int64_t kappa, __nv_bfloat16 *X, cudaStream_t stream);
+                         int64_t n_items, int32_t n_buckets, int64_t kappa, int32_t width, __nv_bfloat16 *X,
+                         cudaStream_t stream);

@@ -18,14 +18,60 @@
 
 namespace {
 
-constexpr int BM = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BK = 64;
 constexpr uint64_t kWaitNs = 2000000000ull; // 2 s: far above any legitimate wait
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// Normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2 with erf from Abramowitz and
+// Stegun, Handbook of Mathematical Functions (1964), formula 7.1.26:
+//   erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),
+//   t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7,
+// odd in x.  The activations are stored as bf16 (relative step 2^-8), so this
+// bound is far below what the network can see; it is branch-free and costs
+// one reciprocal and one exponential.  Also returns exp(-z^2 / 2) for GELU'.
+__device__ __forceinline__ float normal_cdf(float z, float &g)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    float poly = fmaf(1.061405429f, t, -1.453152027f);
+    poly = fmaf(poly, t, 1.421413741f);
+    poly = fmaf(poly, t, -0.284496736f);
+    poly = fmaf(poly, t, 0.254829592f);
+    poly *= t;
+    g = __expf(-x * x);
+    const float erf_abs = 1.0f - poly * g;
+    return 0.5f + copysignf(0.5f * erf_abs, z);
+}
 
+__device__ __forceinline__ float gelu(float z)
+{
+    float g;
+    return z * normal_cdf(z, g);
+}
+
+// d/dz z Phi(z) = Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi)
 __device__ __forceinline__ float gelu_grad(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    float g;
+    const float cdf = normal_cdf(z, g);
+    return fmaf(z * 0.39894228040143268f, g, cdf);
+}
+
+// a[i] += bias[col0 + i] (columns past N get nothing); bias is 16-byte aligned
+__device__ __forceinline__ void add_bias(const TcEpilogue &ep, int col0, bool full, float (&a)[32])
+{
+    if (full) {
+        const float4 *b4 = reinterpret_cast<const float4 *>(ep.bias + col0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 v = __ldg(b4 + i);
+            a[4 * i] += v.x;
+            a[4 * i + 1] += v.y;
+            a[4 * i + 2] += v.z;
+            a[4 * i + 3] += v.w;
+        }
+    } else {
+        for (int i = 0; i < 32; ++i) a[i] += (col0 + i < ep.N) ? ep.bias[col0 + i] : 0.0f;
+    }
 }
 
 // 32 consecutive accumulator columns col0.. of one output row
@@ -39,9 +85,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcEpilogue &ep, int row, in
     switch (ep.mode) {
     case TC_EPI_STORE_F32:
     case TC_EPI_BIAS_F32: {
-        if (ep.mode == TC_EPI_BIAS_F32)
-#pragma unroll
-            for (int i = 0; i < 32; ++i) a[i] += (col0 + i < ep.N) ? ep.bias[col0 + i] : 0.0f;
+        if (ep.mode == TC_EPI_BIAS_F32) add_bias(ep, col0, full, a);
         float *c = ep.C + (size_t)row * ep.ldc + col0;
         if (full) {
 #pragma unroll
@@ -63,9 +107,10 @@ __device__ __forceinline__ void epilogue_chunk(const TcEpilogue &ep, int row, in
         __nv_bfloat16 out[32];
         if (ep.mode == TC_EPI_BIAS_GELU) {
             __nv_bfloat16 zb[32];
+            add_bias(ep, col0, full, a);
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                zb[i] = __float2bfloat16_rn(a[i] + ((col0 + i < ep.N) ? ep.bias[col0 + i] : 0.0f));
+                zb[i] = __float2bfloat16_rn(a[i]);
                 out[i] = __float2bfloat16_rn(gelu(__bfloat162float(zb[i])));
             }
             if (ep.Z && full) {
@@ -98,7 +143,7 @@ __device__ __forceinline__ void epilogue_chunk(const TcEpilogue &ep, int row, in
     }
 }
 
-template <int BN>
+template <int BN, int STAGES>
 struct GemmSmem {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
@@ -107,14 +152,18 @@ struct GemmSmem {
     static constexpr int TOTAL = TILES + 256 + 1024; // barriers and flags, alignment slack
 };
 
-template <int BN>
-__global__ void __launch_bounds__(192) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+// Warp roles: 0 TMA producer, 1 TMEM owner and MMA issuer, 2..9 epilogue (two
+// warps per TMEM lane quadrant, one per half of the tile's columns).
+constexpr int kGemmThreads = 320;
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kGemmThreads, 2) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, int kb_total,
                                                       int kb_per_split, TcEpilogue ep, int32_t *err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023); // swizzled tiles
-    using L = GemmSmem<BN>;
+    using L = GemmSmem<BN, STAGES>;
     uint64_t *full = (uint64_t *)(smem + L::TILES);
     uint64_t *empty = full + STAGES;
     uint64_t *done = empty + STAGES;
@@ -186,8 +235,9 @@ __global__ void __launch_bounds__(192) tc_gemm_kernel(const __grid_constant__ CU
             tc::mma_commit(&empty[s]); // frees the stage once these MMAs have read it
         }
         if (ok) tc::mma_commit(done);
-    } else if (warp >= 2) { // ---- epilogue: one output row per thread
+    } else if (warp >= 2) { // ---- epilogue: one output row per thread, half the columns per warp
         const int q = warp & 3; // the TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;
         const int row = m0 + 32 * q + lane;
         bool ok = nkb > 0;
         if (ok && !tc::mbar_wait(done, 0, kWaitNs)) {
@@ -198,7 +248,7 @@ __global__ void __launch_bounds__(192) tc_gemm_kernel(const __grid_constant__ CU
         tc::fence_after_sync();
         if (ok) {
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int c = half * (BN / 64); c < (half + 1) * (BN / 64); ++c) {
                 uint32_t v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * c), v);
                 tc::tmem_wait_ld();
@@ -214,6 +264,171 @@ __global__ void __launch_bounds__(192) tc_gemm_kernel(const __grid_constant__ CU
         for (int s = 0; s < STAGES && s < n_issued; ++s) {
             const int last = ((n_issued - 1 - s) / STAGES) * STAGES + s;
             tc::mbar_wait(&full[s], (last / STAGES) & 1, kWaitNs / 4);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, kCols);
+    }
+}
+
+// ---- persistent, weight-stationary layer -------------------------------------------
+// For K <= 256 and one column tile (N = BN) the whole B operand (a layer's
+// weights, at most 256 x 256 bf16 = 128 KB) stays in shared memory; each CTA
+// loops over row tiles, A tiles stream through a 4-stage TMA ring, and the
+// accumulator is double-buffered in TMEM (2 x BN columns) so the epilogue of
+// row tile i (16 warps, four per TMEM lane quadrant) overlaps the loads and
+// MMAs of tile i + 1.
+constexpr int kPersistThreads = 576; // warp 0 TMA, warp 1 TMEM + MMA, warps 2..17 epilogue
+constexpr int kPersistEpiWarps = kPersistThreads / 32 - 2;
+constexpr int kPersistStages = 4;
+
+template <int BN>
+struct PersistSmem {
+    static constexpr int W_BYTES = 256 * BN * 2; // K up to 256
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int TILES = W_BYTES + kPersistStages * A_BYTES;
+    static constexpr int TOTAL = TILES + 256 + 1024;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    tc_layer_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                               int kb_total, int m_tiles, TcEpilogue ep, int32_t *err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    using L = PersistSmem<BN>;
+    uint8_t *wsm = smem;               // kb_total blocks of [BN][64] bf16, 128-byte swizzled
+    uint8_t *asm_a = smem + L::W_BYTES; // A ring
+    uint64_t *full = (uint64_t *)(smem + L::TILES);
+    uint64_t *empty = full + kPersistStages;
+    uint64_t *acc_full = empty + kPersistStages;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *wbar = acc_empty + 2;
+    uint64_t *fin = wbar + 1;
+    uint32_t *tmem_slot = (uint32_t *)(fin + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    volatile int *issued = abort_flag + 1;
+    constexpr uint32_t kCols = 2 * BN; // BN in {64, 128, 256}: a power of two >= 32
+    constexpr int W_BLOCK = BN * BK * 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPersistStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&acc_full[b], 1);
+            tc::mbar_init(&acc_empty[b], kPersistEpiWarps);
+        }
+        tc::mbar_init(wbar, 1);
+        tc::mbar_init(fin, 1);
+        *abort_flag = 0;
+        *issued = 0;
+        tc::fence_barrier_init();
+        tc::prefetch_tmap(&tmA);
+        tc::prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, kCols);
+        tc::tmem_relinquish();
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) { // ---- TMA producer: W once, then A tiles
+        tc::mbar_expect_tx(wbar, (uint32_t)(kb_total * W_BLOCK));
+        for (int kb = 0; kb < kb_total; ++kb) tc::tma_load_2d(wsm + kb * W_BLOCK, &tmB, wbar, kb * BK, 0);
+        int it = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < m_tiles; tile += gridDim.x) {
+            for (int kb = 0; kb < kb_total; ++kb) {
+                const int s = it % kPersistStages, r = it / kPersistStages;
+                if (*abort_flag || (r > 0 && !tc::mbar_wait(&empty[s], (r - 1) & 1, kWaitNs))) {
+                    *abort_flag = 1;
+                    atomicExch(err, PAAM_E_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+                tc::mbar_expect_tx(&full[s], L::A_BYTES);
+                tc::tma_load_2d(asm_a + s * L::A_BYTES, &tmA, &full[s], kb * BK, tile * BM);
+                ++it;
+            }
+        }
+        *issued = it;
+    } else if (warp == 1 && lane == 0) { // ---- MMA issuer
+        constexpr uint32_t idesc = tc::idesc_bf16(BM, BN);
+        bool ok = tc::mbar_wait(wbar, 0, kWaitNs);
+        int it = 0, i = 0;
+        for (int tile = blockIdx.x; ok && tile < m_tiles; tile += gridDim.x, ++i) {
+            const int b = i & 1;
+            if (*abort_flag || (i >= 2 && !tc::mbar_wait(&acc_empty[b], ((i >> 1) - 1) & 1, kWaitNs))) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t d = tmem + (uint32_t)(b * BN);
+            for (int kb = 0; kb < kb_total; ++kb, ++it) {
+                const int s = it % kPersistStages, r = it / kPersistStages;
+                if (*abort_flag || !tc::mbar_wait(&full[s], r & 1, kWaitNs)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t a = tc::smem_u32(asm_a + s * L::A_BYTES);
+                const uint32_t w = tc::smem_u32(wsm + kb * W_BLOCK);
+#pragma unroll
+                for (int j = 0; j < BK / 16; ++j)
+                    tc::mma_bf16(d, tc::desc_sw128(a + 32 * j), tc::desc_sw128(w + 32 * j), idesc,
+                                 (kb > 0 || j > 0) ? 1u : 0u);
+                tc::mma_commit(&empty[s]);
+            }
+            if (!ok) break;
+            tc::mma_commit(&acc_full[b]);
+        }
+        if (!ok) {
+            *abort_flag = 1;
+            atomicExch(err, PAAM_E_TIMEOUT);
+        }
+        // every MMA this thread issued has completed before TMEM can be released
+        tc::mma_commit(fin);
+        tc::mbar_wait(fin, 0, kWaitNs);
+    } else if (warp >= 2) { // ---- epilogue: one output row per thread, a quarter of the columns per warp
+        const int q = warp & 3, cg = (warp - 2) >> 2;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < m_tiles; tile += gridDim.x, ++i) {
+            const int b = i & 1;
+            if (*abort_flag || !tc::mbar_wait(&acc_full[b], (i >> 1) & 1, kWaitNs)) {
+                *abort_flag = 1;
+                atomicExch(err, PAAM_E_TIMEOUT);
+                break;
+            }
+            tc::fence_after_sync();
+            const int row = tile * BM + 32 * q + lane;
+#pragma unroll 1
+            for (int c = cg; c < BN / 32; c += 4) {
+                uint32_t v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + 32 * c), v);
+                tc::tmem_wait_ld();
+                epilogue_chunk(ep, row, 32 * c, v);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        // let TMA copies already issued land before this CTA's shared memory is released
+        tc::mbar_wait(wbar, 0, kWaitNs / 4);
+        const int n_issued = *issued;
+        for (int s = 0; s < kPersistStages && s < n_issued; ++s) {
+            const int last = ((n_issued - 1 - s) / kPersistStages) * kPersistStages + s;
+            tc::mbar_wait(&full[s], (last / kPersistStages) & 1, kWaitNs / 4);
         }
     }
     __syncthreads();
@@ -258,7 +473,7 @@ bool make_map(CUtensorMap *m, const __nv_bfloat16 *base, int rows, int cols, int
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int STAGES>
 int launch_bn(const TcGemm &g, int32_t *err, cudaStream_t stream)
 {
     CUtensorMap ma, mb;
@@ -268,23 +483,90 @@ int launch_bn(const TcGemm &g, int32_t *err, cudaStream_t stream)
     const int splits = g.splits < 1 ? 1 : (g.splits > kb_total ? kb_total : g.splits);
     const int per = (kb_total + splits - 1) / splits;
     const dim3 grid((unsigned)((g.ep.M + BM - 1) / BM), (unsigned)(g.ep.N / BN), (unsigned)((kb_total + per - 1) / per));
-    const int smem = GemmSmem<BN>::TOTAL;
-    PAAM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    tc_gemm_kernel<BN><<<grid, 192, smem, stream>>>(ma, mb, kb_total, per, g.ep, err);
+    const int smem = GemmSmem<BN, STAGES>::TOTAL;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    tc_gemm_kernel<BN, STAGES><<<grid, kGemmThreads, smem, stream>>>(ma, mb, kb_total, per, g.ep, err);
     PAAM_CUDA_TRY(cudaGetLastError());
     paam_count_launch();
     return PAAM_OK;
 }
 
+// Short K (at most 4 steps of 64) needs no deeper ring than 2 stages; the
+// smaller footprint lets 2 CTAs share an SM, so one CTA's epilogue overlaps
+// the other's loads and MMAs (TMEM: 2 x 256 columns at most).
+template <int BN>
+int launch_bn_depth(const TcGemm &g, int32_t *err, cudaStream_t stream)
+{
+    const int per = g.splits > 1 ? (g.K / BK + g.splits - 1) / g.splits : g.K / BK;
+    if (per <= 4) return launch_bn<BN, 2>(g, err, stream);
+    return launch_bn<BN, 4>(g, err, stream);
+}
+
 } // namespace
+
+static int sm_count()
+{
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!cache[dev]) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    return cache[dev];
+}
+
+template <int BN>
+int launch_persistent(const TcGemm &g, int32_t *err, cudaStream_t stream)
+{
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, g.A, g.a_rows, g.K, g.lda, BM) || !make_map(&mb, g.B, g.b_rows, g.K, g.ldb, BN))
+        return PAAM_E_CUDA;
+    const int m_tiles = (g.ep.M + BM - 1) / BM;
+    const int n_sm = sm_count();
+    const int grid = m_tiles < n_sm ? m_tiles : (n_sm > 0 ? n_sm : 1);
+    const int smem = PersistSmem<BN>::TOTAL;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(tc_layer_persistent_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem));
+    tc_layer_persistent_kernel<BN><<<grid, kPersistThreads, smem, stream>>>(ma, mb, g.K / BK, m_tiles, g.ep, err);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    paam_count_launch();
+    return PAAM_OK;
+}
 
 int tc_gemm(const TcGemm &g, int32_t *err, cudaStream_t stream)
 {
     if (g.K <= 0 || g.K % BK || g.lda % 8 || g.ldb % 8 || g.ep.N % 64 || g.ep.M <= 0) return PAAM_E_INVAL;
     if (g.splits > 1 && g.ep.mode != TC_EPI_ATOMIC_F32) return PAAM_E_INVAL;
-    if (g.ep.N % 256 == 0) return launch_bn<256>(g, err, stream);
-    if (g.ep.N % 128 == 0) return launch_bn<128>(g, err, stream);
-    return launch_bn<64>(g, err, stream);
+    // one column tile, short K, many row tiles: weights stay resident, epilogue overlaps MMA
+    if (g.splits <= 1 && g.K <= 256 && g.b_rows == g.ep.N && g.ep.M >= 4 * BM * sm_count()) {
+        if (g.ep.N == 256) return launch_persistent<256>(g, err, stream);
+        if (g.ep.N == 128) return launch_persistent<128>(g, err, stream);
+        if (g.ep.N == 64) return launch_persistent<64>(g, err, stream);
+    }
+    if (g.ep.N % 256 == 0) return launch_bn_depth<256>(g, err, stream);
+    if (g.ep.N % 128 == 0) return launch_bn_depth<128>(g, err, stream);
+    return launch_bn_depth<64>(g, err, stream);
+}
+
+namespace {
+__global__ void diag_gelu_kernel(const float *z, float *g, float *d, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (g) g[i] = gelu(z[i]);
+        if (d) d[i] = gelu_grad(z[i]);
+    }
+}
+} // namespace
+
+extern "C" int paam_diag_gelu(const float *z, float *gelu_out, float *grad_out, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && !z)) return PAAM_E_INVAL;
+    if (n == 0) return PAAM_OK;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    diag_gelu_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(z, gelu_out, grad_out, n);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    paam_count_launch();
+    return PAAM_OK;
 }
 
 // C[M, N] fp32 = A[M, K] * B[N, K]^T (bf16, device, row-major, ld = K).

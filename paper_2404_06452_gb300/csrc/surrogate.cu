@@ -420,12 +420,24 @@ TcGemm gemm(const __nv_bfloat16 *A, int lda, int a_rows, const __nv_bfloat16 *B,
     return g;
 }
 
-// X (rows of w.Xb) through the network into w.Y; keeps Z, H, H^T when training
-int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, bool train, cudaStream_t s)
+// Feature columns that can be non-zero in this batch: 16 per chain slot up to
+// the largest system, rounded up to the GEMM's 64-column K step.
+int input_width(const paam_batch *b)
+{
+    const int w = ((NF * (b->max_chains > 0 ? b->max_chains : 1)) + 63) / 64 * 64;
+    return w < XW ? w : XW;
+}
+
+// X (rows of w.Xb, kx columns) through the network into w.Y; keeps Z, H, H^T
+// when training.  kx < 1024 reads only the first kx input columns of layer 1:
+// exact when the remaining feature columns are zero (chain slots past every
+// system's chains), since their products add nothing to the fp32 sums.
+int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool train, cudaStream_t s)
 {
     const int rows = w.rows;
     for (int l = 0; l < 3; ++l) {
-        TcGemm g = gemm(l == 0 ? X : w.H[l - 1], IN[l], rows, m->Wb[l], IN[l], OUT[l], IN[l]);
+        TcGemm g = l == 0 ? gemm(X, kx, rows, m->Wb[0], IN[0], OUT[0], kx)
+                          : gemm(w.H[l - 1], IN[l], rows, m->Wb[l], IN[l], OUT[l], IN[l]);
         g.ep.mode = TC_EPI_BIAS_GELU;
         g.ep.M = rows;
         g.ep.N = OUT[l];
@@ -561,7 +573,7 @@ extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const in
     __nv_bfloat16 *X = (__nv_bfloat16 *)data;
     float *L = (float *)((char *)data + (size_t)n * 2 * XW);
     int64_t *idx_dev = (int64_t *)((char *)L + (size_t)n * 4 * NCH);
-    if (rc == PAAM_OK) rc = paam_launch_features(b, nullptr, 1, 0, 0, n, o->n_buckets, o->kappa_ns, X, s);
+    if (rc == PAAM_OK) rc = paam_launch_features(b, nullptr, 1, 0, 0, n, o->n_buckets, o->kappa_ns, XW, X, s);
     if (rc == PAAM_OK) {
         labels_kernel<<<grid_for(n * NCH, 256, ctx->n_sm), 256, 0, s>>>(batch_dev(b), R, status, L);
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
@@ -587,7 +599,7 @@ extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const in
             gather_kernel<<<rows, 128, 0, s>>>(X, L, idx_dev + st * rows, rows, w.Xb, w.XbT, w.Lb, w.count);
             if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
             paam_count_launch();
-            if (rc == PAAM_OK) rc = forward(m, w, w.Xb, true, s);
+            if (rc == PAAM_OK) rc = forward(m, w, w.Xb, XW, true, s);
             if (rc == PAAM_OK) rc = backward(m, w, s);
             if (rc == PAAM_OK) rc = adamw(m, o, s);
         }
@@ -630,6 +642,7 @@ extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const pa
     int64_t chunk = (262144 + K - 1) / K;
     if (chunk > b->n_sys) chunk = b->n_sys;
     const int rows = (int)(chunk * K);
+    const int kx = input_width(b);
     Work w;
     int rc = work_alloc(w, rows, false, s);
     if (rc != PAAM_OK) return rc;
@@ -649,8 +662,8 @@ extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const pa
         const int64_t items = ns * K;
         Work wc = w;
         wc.rows = (int)items;
-        rc = paam_launch_features(b, ranks, K, nmax, s0, items, n_buckets, kappa_ns, wc.Xb, s);
-        if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, false, s);
+        rc = paam_launch_features(b, ranks, K, nmax, s0, items, n_buckets, kappa_ns, kx, wc.Xb, s);
+        if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, kx, false, s);
         if (rc == PAAM_OK) {
             score_kernel<<<grid_for(items, 256, ctx->n_sm), 256, 0, s>>>(wc.Y, batch_dev(b), s0, K, items,
                                                                          sc + s0 * K);
@@ -683,6 +696,7 @@ extern "C" int paam_surrogate_predict(paam_ctx *ctx, const paam_model *m, const 
     PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream_;
     const int64_t chunk = b->n_sys < 262144 ? b->n_sys : 262144;
+    const int kx = input_width(b);
     Work w;
     int rc = work_alloc(w, (int)chunk, false, s);
     if (rc != PAAM_OK) return rc;
@@ -691,8 +705,8 @@ extern "C" int paam_surrogate_predict(paam_ctx *ctx, const paam_model *m, const 
         Work wc = w;
         wc.rows = (int)((s0 + chunk <= b->n_sys) ? chunk : b->n_sys - s0);
         wc.Y = pred + s0 * NCH;
-        rc = paam_launch_features(b, nullptr, 1, 0, s0, wc.rows, n_buckets, kappa_ns, wc.Xb, s);
-        if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, false, s);
+        rc = paam_launch_features(b, nullptr, 1, 0, s0, wc.rows, n_buckets, kappa_ns, kx, wc.Xb, s);
+        if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, kx, false, s);
     }
     int32_t herr = 0;
     if (cudaMemcpyAsync(&herr, w.err, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = PAAM_E_CUDA;
@@ -734,7 +748,7 @@ extern "C" int paam_surrogate_grad(paam_ctx *ctx, paam_model *m, const void *X, 
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
         paam_count_launch();
     }
-    if (rc == PAAM_OK) rc = forward(m, w, w.Xb, true, s);
+    if (rc == PAAM_OK) rc = forward(m, w, w.Xb, XW, true, s);
     if (rc == PAAM_OK) rc = backward(m, w, s);
     size_t o = 0;
     for (int l = 0; l < NL && rc == PAAM_OK; ++l) {
@@ -835,6 +849,6 @@ extern "C" int paam_surrogate_features(paam_ctx *ctx, const paam_batch *b, const
     if (b->max_chains > NCH) return PAAM_E_UNSUPPORTED;
     if (ranks ? (K < 1 || nmax < b->max_chains) : K != 1) return PAAM_E_INVAL;
     PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
-    return paam_launch_features(b, ranks, K, nmax, 0, b->n_sys * (int64_t)K, n_buckets, kappa_ns,
+    return paam_launch_features(b, ranks, K, nmax, 0, b->n_sys * (int64_t)K, n_buckets, kappa_ns, XW,
                                 (__nv_bfloat16 *)X, (cudaStream_t)stream);
 }

@@ -51,6 +51,91 @@ def test_features_match_oracle():
     assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 2e-3)
 
 
+@pytest.mark.parametrize("case", ["seg16", "seg32", "many_chains", "many_executors"])
+def test_candidate_features_paths(case):
+    """Candidate mode: 16- and 32-lane segments per candidate order (up to 16 /
+    32 chains, several buckets, more candidates than segments per block), and
+    the per-item kernel for systems beyond 32 chains or 32 executors."""
+    if case == "seg16":
+        sy = g.generate("cfg2", n_sys=30, seed=76)
+    elif case == "seg32":
+        sy = g.generate("cfg3", n_sys=40, seed=77, n_max=32)
+        assert sy.chains_per_system().max() > 16
+    elif case == "many_chains":
+        sy = g.generate("cfg3", n_sys=40, seed=77)
+        assert sy.chains_per_system().max() > 32
+    else:
+        sy = g.generate("cfg4s", n_sys=12, x_min=40, x_max=40, seed=78)
+    ranks = g.candidate_ranks(sy, 37, 5)
+    got = _features(sy, ranks, n_buckets=3, kappa=20_000)
+    ref = ofeat.features(sy, ranks, n_buckets=3, kappa=20_000)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 2e-3)
+    assert np.all(got[ref == 0] == 0)
+
+
+def test_candidate_features_invalid_row_is_zero():
+    sy = g.generate("cfg4s", n_sys=5)
+    ranks = g.candidate_ranks(sy, 4, 3)
+    ranks[2, 1, 3] = ranks[2, 1, 4]  # not a permutation
+    ranks[4, 3, 0] = 99              # out of range
+    got = _features(sy, ranks).reshape(5, 4, 1024)
+    assert np.all(got[2, 1] == 0) and np.all(got[4, 3] == 0)
+    ok = np.ones((5, 4), bool)
+    ok[2, 1] = ok[4, 3] = False
+    ref = ofeat.features(sy, np.where(ok[:, :, None], ranks, g.candidate_ranks(sy, 4, 3))).reshape(5, 4, 1024)
+    assert np.all(np.abs(got[ok] - ref[ok]) <= 2.0 ** -8 * np.abs(ref[ok]) + 2e-3)
+
+
+def _bf16_round(a):
+    import torch
+
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+
+
+def _oracle_net(params, X):
+    """The float64 network on bf16 weights (as the tensor cores see them)."""
+    q, o = params.astype(np.float64).copy(), 0
+    for fin, fout in mlp.SIZES:
+        q[o:o + fin * fout] = _bf16_round(q[o:o + fin * fout])
+        o += fin * fout + fout
+    return mlp.forward(q, X)[0]
+
+
+def test_infer_and_predict_scores_match_oracle_network():
+    """Inference reads only the feature columns a batch can fill (16 per chain
+    slot of its largest system); its scores and the per-chain predictions
+    still follow the full 1024-input network."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    p = _random_params(11)
+    m = pkg.Model.create(ctx(), 2)
+    m.set_params(p)
+    for cfg, K, nb in (("cfg4s", 20, 1), ("cfg1", 7, 2)):
+        sy = g.generate(cfg, n_sys=30)
+        ranks = g.candidate_ranks(sy, K, 8)
+        b = pkg.paam_rta_load_systems(ctx(), sy)
+        r = torch.from_numpy(ranks).cuda()
+        ranked = torch.empty((sy.n_sys, 3), dtype=torch.int32, device="cuda")
+        scores = torch.empty((sy.n_sys, K), dtype=torch.float32, device="cuda")
+        pkg.paam_surrogate_infer(ctx(), m, b, r, 3, ranked, scores, n_buckets=nb)
+        pred = torch.empty((sy.n_sys, 64), dtype=torch.float32, device="cuda")
+        pkg.paam_surrogate_predict(ctx(), m, b, pred, n_buckets=nb)
+        torch.cuda.synchronize()
+        n = sy.chains_per_system()
+        Y = _oracle_net(p, _bf16_round(ofeat.features(sy, ranks, n_buckets=nb))).reshape(sy.n_sys, K, 64)
+        want = np.stack([np.maximum(Y[s, :, :n[s]].max(axis=1), 0.0) for s in range(sy.n_sys)])
+        got = scores.cpu().numpy()
+        assert np.all(np.abs(got - want) <= 3e-2 * (np.abs(want) + 1.0)), np.abs(got - want).max()
+        Yp = _oracle_net(p, _bf16_round(ofeat.features(sy, n_buckets=nb)))
+        gp = pred.cpu().numpy()
+        for s in range(sy.n_sys):
+            assert np.all(np.abs(gp[s, :n[s]] - Yp[s, :n[s]]) <= 3e-2 * (np.abs(Yp[s, :n[s]]) + 1.0))
+        b.free()
+    m.free()
+
+
 def _random_params(seed):
     rng = np.random.default_rng(seed)
     out = []
