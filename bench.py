@@ -116,8 +116,11 @@ def peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
 
 
-# launch configurations whose main kernel is the register-table family
-REG_CONFIGS = {0, 3, 4, 5, 6, 7, 10, 11}
+# main kernel of each launch configuration (the table in csrc/analyze_fast.cu)
+CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>", 2: "analyze_fast_kernel<16, 32>",
+                 3: "analyze_reg_kernel<16, 1>", 4: "analyze_reg_kernel<4, 4>", 5: "analyze_reg_kernel<16, 2>",
+                 6: "analyze_reg_kernel<32, 1>", 7: "analyze_reg_kernel<8, 2>", 8: "analyze_fast_kernel<4, 16>",
+                 9: "analyze_fast_kernel<8, 32>", 10: "analyze_reg_kernel<16, 2>", 11: "analyze_reg_kernel<4, 4>"}
 
 
 def algorithmic_bytes(sy) -> int:
@@ -479,7 +482,7 @@ def run_ours(args):
     achieved = alg / (kern_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"],
-                "kernel": "analyze_reg_kernel" if cfg_index in REG_CONFIGS else "analyze_fast_kernel",
+                "kernel": CONFIG_KERNEL.get(cfg_index, "analysis kernel"),
                 "algorithmic_bytes_per_launch": alg}
 
     # ---- end to end through the C ABI with host buffers ----------------------

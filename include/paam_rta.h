@@ -352,9 +352,10 @@ int paam_tc_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int 
 
 /*
  * The network's activation as its GEMM epilogues compute it, exposed for
- * testing: for i < n, gelu[i] = z Phi(z) and grad[i] = Phi(z) + z phi(z) at
- * z = z[i] (fp32 device arrays; either output may be NULL).  Phi is evaluated
- * with the Abramowitz-Stegun 7.1.26 form of erf (|error| <= 1.5e-7).
+ * testing: for i < n, gelu[i] = z Phi(z) and grad[i] = Phi(z) + z Phi'(z) at
+ * z = z[i] (fp32 device arrays; either output may be NULL), with GELU in its
+ * tanh form: Phi(z) is taken as (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))) / 2
+ * (Hendrycks and Gimpel 2016) and phi as its derivative.
  * Enqueued on `stream`.  PAAM_E_INVAL for n < 0 or a NULL z with n > 0.
  * Not part of the paper.
  */

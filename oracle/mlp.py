@@ -1,7 +1,8 @@
 """Float64 forward and backward of the surrogate network -- TEST INFRASTRUCTURE ONLY.
 
-Layers 1024 -> 256 -> 256 -> 256 -> 64; hidden activation GELU(z) =
-z * Phi(z) with the exact normal CDF; output linear; loss = mean over the
+Layers 1024 -> 256 -> 256 -> 256 -> 64; hidden activation GELU in its tanh
+form (Hendrycks and Gimpel 2016): gelu(z) = z (1 + tanh(u)) / 2 with
+u = sqrt(2 / pi) (z + 0.044715 z^3); output linear; loss = mean over the
 valid (label >= 0) entries of (y - label)^2.  Parameters are one flat vector:
 per layer the weights [out][in] row-major, then the biases.  Gradients by
 hand-written backpropagation in numpy; shares no code with the CUDA path.
@@ -9,7 +10,6 @@ hand-written backpropagation in numpy; shares no code with the CUDA path.
 from __future__ import annotations
 
 import numpy as np
-from scipy.special import erf
 
 SIZES = [(1024, 256), (256, 256), (256, 256), (256, 64)]
 
@@ -27,12 +27,16 @@ def unpack(params):
     return out
 
 
+_C = np.sqrt(2.0 / np.pi)
+
+
 def gelu(z):
-    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+    return 0.5 * z * (1.0 + np.tanh(_C * (z + 0.044715 * z ** 3)))
 
 
 def gelu_grad(z):
-    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+    t = np.tanh(_C * (z + 0.044715 * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * _C * (1.0 + 3.0 * 0.044715 * z * z)
 
 
 def forward(params, X):

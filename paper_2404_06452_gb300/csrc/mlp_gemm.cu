@@ -21,39 +21,45 @@ namespace {
 constexpr int BM = 128, BK = 64;
 constexpr uint64_t kWaitNs = 2000000000ull; // 2 s: far above any legitimate wait
 
-// Normal CDF Phi(z) = (1 + erf(z / sqrt 2)) / 2 with erf from Abramowitz and
-// Stegun, Handbook of Mathematical Functions (1964), formula 7.1.26:
-//   erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),
-//   t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7,
-// odd in x.  The activations are stored as bf16 (relative step 2^-8), so this
-// bound is far below what the network can see; it is branch-free and costs
-// one reciprocal and one exponential.  Also returns exp(-z^2 / 2) for GELU'.
-__device__ __forceinline__ float normal_cdf(float z, float &g)
+// The network's activation: GELU in its tanh form (Hendrycks and Gimpel,
+// "Gaussian Error Linear Units", 2016),
+//   gelu(z) = z (1 + tanh(u)) / 2,  u = sqrt(2 / pi) (z + 0.044715 z^3),
+// evaluated through (1 + tanh(u)) / 2 = 1 / (1 + exp(-2u)) with one base-2
+// exponential and one reciprocal (PTX ex2.approx / rcp.approx, relative error
+// near 2^-22), so the result is the tanh form to about 1e-6 relative: far below
+// the bf16 step (2^-8) of the stored activations.  The exponent is clamped so
+// the reciprocal never sees infinity.
+__device__ __forceinline__ float ex2_approx(float x)
 {
-    const float x = fabsf(z) * 0.70710678118654752f;
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-    float poly = fmaf(1.061405429f, t, -1.453152027f);
-    poly = fmaf(poly, t, 1.421413741f);
-    poly = fmaf(poly, t, -0.284496736f);
-    poly = fmaf(poly, t, 0.254829592f);
-    poly *= t;
-    g = __expf(-x * x);
-    const float erf_abs = 1.0f - poly * g;
-    return 0.5f + copysignf(0.5f * erf_abs, z);
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-__device__ __forceinline__ float gelu(float z)
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    float g;
-    return z * normal_cdf(z, g);
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
-// d/dz z Phi(z) = Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi)
+// sigmoid(2u) for the activation at z
+__device__ __forceinline__ float gelu_gate(float z)
+{
+    // -2u log2(e) = z (k0 + k1 z^2), k0 = -2 sqrt(2/pi) log2(e), k1 = 0.044715 k0
+    constexpr float k0 = -2.3022082f, k1 = -0.10294324f;
+    const float w = fminf(z * fmaf(k1, z * z, k0), 126.0f);
+    return rcp_approx(1.0f + ex2_approx(w));
+}
+
+__device__ __forceinline__ float gelu(float z) { return z * gelu_gate(z); }
+
+// d/dz z s(z), s = sigmoid(2u): s + z s (1 - s) d(2u)/dz, d(2u)/dz = c0 + 3 c1 z^2
 __device__ __forceinline__ float gelu_grad(float z)
 {
-    float g;
-    const float cdf = normal_cdf(z, g);
-    return fmaf(z * 0.39894228040143268f, g, cdf);
+    constexpr float c0 = 1.5957691f, c1x3 = 0.21406444f; // 2 sqrt(2/pi), 3 * 0.044715 * c0
+    const float g = gelu_gate(z);
+    return fmaf(z * g * (1.0f - g), fmaf(c1x3, z * z, c0), g);
 }
 
 // a[i] += bias[col0 + i] (columns past N get nothing); bias is 16-byte aligned
@@ -106,18 +112,18 @@ __device__ __forceinline__ void epilogue_chunk(const TcEpilogue &ep, int row, in
     case TC_EPI_DGELU: {
         __nv_bfloat16 out[32];
         if (ep.mode == TC_EPI_BIAS_GELU) {
-            __nv_bfloat16 zb[32];
             add_bias(ep, col0, full, a);
+            if (ep.Z && full) { // the pre-activation, kept for the backward pass
+                __nv_bfloat162 zb[16];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                zb[i] = __float2bfloat16_rn(a[i]);
-                out[i] = __float2bfloat16_rn(gelu(__bfloat162float(zb[i])));
-            }
-            if (ep.Z && full) {
+                for (int i = 0; i < 16; ++i) zb[i] = __floats2bfloat162_rn(a[2 * i], a[2 * i + 1]);
                 uint4 *z = (uint4 *)(ep.Z + (size_t)row * ep.ldz + col0);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) z[i] = ((const uint4 *)zb)[i];
             }
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                ((__nv_bfloat162 *)out)[i] = __floats2bfloat162_rn(gelu(a[2 * i]), gelu(a[2 * i + 1]));
         } else {
             const __nv_bfloat16 *zin = ep.Zin + (size_t)row * ep.ldzin + col0;
             __nv_bfloat16 zb[32];
