@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--top-k", type=int, default=16)
     ap.add_argument("--gemm", type=int, nargs=3, default=None, metavar=("M", "N", "K"),
                     help="time only the tensor-core GEMM C[M,N] = A[M,K] B[N,K]^T")
+    ap.add_argument("--infer", type=int, default=None, metavar="N_SYS",
+                    help="time only the network's ranking of 256 candidate orders of N_SYS search systems")
     ap.add_argument("--launch-config", type=int, default=None, help="fixed launch configuration (no autotune)")
     return ap.parse_args()
 
@@ -241,7 +243,14 @@ def _random_orders(sy, seed):
     return sy
 
 
-def surrogate_bench(pkg, ctx, train_sys, n_search, top_k):
+# training recipe: chunks of 1M systems cycling through these generators (the
+# search workload's shape twice per cycle, with random priority orders), each
+# chunk trained for TRAIN_EPOCHS passes
+TRAIN_SOURCES = ("cfg4s", "cfg2", "cfg4s", "cfg3")
+TRAIN_EPOCHS, TRAIN_LR = 3, 2e-3
+
+
+def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, lr=TRAIN_LR, sources=TRAIN_SOURCES):
     """Train the ranking network on exactly analysed systems, then compare the
     guided search (network ranking + exact confirmation of the top-k) with the
     exhaustive exact search on the same candidates."""
@@ -250,7 +259,7 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k):
     import paam_gen
 
     flops_row = 2.0 * (1024 * 256 + 256 * 256 + 256 * 256 + 256 * 64)  # one forward pass, one row
-    sources = ("cfg2", "cfg3", "cfg4s")
+    sources = tuple(sources)
     chunk = 1_000_000
     model, t_train, t_label, losses, rows = None, 0.0, 0.0, [], 0
     for i, lo in enumerate(range(0, train_sys, chunk)):
@@ -262,16 +271,16 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k):
         b = pkg.paam_rta_load_systems(ctx, sy)
         dt, (R, st, _) = _timed(lambda: pkg.analyze(ctx, b))
         t_label += dt
-        loss = np.zeros(1, np.float32)
-        opts = pkg.train_opts(epochs=1, batch_rows=8192, lr=1e-3, seed=i, epoch_loss=loss)
+        loss = np.zeros(epochs, np.float32)
+        opts = pkg.train_opts(epochs=epochs, batch_rows=8192, lr=lr, seed=i, epoch_loss=loss)
         dt, model = _timed(lambda: pkg.paam_surrogate_train(ctx, b, R, st, opts, model))
         t_train += dt
-        losses.append(round(float(loss[0]), 5))
+        losses.append(round(float(loss[-1]), 5))
         rows += n
         b.free()
     # held-out error of the predicted R/D on each training source
     mae = {}
-    for cfg in sources:
+    for cfg in dict.fromkeys(sources):
         sy = paam_gen.generate(cfg, n_sys=50_000, seed=paam_gen.CONFIGS[cfg]["seed"] + 999)
         if cfg == "cfg4s":
             sy = _random_orders(sy, 999)
@@ -331,12 +340,17 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k):
     guided(order_all, True, None)
     t_fb, _ = _timed(lambda: guided(order_all, True, None), 3)
     fb_same = bool(np.array_equal(first.cpu().numpy() >= 0, has))
+    # recall of the network's ranking at other budgets (an admissible order among the first k)
+    ranked_all = order_all.cpu().numpy()
+    ok_in_rank = np.take_along_axis(cx, ranked_all, 1)
+    recall_at = {str(k): float(ok_in_rank[:, :k][has].any(axis=1).mean()) for k in (1, 2, 4, 8, 16, 32, 64)
+                 if k <= K} if has.any() else {}
     b.free()
     model.free()
     return {
-        "train": {"systems": rows, "sources": list(sources), "epochs": 1, "minibatch": 8192,
+        "train": {"systems": rows, "sources": list(sources), "epochs": epochs, "lr": lr, "minibatch": 8192,
                   "label_analysis_s": round(t_label, 4), "train_s": round(t_train, 4),
-                  "train_tflops": 3 * flops_row * rows / t_train / 1e12, "chunk_loss": losses,
+                  "train_tflops": 3 * flops_row * rows * epochs / t_train / 1e12, "chunk_loss": losses,
                   "heldout_mae_R_over_D": mae},
         "workload": f"cfg4s: {S} systems x {K} candidate orders",
         "exhaustive_systems_per_s": S / t_ex, "exhaustive_ms": t_ex * 1e3,
@@ -345,7 +359,7 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k):
         "speedup_vs_exhaustive": t_ex / t_g, "speedup_vs_early_exit": t_ee / t_g,
         "infer_ms": t_inf * 1e3, "infer_tflops": flops_row * S * K / t_inf / 1e12,
         "false_accepts": false_accepts, "recall": recall, "recall_first_k_slots": slot_recall,
-        "recall_random_k": rand_recall,
+        "recall_random_k": rand_recall, "recall_at_k": recall_at,
         "fallback": {"systems_per_s": S / t_fb, "ms": t_fb * 1e3, "same_verdicts_as_exhaustive": fb_same,
                      "speedup_vs_exhaustive": t_ex / t_fb, "speedup_vs_early_exit": t_ee / t_fb},
     }
@@ -382,6 +396,35 @@ def gemm_bench(pkg, M, N, K, steps, warmup):
     return {"M": M, "N": N, "K": K, "ms": ms, "tflops": tf, "peak_tflops": pk["bf16_tflops"],
             "frac": tf / pk["bf16_tflops"], "peak_src": pk["src"], "max_rel_err_vs_fp32": rel,
             "err_flag": int(err.item())}
+
+
+def infer_bench(pkg, n_sys, steps, warmup):
+    """The network's ranking alone (features, 4 layers with the fused score,
+    top-k) on the search workload, random weights: what a step of guided search
+    spends before its exact confirmation."""
+    import torch
+
+    import paam_gen
+
+    ctx = pkg.Context(0)
+    rng = np.random.default_rng(1)
+    sizes = [(1024, 256), (256, 256), (256, 256), (256, 64)]
+    p = np.concatenate([np.concatenate([rng.uniform(-1, 1, fi * fo) * np.sqrt(6 / fi), rng.uniform(-.1, .1, fo)])
+                        for fi, fo in sizes]).astype(np.float32)
+    m = pkg.Model.create(ctx, 1)
+    m.set_params(p)
+    sy = paam_gen.generate("cfg4s", n_sys=n_sys)
+    ranks = paam_gen.candidate_ranks(sy, SEARCH_K, paam_gen.CONFIGS["cfg4s"]["seed"] + 7)
+    b = pkg.paam_rta_load_systems(ctx, sy)
+    r = torch.from_numpy(ranks).cuda()
+    ranked = torch.empty((n_sys, 16), dtype=torch.int32, device="cuda")
+    for _ in range(warmup):
+        pkg.paam_surrogate_infer(ctx, m, b, r, 16, ranked)
+    t, _ = _timed(lambda: pkg.paam_surrogate_infer(ctx, m, b, r, 16, ranked), max(1, steps))
+    b.free()
+    m.free()
+    return {"systems": n_sys, "candidates": n_sys * SEARCH_K, "ms": t * 1e3,
+            "candidates_per_s": n_sys * SEARCH_K / t}
 
 
 def search_cpu_baseline(n_sys):
@@ -421,6 +464,10 @@ def run_ours(args):
     if args.gemm:
         if rank == 0:
             print(json.dumps({"gemm": gemm_bench(pkg, *args.gemm, args.steps, args.warmup)}), flush=True)
+        return
+    if args.infer:
+        if rank == 0:
+            print(json.dumps({"infer": infer_bench(pkg, args.infer, args.steps, args.warmup)}), flush=True)
         return
 
     n_sys = args.n_sys or paam_gen.CONFIGS[WORKLOAD]["n_sys"]

@@ -182,6 +182,9 @@ struct CandSmem {
     float uEpS[32], uE[32], uS[32], EpS[32], Emax[32], M[32], D[32];
     uint8_t x[32], lc[32], user[32];
     float UcpuX[32], EpSX[32];
+    float invD[32];                   // 1 / D per chain
+    int32_t bkt[32];                  // bucket of the accelerator user of rank r (R2)
+    float inv_n;
     uint8_t ord[CF_THREADS / 16][16]; // per 16-lane segment: chain at position k
     uint8_t ord_hi[CF_THREADS / 32][16]; // positions 16..31 of 32-lane segments
 };
@@ -248,6 +251,7 @@ __global__ void __launch_bounds__(CF_THREADS) cand_features_kernel(BatchDev b, c
                 s.Emax[t] = Em;
                 s.M[t] = Mc;
                 s.D[t] = Dc;
+                s.invD[t] = 1.0f / Dc;
                 s.x[t] = (uint8_t)xc;
                 s.user[t] = dl > 0 ? 1 : 0;
                 const int kc = b.exec_core[x0 + xc]; // local core: lowest executor on the same core
@@ -289,15 +293,22 @@ __global__ void __launch_bounds__(CF_THREADS) cand_features_kernel(BatchDev b, c
         __syncthreads();
         int n_users = 0;
         for (int c = 0; c < n; ++c) n_users += s.user[c];
+        if (t < n_users) s.bkt[t] = (int32_t)((int64_t)t * n_buckets / n_users);
+        if (t == 0) s.inv_n = 1.0f / (float)n;
+        __syncthreads();
+        const float inv_n = s.inv_n;
         // ---- one candidate per segment ---------------------------------------------
         // lane k reads chain k's rank; the next candidate's row is fetched one
         // iteration ahead so its latency overlaps this candidate's work
-        int r_next = (sg < K && k < n) ? ranks[(sys * K + sg) * (int64_t)nmax + k] : -1;
+        const int16_t *rrow = ranks + (sys * K + sg) * (int64_t)nmax + k; // this lane's entry, candidate sg
+        const int64_t rstep = (int64_t)SEGS * nmax;
+        int r_next = (sg < K && k < n) ? *rrow : -1;
         for (int cand0 = 0; cand0 < K; cand0 += SEGS) {
             const int cand = cand0 + sg;
             const bool live = cand < K; // whole segments are live or not
             const int r = r_next;
-            r_next = (cand + SEGS < K && k < n) ? ranks[(sys * K + cand + SEGS) * (int64_t)nmax + k] : -1;
+            rrow += rstep;
+            r_next = (cand + SEGS < K && k < n) ? *rrow : -1;
             const bool in = r >= 0 && r < n;
             unsigned bits = (k < n && in) ? (1u << r) : 0u;
 #pragma unroll
@@ -321,7 +332,7 @@ __global__ void __launch_bounds__(CF_THREADS) cand_features_kernel(BatchDev b, c
             const int lcx = act ? s.lc[c] : 255;
             const bool user = act && s.user[c];
             const float uEpS = act ? s.uEpS[c] : 0.0f, EpS = act ? s.EpS[c] : 0.0f;
-            const float Emax = act ? s.Emax[c] : 0.0f, Mc = act ? s.M[c] : 0.0f, Dc = act ? s.D[c] : 1.0f;
+            const float Emax = act ? s.Emax[c] : 0.0f, Mc = act ? s.M[c] : 0.0f, iD = act ? s.invD[c] : 1.0f;
             const float uS = act ? s.uS[c] : 0.0f;
             // same executor / same core within this segment
             const unsigned same = __match_any_sync(full, (unsigned)(x | (sg << 8))) & segmask;
@@ -370,7 +381,7 @@ __global__ void __launch_bounds__(CF_THREADS) cand_features_kernel(BatchDev b, c
             if (k == 0) hps = 0.0f;
             const unsigned users = __ballot_sync(full, user) & segmask;
             const int urank = __popc(users & lt);
-            const int key = urank < n_users ? (int)((int64_t)urank * n_buckets / n_users) : 0x7fffffff;
+            const int key = urank < n_users ? s.bkt[urank] : 0x7fffffff;
             // blk: segmented suffix maximum of M* over users with the same key
             float acc = user ? Mc : 0.0f;
 #pragma unroll
@@ -387,11 +398,11 @@ __global__ void __launch_bounds__(CF_THREADS) cand_features_kernel(BatchDev b, c
                 uint4 *out = reinterpret_cast<uint4 *>(X + ((si * K + cand) * (int64_t)(slots * NF)));
                 if (act) {
                     uint4 lo = s.tmpl[c][0], hi = s.tmpl[c][1];
-                    lo.z |= bf16_bits((float)k / (float)n);                    // 4: rank / n
+                    lo.z |= bf16_bits((float)k * inv_n);                       // 4: rank / n
                     hi.x = bf16_bits(hpU) | bf16_bits(hppU) << 16;             // 8, 9
-                    hi.y = bf16_bits(hps) | bf16_bits(B / Dc) << 16;           // 10, 11
-                    hi.z |= bf16_bits(blk / Dc);                               // 12
-                    hi.w |= bf16_bits((hpE + hppE) / Dc);                      // 14
+                    hi.y = bf16_bits(hps) | bf16_bits(B * iD) << 16;           // 10, 11
+                    hi.z |= bf16_bits(blk * iD);                               // 12
+                    hi.w |= bf16_bits((hpE + hppE) * iD);                      // 14
                     out[2 * c] = lo;
                     out[2 * c + 1] = hi;
                 }

@@ -12,6 +12,7 @@ enum TcEpiMode {
     TC_EPI_BIAS_F32 = 2,   // C = acc + bias
     TC_EPI_DGELU = 3,      // H = bf16(acc * gelu'(Zin)); HT = H^T (optional)
     TC_EPI_ATOMIC_F32 = 4, // C += acc (split-K partial sums)
+    TC_EPI_ROWMAX = 5,     // C[row] = max(C[row], 0, max over the row's valid columns of acc + bias)
 };
 
 struct TcEpilogue {
@@ -27,6 +28,12 @@ struct TcEpilogue {
     int ldh;
     __nv_bfloat16 *HT;             // H transposed ([N][M]), optional
     int ldht;
+    // TC_EPI_ROWMAX: row r belongs to system sys0 + r / rows_per_sys, whose
+    // chain count (sys_off[s + 1] - sys_off[s]) is the number of valid columns;
+    // C[r] must start non-negative (the maximum is taken on the float bits)
+    const int64_t *sys_off;
+    int64_t sys0;
+    int rows_per_sys;
 };
 
 // C[M, N] (epilogue) = A[M, K] * B[N, K]^T with A, B bf16 row-major, lda/ldb in

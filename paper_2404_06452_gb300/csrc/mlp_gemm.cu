@@ -102,6 +102,18 @@ __device__ __forceinline__ void epilogue_chunk(const TcEpilogue &ep, int row, in
         }
         break;
     }
+    case TC_EPI_ROWMAX: {
+        const int64_t sys = ep.sys0 + row / ep.rows_per_sys;
+        const int n = (int)(ep.sys_off[sys + 1] - ep.sys_off[sys]);
+        if (col0 >= n) break;
+        add_bias(ep, col0, full, a);
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (col0 + i < n) m = fmaxf(m, a[i]); // a NaN prediction is ignored
+        atomicMax(reinterpret_cast<int *>(ep.C) + row, __float_as_int(m));
+        break;
+    }
     case TC_EPI_ATOMIC_F32: {
         float *c = ep.C + (size_t)row * ep.ldc + col0;
         for (int i = 0; i < 32; ++i)

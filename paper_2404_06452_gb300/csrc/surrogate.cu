@@ -155,19 +155,6 @@ __global__ void to_bf16_kernel(const float *W, int64_t n, int rows, int cols, __
     }
 }
 
-// ---- inference: score = largest predicted R / D over the system's chains
-__global__ void score_kernel(const float *Y, BatchDev b, int64_t sys0, int32_t K, int64_t items, float *score)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < items; i += stride) {
-        const int64_t sys = sys0 + i / K;
-        const int n = (int)(b.sys_chain_off[sys + 1] - b.sys_chain_off[sys]);
-        float s = 0.0f;
-        for (int c = 0; c < n && c < NCH; ++c) s = fmaxf(s, Y[i * NCH + c]);
-        score[i] = s;
-    }
-}
-
 // ---- per system: the top_k candidates in increasing score (ties: lower index)
 __global__ void topk_kernel(const float *score, int64_t n_sys, int32_t K, int32_t top_k, int32_t *ranked)
 {
@@ -432,7 +419,19 @@ int input_width(const paam_batch *b)
 // when training.  kx < 1024 reads only the first kx input columns of layer 1:
 // exact when the remaining feature columns are zero (chain slots past every
 // system's chains), since their products add nothing to the fp32 sums.
-int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool train, cudaStream_t s)
+// With score != NULL the output layer writes, per row, the largest
+// prediction over the row's system's chains (at least 0) into score[row]
+// (zeroed here) instead of all 64 outputs into w.Y; rows are candidates of
+// systems sys0.. in groups of K.
+struct ScoreOut {
+    float *score;
+    const int64_t *sys_off;
+    int64_t sys0;
+    int K;
+};
+
+int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool train, cudaStream_t s,
+            const ScoreOut *so = nullptr)
 {
     const int rows = w.rows;
     for (int l = 0; l < 3; ++l) {
@@ -458,6 +457,14 @@ int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool t
     g.ep.bias = m->bias[3];
     g.ep.C = w.Y;
     g.ep.ldc = OUT[3];
+    if (so) {
+        PAAM_CUDA_TRY(cudaMemsetAsync(so->score, 0, 4 * (size_t)rows, s));
+        g.ep.mode = TC_EPI_ROWMAX;
+        g.ep.C = so->score;
+        g.ep.sys_off = so->sys_off;
+        g.ep.sys0 = so->sys0;
+        g.ep.rows_per_sys = so->K;
+    }
     return tc_gemm(g, w.err, s);
 }
 
@@ -663,13 +670,8 @@ extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const pa
         Work wc = w;
         wc.rows = (int)items;
         rc = paam_launch_features(b, ranks, K, nmax, s0, items, n_buckets, kappa_ns, kx, wc.Xb, s);
-        if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, kx, false, s);
-        if (rc == PAAM_OK) {
-            score_kernel<<<grid_for(items, 256, ctx->n_sm), 256, 0, s>>>(wc.Y, batch_dev(b), s0, K, items,
-                                                                         sc + s0 * K);
-            if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-            paam_count_launch();
-        }
+        const ScoreOut so = {sc + s0 * K, b->sys_chain_off, s0, K};
+        if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, kx, false, s, &so);
     }
     if (rc == PAAM_OK) {
         topk_kernel<<<(unsigned)((b->n_sys + 7) / 8), 256, 0, s>>>(sc, b->n_sys, K, top_k, ranked);
