@@ -88,8 +88,8 @@ def analyze(sy, n_buckets: int = 1, eps: int = 0, kappa: int = 0, blocking_mode:
     ``verdict`` (uint8 per system) and optionally ``aux`` ([n_chain, 12]) and
     ``work`` (interference terms per system).
     """
-    if blocking_mode != 0:
-        raise NotImplementedError("only the paper's literal blocking term (Lemma 4) is defined here")
+    if blocking_mode not in (0, 1):
+        raise ValueError("blocking_mode: 0 (Lemma 4 as printed) or 1 (safe reading)")
     lib = _lib("paam_oracle")
     a = _arrays(sy)
     if derive_exec_prio:
@@ -103,13 +103,13 @@ def analyze(sy, n_buckets: int = 1, eps: int = 0, kappa: int = 0, blocking_mode:
     f = lib.oracle_analyze
     f.restype = None
     f.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 13 + [
-        ctypes.c_int32, ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 5
+        ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32] + [ctypes.c_void_p] * 5
 
     def run(r):
         f(r[0], r[1], _p(a["sys_chain_off"]), _p(a["chain_cb_off"]), _p(a["cb_seg_off"]), _p(a["T"]),
           _p(a["D"]), _p(a["prio"]), _p(a["exec"]), _p(a["spin"]), _p(a["E"]), _p(a["A"]),
           _p(a["sys_exec_off"]), _p(a["exec_core"]), _p(a["exec_prio"]), int(n_buckets), int(eps),
-          int(kappa), _p(R), _p(st), _p(verdict), _p(ax), _p(wk))
+          int(kappa), int(blocking_mode), _p(R), _p(st), _p(verdict), _p(ax), _p(wk))
 
     rs = _ranges(ns, threads)
     if len(rs) <= 1:
@@ -130,7 +130,7 @@ AUX_FIELDS = ("E", "Emax", "delta", "S", "M", "bucket", "blk", "B", "Hseg", "Hst
 
 
 def search(sy, ranks: np.ndarray, n_buckets: int = 1, eps: int = 0, kappa: int = 0,
-           stop_at_first: bool = False, threads: int = 1):
+           stop_at_first: bool = False, threads: int = 1, blocking_mode: int = 0):
     """Exact priority-assignment search over candidate rank orders.
 
     ``ranks[s, k, c]`` is the rank (0 = highest priority) of chain c of system
@@ -148,15 +148,16 @@ def search(sy, ranks: np.ndarray, n_buckets: int = 1, eps: int = 0, kappa: int =
     f = lib.oracle_search
     f.restype = None
     f.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 12 + [
-        ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
-        ctypes.c_int32] + [ctypes.c_void_p] * 4
+        ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+        ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4
 
     def run(r):
         Rs = np.zeros(nc, np.int64)
         sts = np.zeros(nc, np.uint8)
         f(r[0], r[1], _p(a["sys_chain_off"]), _p(a["chain_cb_off"]), _p(a["cb_seg_off"]), _p(a["T"]),
           _p(a["D"]), _p(a["prio"]), _p(a["exec"]), _p(a["spin"]), _p(a["E"]), _p(a["A"]),
-          _p(a["sys_exec_off"]), _p(a["exec_core"]), int(n_buckets), int(eps), int(kappa), _p(ranks),
+          _p(a["sys_exec_off"]), _p(a["exec_core"]), int(n_buckets), int(eps), int(kappa), int(blocking_mode),
+          _p(ranks),
           K, nmax, 1 if stop_at_first else 0, _p(cand_ok), _p(first_ok), _p(Rs), _p(sts))
 
     rs = _ranges(S, threads)

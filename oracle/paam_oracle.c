@@ -102,8 +102,8 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                            const int64_t *E, const int64_t *A, const int64_t *sys_exec_off,
                            const int32_t *exec_core, const int32_t *exec_prio,
                            const int16_t *rank, int32_t n_buckets, int64_t eps, int64_t kappa,
-                           int64_t *R_out, uint8_t *st_out, uint8_t *verdict, int64_t *aux,
-                           int64_t *work_out)
+                           int32_t blocking_mode, int64_t *R_out, uint8_t *st_out, uint8_t *verdict,
+                           int64_t *aux, int64_t *work_out)
 {
     const int64_t c0 = sys_chain_off[s], n = sys_chain_off[s + 1] - c0;
     const int64_t x0 = sys_exec_off[s], nx = sys_exec_off[s + 1] - x0;
@@ -181,7 +181,11 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                 ch[c].B = ch[l].Emax;
     }
 
-    /* step 5: per-segment handling times (Lemma 2, Eq. 3) */
+    /* step 5: per-segment handling times (Lemma 2, Eq. 3); each segment's
+     * bound is kept for the safe blocking term below */
+    const int64_t q_sys = n > 0 ? ch[0].seg_lo : 0;
+    const int64_t n_q = n > 0 ? ch[n - 1].seg_hi - q_sys : 0;
+    int64_t *hq = (int64_t *)calloc((size_t)(n_q > 0 ? n_q : 1), sizeof(int64_t));
     for (int64_t c = 0; c < n; ++c) {
         ch[c].Hseg = 0;
         for (int64_t q = ch[c].seg_lo; q < ch[c].seg_hi; ++q) {
@@ -208,12 +212,39 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                     break;
                 }
             }
+            hq[q - q_sys] = h;
             if (h == O_INF || ch[c].Hseg == O_INF)
                 ch[c].Hseg = O_INF;
             else
                 ch[c].Hseg += h;
         }
     }
+
+    /* safe blocking (blocking_mode 1, a reading beyond the paper): a
+     * lower-priority callback keeps the single-threaded executor for its CPU
+     * work and for each of its accelerator requests, each bounded by its
+     * segment's Lemma 2 handling time plus the overhead eps; B_c is the
+     * longest such callback of a lower-priority chain on c's executor, and
+     * infinite when one of those segments has no bound */
+    if (blocking_mode == 1) {
+        int64_t *hold = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+        for (int64_t l = 0; l < n; ++l) {
+            const int64_t cb_lo = chain_cb_off[c0 + l], cb_hi = chain_cb_off[c0 + l + 1];
+            for (int64_t b = cb_lo; b < cb_hi; ++b) {
+                int64_t t = E[b];
+                for (int64_t q = cb_seg_off[b]; q < cb_seg_off[b + 1] && t != O_INF; ++q)
+                    t = hq[q - q_sys] == O_INF ? O_INF : t + hq[q - q_sys] + eps;
+                if (t > hold[l]) hold[l] = t;
+            }
+        }
+        for (int64_t c = 0; c < n; ++c) {
+            ch[c].B = 0;
+            for (int64_t l = 0; l < n; ++l)
+                if (ch[l].exec == ch[c].exec && ch[l].prio < ch[c].prio && hold[l] > ch[c].B) ch[c].B = hold[l];
+        }
+        free(hold);
+    }
+    free(hq);
 
     /* step 6: Theorem 1 (Eq. 6) chain by chain, each after every chain whose
      * H* it needs: higher-priority chains of its executor and spinning chains
@@ -241,6 +272,11 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
             progressed = 1;
             if (dep_failed) {
                 ch[c].status = ST_DEP;
+                ch[c].R = -1;
+                continue;
+            }
+            if (ch[c].B == O_INF) { /* unbounded blocking (safe mode only) */
+                ch[c].status = ST_OVERRUN;
                 ch[c].R = -1;
                 continue;
             }
@@ -321,21 +357,23 @@ void oracle_analyze_iters(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
                           const uint8_t *spin, const int64_t *E, const int64_t *A,
                           const int64_t *sys_exec_off, const int32_t *exec_core,
                           const int32_t *exec_prio, int32_t n_buckets, int64_t eps, int64_t kappa,
-                          int64_t *R, uint8_t *status, int64_t *seg_iters, int64_t *chain_iters)
+                          int32_t blocking_mode, int64_t *R, uint8_t *status, int64_t *seg_iters,
+                          int64_t *chain_iters)
 {
     for (int64_t s = lo; s < hi; ++s) {
         g_seg_iters = 0;
         g_chain_iters = 0;
         analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A,
-                       sys_exec_off, exec_core, exec_prio, NULL, n_buckets, eps, kappa, R, status,
-                       NULL, NULL, NULL);
+                       sys_exec_off, exec_core, exec_prio, NULL, n_buckets, eps, kappa, blocking_mode, R,
+                       status, NULL, NULL, NULL);
         seg_iters[s] = g_seg_iters;
         chain_iters[s] = g_chain_iters;
     }
 }
 
 /*
- * Analyse systems [lo, hi).  exec_prio may be NULL (derived).  aux, when
+ * Analyse systems [lo, hi).  exec_prio may be NULL (derived).  blocking_mode
+ * 0 is Lemma 4 as printed, 1 the safe reading (see step 5).  aux, when
  * non-NULL, receives 12 int64 per chain: E, Emax, delta, S*, M*, bucket, blk,
  * B, Hseg (-1 = infinite), H* at R (-1 unless SCHED), executor priority,
  * chain priority.  work, when non-NULL, receives per system the number of
@@ -347,12 +385,13 @@ void oracle_analyze(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
                     const uint8_t *spin, const int64_t *E, const int64_t *A,
                     const int64_t *sys_exec_off, const int32_t *exec_core,
                     const int32_t *exec_prio, int32_t n_buckets, int64_t eps, int64_t kappa,
-                    int64_t *R, uint8_t *status, uint8_t *verdict, int64_t *aux, int64_t *work)
+                    int32_t blocking_mode, int64_t *R, uint8_t *status, uint8_t *verdict, int64_t *aux,
+                    int64_t *work)
 {
     for (int64_t s = lo; s < hi; ++s)
         analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A,
-                       sys_exec_off, exec_core, exec_prio, NULL, n_buckets, eps, kappa, R, status,
-                       verdict, aux, work);
+                       sys_exec_off, exec_core, exec_prio, NULL, n_buckets, eps, kappa, blocking_mode, R,
+                       status, verdict, aux, work);
 }
 
 /*
@@ -366,7 +405,7 @@ void oracle_search(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
                    const int64_t *D, const int32_t *prio, const int32_t *exec, const uint8_t *spin,
                    const int64_t *E, const int64_t *A, const int64_t *sys_exec_off,
                    const int32_t *exec_core, int32_t n_buckets, int64_t eps, int64_t kappa,
-                   const int16_t *ranks, int32_t K, int32_t nmax, int32_t stop_at_first,
+                   int32_t blocking_mode, const int16_t *ranks, int32_t K, int32_t nmax, int32_t stop_at_first,
                    uint8_t *cand_ok, int32_t *first_ok, int64_t *R_scratch, uint8_t *st_scratch)
 {
     for (int64_t s = lo; s < hi; ++s) {
@@ -375,7 +414,7 @@ void oracle_search(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
             uint8_t v = 0;
             analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E,
                            A, sys_exec_off, exec_core, NULL, ranks + (s * (int64_t)K + k) * nmax,
-                           n_buckets, eps, kappa, R_scratch, st_scratch, NULL, NULL, NULL);
+                           n_buckets, eps, kappa, blocking_mode, R_scratch, st_scratch, NULL, NULL, NULL);
             v = 1;
             for (int64_t c = sys_chain_off[s]; c < sys_chain_off[s + 1]; ++c)
                 if (st_scratch[c] != ST_SCHED) v = 0;

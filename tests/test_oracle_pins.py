@@ -202,6 +202,45 @@ def test_des_never_exceeds_bound():
     assert checked > 300
 
 
+def test_des_never_exceeds_safe_bound():
+    """The safe blocking reading (blocking_mode=1: a lower-priority callback
+    holds the executor for its CPU work and for each of its accelerator
+    requests, bounded by Lemma 2 plus eps) covers every observed response,
+    including where Lemma 4 as printed does not."""
+    rng = random.Random(12)
+    checked, exposed = 0, 0
+    for trial in range(3000):
+        d = tiny.tiny_system(rng, n_max=3, cb_max=2, x_max=2, exec_per_core=2, periods=(4, 6, 8, 12),
+                             e_max=2, a_max=2, p_seg=0.5, p_spin=0.5)
+        p = dict(n_buckets=rng.choice([1, 2]), eps=rng.choice([0, 1]), kappa=rng.choice([0, 1]))
+        out = oracle.analyze(tiny.to_systems([d]), blocking_mode=1, **p)
+        if not out["verdict"][0]:
+            continue
+        obs = des_sim.explore(d, **p)
+        for c, (r, o) in enumerate(zip(out["R"].tolist(), obs)):
+            assert o <= r, (d, p, c, r, o)
+            checked += 1
+            exposed += int(_lp_same_exec_has_segments(d, c))
+    assert checked > 1000 and exposed > 60, (checked, exposed)
+
+
+def test_safe_blocking_relations():
+    """Without accelerator segments the two readings coincide; with them the
+    safe bound is never below the literal one, and admits no more systems."""
+    sy = g.generate("cfg2", n_sys=3000, p_acc=0.0, p_spin=0.5)
+    a, b = oracle.analyze(sy), oracle.analyze(sy, blocking_mode=1)
+    assert np.array_equal(a["R"], b["R"]) and np.array_equal(a["status"], b["status"])
+    sy = g.generate("cfg1", n_sys=3000, p_spin=0.5, util_lo=0.2, util_hi=0.2)
+    for p in (dict(), dict(eps=391_000, kappa=129_180, n_buckets=2)):
+        a, b = oracle.analyze(sy, aux=True, **p), oracle.analyze(sy, blocking_mode=1, aux=True, **p)
+        both = (a["status"] == 0) & (b["status"] == 0)
+        assert np.all(b["R"][both] >= a["R"][both])
+        assert np.all(a["verdict"] >= b["verdict"])
+        B = oracle.AUX_FIELDS.index("B")
+        assert np.all(b["aux"][:, B] >= a["aux"][:, B]) and np.any(b["aux"][:, B] > a["aux"][:, B])
+        assert b["verdict"].mean() > 0.05
+
+
 def test_des_witness_literal_blocking_gap():
     """A finding about Lemma 4 used inside Theorem 1: B_c counts only the CPU
     WCET of one lower-priority callback, but that callback keeps the
@@ -215,3 +254,7 @@ def test_des_witness_literal_blocking_gap():
     out = oracle.analyze(tiny.to_systems([d]), **p)
     assert out["R"].tolist()[0] == 3 and out["verdict"][0] == 1
     assert des_sim.explore(d, **p)[0] == 4
+    # the safe reading: B = E + (h + eps) = 2 + (1 + 1) = 4 for the low chain's
+    # one callback (its segment's Lemma 2 bound is h = A* = 1), so R = 4 + 1 = 5
+    safe = oracle.analyze(tiny.to_systems([d]), blocking_mode=1, aux=True, **p)
+    assert safe["R"].tolist()[0] == 5 and safe["aux"][0, oracle.AUX_FIELDS.index("B")] == 4
