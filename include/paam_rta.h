@@ -108,8 +108,15 @@ typedef struct {
  *                  users are ranked by descending chain priority and rank r of
  *                  |U| users goes to bucket floor(r * n / |U|)
  *   blocking_mode  0: B_c as in Lemma 4 (largest CPU WCET of one callback of
- *                  a lower-priority chain on the executor); other values
- *                  PAAM_E_UNSUPPORTED in this build
+ *                  a lower-priority chain on the executor);
+ *                  1: a safe reading of the same blocking: that callback also
+ *                  holds the single-threaded executor during each of its
+ *                  accelerator requests, so B_c is the largest E_i + sum over
+ *                  callback i's segments of (Lemma 2 bound + eps) of a
+ *                  lower-priority chain on the executor, and a segment
+ *                  without a bound (above its chain's deadline) makes the
+ *                  chain PAAM_ST_OVERRUN.  Mode 1 runs the exact int64 kernel
+ *                  for every system (slower).  Other values: PAAM_E_INVAL
  *   eps_ns         per-request server overhead epsilon (Eq. 1), 0..2^32
  *   kappa_ns       device preemption cost kappa, A* = A + 2 kappa, 0..2^32
  */
@@ -164,8 +171,8 @@ void paam_batch_free(paam_batch *b);
  * launch configuration) captures the analysis into a CUDA graph owned by the
  * batch; later calls with the same key replay it on `stream`.  A batch may be
  * analysed by one host thread at a time.  Errors: PAAM_E_INVAL (NULL outputs, n_buckets < 1),
- * PAAM_E_RANGE (eps or kappa above PAAM_MAX_OVERHEAD), PAAM_E_UNSUPPORTED
- * (blocking_mode != 0), PAAM_E_CUDA (launch failure).
+ * PAAM_E_RANGE (eps or kappa above PAAM_MAX_OVERHEAD), PAAM_E_INVAL
+ * (blocking_mode not 0 or 1), PAAM_E_CUDA (launch failure).
  */
 int paam_rta_analyze_batch(paam_ctx *ctx, const paam_batch *batch, const paam_analysis_opts *opts,
                            int64_t *R, uint8_t *status, uint8_t *verdict, void *stream);

@@ -28,7 +28,8 @@ def to_device(sy, device="cuda", pin: bool = False):
     return out
 
 
-def analyze(ctx: B.Context, batch: B.Batch, n_buckets: int = 1, eps: int = 0, kappa: int = 0, stream=None):
+def analyze(ctx: B.Context, batch: B.Batch, n_buckets: int = 1, eps: int = 0, kappa: int = 0, stream=None,
+            blocking_mode: int = 0):
     """Run ``paam_rta_analyze_batch`` into fresh torch device tensors."""
     import torch
 
@@ -36,12 +37,13 @@ def analyze(ctx: B.Context, batch: B.Batch, n_buckets: int = 1, eps: int = 0, ka
     R = torch.empty(batch.n_chain, dtype=torch.int64, device=dev)
     st = torch.empty(batch.n_chain, dtype=torch.uint8, device=dev)
     v = torch.empty(batch.n_sys, dtype=torch.uint8, device=dev)
-    B.paam_rta_analyze_batch(ctx, batch, B.analysis_opts(n_buckets, eps, kappa), R, st, v, stream=stream)
+    B.paam_rta_analyze_batch(ctx, batch, B.analysis_opts(n_buckets, eps, kappa, blocking_mode), R, st, v,
+                             stream=stream)
     return R, st, v
 
 
 def search(ctx: B.Context, batch: B.Batch, ranks, n_buckets: int = 1, eps: int = 0, kappa: int = 0,
-           stop_at_first: bool = False, want_cand_ok: bool = True, stream=None):
+           stop_at_first: bool = False, want_cand_ok: bool = True, stream=None, blocking_mode: int = 0):
     """Run ``paam_rta_search_priorities`` on device rank rows; returns torch
     tensors (first_ok [S], cand_ok [S, K] or None)."""
     import torch
@@ -50,6 +52,7 @@ def search(ctx: B.Context, batch: B.Batch, ranks, n_buckets: int = 1, eps: int =
     S, K, _ = ranks.shape
     first_ok = torch.empty(S, dtype=torch.int32, device=dev)
     cand_ok = torch.empty((S, K), dtype=torch.uint8, device=dev) if want_cand_ok else None
-    B.paam_rta_search_priorities(ctx, batch, B.analysis_opts(n_buckets, eps, kappa), ranks, stop_at_first,
+    B.paam_rta_search_priorities(ctx, batch, B.analysis_opts(n_buckets, eps, kappa, blocking_mode), ranks,
+                                 stop_at_first,
                                  cand_ok, first_ok, stream=stream)
     return first_ok, cand_ok

@@ -18,7 +18,7 @@ constexpr int64_t kInf = INT64_MAX;
 template <int MAXN>
 struct SysSmem {
     int64_t T[MAXN], D[MAXN], E[MAXN], S[MAXN], Hs[MAXN], B[MAXN], blk[MAXN], Hseg[MAXN];
-    int64_t Emax[MAXN], M[MAXN], seglo[MAXN];
+    int64_t Emax[MAXN], M[MAXN], seglo[MAXN], hold[MAXN];
     int32_t prio[MAXN], eprio[MAXN], delta[MAXN], core[MAXN], exec[MAXN], bucket[MAXN];
     uint8_t spin[MAXN], status[MAXN], order[MAXN];
 };
@@ -167,29 +167,53 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     __syncwarp(gmask);
 
     // ---- Lemma 2 (Eq. 3): per-segment handling times, chains in parallel ---
+    // Safe blocking (blocking_mode 1) also needs, per chain, its longest
+    // callback with every request: hold = max_i E_i + sum over i's segments
+    // of (Lemma 2 bound + eps), infinite when a segment has no bound.
+    const bool safe = p.blocking_mode == 1;
     for (int c = lane; c < n; c += G) {
-        int64_t Hseg = 0;
+        int64_t Hseg = 0, hold = 0;
         const int64_t Dc = s.D[c], blk = s.blk[c];
         const int32_t pc = s.prio[c];
-        for (int j = 0; j < s.delta[c] && Hseg != kInf; ++j) {
-            const int64_t a = b.A[s.seglo[c] + j] + kappa2;
-            int64_t h = a + blk;
-            for (;;) {
-                if (h > Dc) {
-                    Hseg = kInf;
-                    break;
+        const int64_t g = c0 + c;
+        const int64_t cb1 = b.chain_cb_off[g + 1];
+        for (int64_t cb = b.chain_cb_off[g]; cb < cb1 && Hseg != kInf; ++cb) {
+            int64_t t = b.E[cb];
+            const int64_t q1 = b.cb_seg_off[cb + 1];
+            for (int64_t q = b.cb_seg_off[cb]; q < q1 && Hseg != kInf; ++q) {
+                const int64_t a = b.A[q] + kappa2;
+                int64_t h = a + blk;
+                for (;;) {
+                    if (h > Dc) {
+                        Hseg = kInf;
+                        break;
+                    }
+                    int64_t nh = a + blk;
+                    for (int k = 0; k < n; ++k)
+                        if (s.delta[k] > 0 && s.prio[k] > pc) nh += arrivals(h, s.T[k]) * s.S[k];
+                    if (nh == h) break; // each step raises some ceil(h/T_k): at most n*(D/Tmin+1) steps
+                    h = nh;
                 }
-                int64_t nh = a + blk;
-                for (int k = 0; k < n; ++k)
-                    if (s.delta[k] > 0 && s.prio[k] > pc) nh += arrivals(h, s.T[k]) * s.S[k];
-                if (nh == h) break; // each step raises some ceil(h/T_k): at most n*(D/Tmin+1) steps
-                h = nh;
+                if (Hseg != kInf) {
+                    Hseg += h;
+                    t += h + eps;
+                }
             }
-            if (Hseg != kInf) Hseg += h;
+            if (safe && t > hold) hold = t;
         }
         s.Hseg[c] = Hseg;
+        s.hold[c] = Hseg == kInf ? kInf : hold;
     }
     __syncwarp(gmask);
+    if (safe) { // B_c: the longest hold of a lower-priority chain on the same executor
+        for (int c = lane; c < n; c += G) {
+            int64_t B = 0;
+            for (int l = 0; l < n; ++l)
+                if (s.exec[l] == s.exec[c] && s.prio[l] < s.prio[c] && s.hold[l] > B) B = s.hold[l];
+            s.B[c] = B;
+        }
+        __syncwarp(gmask);
+    }
 
     // ---- Theorem 1 (Eq. 6) chain by chain ----------------------------------
     for (int k = 0; k < n; ++k) {
@@ -207,7 +231,9 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
         int64_t R = -1;
         uint8_t st = PAAM_ST_DEP;
         int64_t hs_final = 0;
-        if (!dep_bad) {
+        if (!dep_bad && s.B[c] == kInf) { // unbounded safe blocking
+            st = PAAM_ST_OVERRUN;
+        } else if (!dep_bad) {
             const int64_t Dc = s.D[c], Bc = s.B[c], Ec = s.E[c], Sc = s.S[c], Hseg = s.Hseg[c];
             const int64_t dc = s.delta[c];
             const int64_t own = Sc + dc * s.blk[c];

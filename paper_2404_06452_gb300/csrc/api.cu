@@ -390,7 +390,7 @@ static int check_opts(const paam_analysis_opts *o)
     if (o->n_buckets < 1) return PAAM_E_INVAL;
     if (o->eps_ns < 0 || o->kappa_ns < 0) return PAAM_E_INVAL;
     if (o->eps_ns > PAAM_MAX_OVERHEAD || o->kappa_ns > PAAM_MAX_OVERHEAD) return PAAM_E_RANGE;
-    if (o->blocking_mode != 0) return PAAM_E_UNSUPPORTED;
+    if (o->blocking_mode != 0 && o->blocking_mode != 1) return PAAM_E_INVAL;
     return PAAM_OK;
 }
 
@@ -400,6 +400,7 @@ static AnalysisParams params_of(const paam_analysis_opts *o)
     p.n_buckets = o->n_buckets;
     p.eps = o->eps_ns;
     p.kappa = o->kappa_ns;
+    p.blocking_mode = o->blocking_mode;
     return p;
 }
 
@@ -419,7 +420,7 @@ extern "C" int paam_rta_analyze_batch(paam_ctx *ctx, const paam_batch *b, const 
     const bool same = bm->graph && bm->graph_key.R == R && bm->graph_key.status == status &&
                       bm->graph_key.verdict == verdict && bm->graph_key.cfg_index == bm->cfg_index &&
                       bm->graph_key.p.n_buckets == p.n_buckets && bm->graph_key.p.eps == p.eps &&
-                      bm->graph_key.p.kappa == p.kappa;
+                      bm->graph_key.p.kappa == p.kappa && bm->graph_key.p.blocking_mode == p.blocking_mode;
     if (!same) {
         if (bm->graph) {
             cudaGraphExecDestroy(bm->graph);

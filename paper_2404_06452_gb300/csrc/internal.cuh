@@ -22,6 +22,7 @@ void paam_count_launch(unsigned n = 1);
 
 struct AnalysisParams {
     int32_t n_buckets;
+    int32_t blocking_mode; // 0: Lemma 4 as printed; 1: the safe reading (analyze_wide.cu only)
     int32_t K; // 0: analyse every system once; K > 0: candidate mode (below)
     int64_t eps;
     int64_t kappa;

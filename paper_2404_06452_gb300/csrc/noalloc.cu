@@ -65,7 +65,7 @@ extern "C" int paam_rta_analyze_noalloc(const paam_systems_view *v, const paam_a
     if (v->n_sys > PAAM_NOALLOC_MAX_SYS) return PAAM_E_RANGE;
     if (o->n_buckets < 1 || o->eps_ns < 0 || o->kappa_ns < 0) return PAAM_E_INVAL;
     if (o->eps_ns > PAAM_MAX_OVERHEAD || o->kappa_ns > PAAM_MAX_OVERHEAD) return PAAM_E_RANGE;
-    if (o->blocking_mode != 0) return PAAM_E_UNSUPPORTED;
+    if (o->blocking_mode != 0 && o->blocking_mode != 1) return PAAM_E_INVAL;
     if (!v->sys_chain_off || !v->chain_cb_off || !v->cb_seg_off || !v->sys_exec_off) return PAAM_E_INVAL;
     if ((v->n_chain > 0 && (!v->T || !v->D || !v->prio || !v->exec || !v->spin || !R || !status)) ||
         (v->n_cb > 0 && !v->E) || (v->n_seg > 0 && !v->A) || (v->n_exec > 0 && !v->exec_core))
@@ -130,6 +130,7 @@ extern "C" int paam_rta_analyze_noalloc(const paam_systems_view *v, const paam_a
     p.n_buckets = o->n_buckets;
     p.eps = o->eps_ns;
     p.kappa = o->kappa_ns;
+    p.blocking_mode = o->blocking_mode;
     int nk = 0;
     rc = paam_enqueue_analysis(&b, p, kLaunchCfgs[0], R, status, verdict, stream, &nk);
     if (rc == PAAM_OK) paam_count_launch((unsigned)nk);

@@ -55,7 +55,7 @@ extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const
     if (b->ctx != ctx) return PAAM_E_STATE;
     if (o->n_buckets < 1 || o->eps_ns < 0 || o->kappa_ns < 0) return PAAM_E_INVAL;
     if (o->eps_ns > PAAM_MAX_OVERHEAD || o->kappa_ns > PAAM_MAX_OVERHEAD) return PAAM_E_RANGE;
-    if (o->blocking_mode != 0) return PAAM_E_UNSUPPORTED;
+    if (o->blocking_mode != 0 && o->blocking_mode != 1) return PAAM_E_INVAL;
     if (Kc < 1 || K < 1 || (!order && K != Kc) || nmax < b->max_chains || nmax < 1 || (b->n_sys > 0 && !ranks))
         return PAAM_E_INVAL;
     if (b->n_sys * (int64_t)Kc > (int64_t)INT32_MAX) return PAAM_E_RANGE;
@@ -100,6 +100,7 @@ extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const
     p.n_buckets = o->n_buckets;
     p.eps = o->eps_ns;
     p.kappa = o->kappa_ns;
+    p.blocking_mode = o->blocking_mode;
     p.K = K;
     p.Kc = Kc;
     p.order = order;

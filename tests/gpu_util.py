@@ -14,7 +14,7 @@ def ctx():
     return ctx._c
 
 
-def gpu_analyze(sy, n_buckets=1, eps=0, kappa=0, device_view=False, autotune=False):
+def gpu_analyze(sy, n_buckets=1, eps=0, kappa=0, device_view=False, autotune=False, blocking_mode=0):
     """Analyse ``sy`` through the C ABI; with ``autotune`` in the launch
     configuration the autotuner picks (as the benchmark does)."""
     import torch
@@ -26,7 +26,7 @@ def gpu_analyze(sy, n_buckets=1, eps=0, kappa=0, device_view=False, autotune=Fal
     b = pkg.paam_rta_load_systems(c, src)
     if autotune:
         pkg.paam_rta_autotune(c, b, pkg.analysis_opts(n_buckets, eps, kappa))
-    R, st, v = pkg.analyze(c, b, n_buckets=n_buckets, eps=eps, kappa=kappa)
+    R, st, v = pkg.analyze(c, b, n_buckets=n_buckets, eps=eps, kappa=kappa, blocking_mode=blocking_mode)
     torch.cuda.synchronize()
     out = dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy())
     b.free()

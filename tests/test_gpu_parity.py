@@ -11,7 +11,7 @@ import oracle
 import paam_gen as g
 from paam_gen import tiny
 
-from gpu_util import assert_same, gpu_analyze, oracle_on
+from gpu_util import assert_same, ctx, gpu_analyze, oracle_on
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -140,3 +140,26 @@ def test_invalid_inputs_rejected():
     big = mod(lambda d: d["chains"][0].update(T=2**40, D=2**40, cbs=[(2**40, [2**40] * 8)]))
     _expect_error(big, -2)                                             # int64 range
     _expect_error(mod(lambda d: None), -2, eps=2**33)                  # eps above the cap
+
+
+@pytest.mark.parametrize("p", PARAMS[:2])
+def test_safe_blocking_mode(p):
+    """blocking_mode=1 (the safe reading of Lemma 4) on every shape: uneven
+    sizes up to 64 chains, spinning chains, overheads; bit-exact with the
+    oracle, and the search in the same mode."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    for sy in (g.generate("cfg1", p_spin=0.5), g.generate("cfg3", n_sys=3000, seed=31),
+               g.generate("cfg2", n_sys=3000, p_spin=0.3, exec_prio_mode=1)):
+        assert_same(gpu_analyze(sy, blocking_mode=1, **p), oracle.analyze(sy, blocking_mode=1, threads=8, **p))
+    sy = g.generate("cfg4s", n_sys=200)
+    ranks = g.candidate_ranks(sy, 24, 3)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    first, cand = pkg.search(ctx(), b, torch.from_numpy(ranks).cuda(), blocking_mode=1, **p)
+    torch.cuda.synchronize()
+    ref = oracle.search(sy, ranks, blocking_mode=1, threads=8, **p)
+    assert np.array_equal(cand.cpu().numpy(), ref["cand_ok"])
+    assert np.array_equal(first.cpu().numpy(), ref["first_ok"])
+    b.free()
