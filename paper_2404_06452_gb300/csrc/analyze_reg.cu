@@ -192,12 +192,14 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         sp[k] = b.spin[g] != 0;
         const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
         uint64_t E = 0, Emax = 0, S = 0, M = 0, Amin = ~0ull;
+#pragma unroll 4
         for (int64_t cb = cb0; cb < cb1; ++cb) {
             const uint64_t e = (uint64_t)b.E[cb];
             E += e;
             Emax = e > Emax ? e : Emax;
         }
         const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
+#pragma unroll 4
         for (int64_t q = q0; q < q1; ++q) {
             const uint64_t a = (uint64_t)b.A[q] + kappa2; // A* = A + 2 kappa
             S += a;
@@ -263,20 +265,28 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         for (int k = 0; k < CPL; ++k) ep[k] = best[k];
     }
 
-    // ---- relations, analysis order, CPU blocking (Lemma 4) -------------------
+    // ---- relations, analysis order, CPU blocking (Lemma 4), and the sums of
+    // the Lemma 2 skip test over hps; with one bucket (every user shares it)
+    // also the same-bucket blocking of R2-R3
     Mask higher[CPL], samex[CPL], hppm[CPL];
     int pos[CPL], rank[CPL];
-    uint32_t Bv[CPL];
+    uint32_t Bv[CPL], blk[CPL];
+    uint64_t hchd[CPL], sums[CPL];
+    const bool one_bucket = p.n_buckets == 1;
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         higher[k] = samex[k] = hppm[k] = 0;
         pos[k] = rank[k] = 0;
-        Bv[k] = 0;
+        Bv[k] = blk[k] = 0;
+        hchd[k] = sums[k] = 0;
     }
     for (int t = 0; t < n; ++t) {
         const int32_t pt = bcast<G, CPL>(pr, t, gm), xt = bcast<G, CPL>(ex, t, gm);
         const int32_t kt = bcast<G, CPL>(co, t, gm), et = bcast<G, CPL>(ep, t, gm);
         const uint32_t emt = bcast<G, CPL>(Emx, t, gm);
+        const uint32_t tmt = bcast<G, CPL>(tm1, t, gm), mgt = bcast<G, CPL>(mg, t, gm);
+        const uint32_t sht = bcast<G, CPL>(sh, t, gm), st = bcast<G, CPL>(Sv, t, gm);
+        const uint32_t mt = one_bucket ? bcast<G, CPL>(Mv, t, gm) : 0u;
         const bool ut = (users >> t) & 1;
         const Mask bit = (Mask)1 << t;
 #pragma unroll
@@ -289,6 +299,11 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             pos[k] += (et > ep[k]) || (et == ep[k] && hi);           // executor, then chain priority
             rank[k] += (ut && hi) ? 1 : 0;
             if (sx && pt < pr[k] && emt > Bv[k]) Bv[k] = emt; // one LP callback on the executor
+            const bool act = dlv[k] != 0 && ut;               // c and t both use the accelerator
+            const uint32_t sv = (act && hi) ? st : 0u;
+            hchd[k] += (uint64_t)rarrivals(Dv[k], tmt, mgt, sht) * sv;
+            sums[k] += sv;
+            if (one_bucket && act && pt < pr[k] && mt > blk[k]) blk[k] = mt;
         }
     }
     const int n_users = rpopc(users);
@@ -298,29 +313,19 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         bucket[k] = (val[k] && dlv[k]) ? (int32_t)((uint32_t)rank[k] * (uint32_t)p.n_buckets / (uint32_t)n_users)
                                        : -1;
 
-    // ---- same-bucket blocking (R2-R3) and the Lemma 2 skip test -------------
-    uint32_t blk[CPL];
-    uint64_t hchd[CPL], sums[CPL];
+    // ---- same-bucket blocking (R2-R3) with several buckets ------------------
+    if (!one_bucket) {
+        for (int t = 0; t < n; ++t) {
+            const uint32_t mt = bcast<G, CPL>(Mv, t, gm);
+            const int32_t bt = bcast<G, CPL>(bucket, t, gm);
+            const bool ut = (users >> t) & 1;
 #pragma unroll
-    for (int k = 0; k < CPL; ++k) {
-        blk[k] = 0;
-        hchd[k] = sums[k] = 0;
-    }
-    for (int t = 0; t < n; ++t) {
-        const uint32_t mt = bcast<G, CPL>(Mv, t, gm);
-        const int32_t bt = bcast<G, CPL>(bucket, t, gm);
-        const uint32_t tmt = bcast<G, CPL>(tm1, t, gm), mgt = bcast<G, CPL>(mg, t, gm);
-        const uint32_t sht = bcast<G, CPL>(sh, t, gm), st = bcast<G, CPL>(Sv, t, gm);
-        const bool ut = (users >> t) & 1;
-#pragma unroll
-        for (int k = 0; k < CPL; ++k) {
-            const bool act = bucket[k] >= 0 && ut;
-            const bool hi = (higher[k] >> t) & 1;
-            const bool same = act && !hi && t != lane + G * k && bt == bucket[k];
-            blk[k] = (same && mt > blk[k]) ? mt : blk[k];
-            const uint32_t sv = (act && hi) ? st : 0u;
-            hchd[k] += (uint64_t)rarrivals(Dv[k], tmt, mgt, sht) * sv;
-            sums[k] += sv;
+            for (int k = 0; k < CPL; ++k) {
+                const bool act = bucket[k] >= 0 && ut;
+                const bool hi = (higher[k] >> t) & 1;
+                const bool same = act && !hi && t != lane + G * k && bt == bucket[k];
+                blk[k] = (same && mt > blk[k]) ? mt : blk[k];
+            }
         }
     }
 
@@ -473,11 +478,10 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
 }
 
 template <int G, int CPL>
-__global__ void __launch_bounds__(256) analyze_reg_kernel(BatchDev b, AnalysisParams p, int64_t *R, uint8_t *st,
-                                                          uint8_t *verdict, const int32_t *list,
-                                                          const int32_t *count, int32_t *big_list,
-                                                          int32_t *big_count, int32_t *wide_list,
-                                                          int32_t *wide_count)
+__device__ __forceinline__ void reg_items(const BatchDev &b, const AnalysisParams &p, int64_t *R, uint8_t *st,
+                                          uint8_t *verdict, const int32_t *list, const int32_t *count,
+                                          int32_t *big_list, int32_t *big_count, int32_t *wide_list,
+                                          int32_t *wide_count)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int groups = blockDim.x / G;
@@ -492,6 +496,28 @@ __global__ void __launch_bounds__(256) analyze_reg_kernel(BatchDev b, AnalysisPa
     }
 }
 
+template <int G, int CPL>
+__global__ void __launch_bounds__(256) analyze_reg_kernel(BatchDev b, AnalysisParams p, int64_t *R, uint8_t *st,
+                                                          uint8_t *verdict, const int32_t *list,
+                                                          const int32_t *count, int32_t *big_list,
+                                                          int32_t *big_count, int32_t *wide_list,
+                                                          int32_t *wide_count)
+{
+    reg_items<G, CPL>(b, p, R, st, verdict, list, count, big_list, big_count, wide_list, wide_count);
+}
+
+// One chain per lane keeps few values per thread: 64 registers leave room for
+// four resident blocks of 256 threads.
+template <int G>
+__global__ void __launch_bounds__(256, 4) analyze_reg1_kernel(BatchDev b, AnalysisParams p, int64_t *R,
+                                                              uint8_t *st, uint8_t *verdict, const int32_t *list,
+                                                              const int32_t *count, int32_t *big_list,
+                                                              int32_t *big_count, int32_t *wide_list,
+                                                              int32_t *wide_count)
+{
+    reg_items<G, 1>(b, p, R, st, verdict, list, count, big_list, big_count, wide_list, wide_count);
+}
+
 } // namespace
 
 template <int G, int CPL>
@@ -501,7 +527,12 @@ int launch_reg(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_
     if (threads % 32 != 0 || threads > 256) return PAAM_E_INVAL;
     const int groups = threads / G;
     const size_t smem = sizeof(OwnSmem<G * CPL>) * groups;
-    auto kern = analyze_reg_kernel<G, CPL>;
+    void (*kern)(BatchDev, AnalysisParams, int64_t *, uint8_t *, uint8_t *, const int32_t *, const int32_t *,
+                 int32_t *, int32_t *, int32_t *, int32_t *);
+    if constexpr (CPL == 1)
+        kern = analyze_reg1_kernel<G>;
+    else
+        kern = analyze_reg_kernel<G, CPL>;
     PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
