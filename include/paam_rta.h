@@ -303,10 +303,11 @@ int paam_surrogate_features(paam_ctx *ctx, const paam_batch *batch, const int16_
  * bit-identical results.  A batch starts with configuration 0.
  *
  * paam_rta_autotune times every configuration on the batch itself (the
- * analysis is run 4 times per configuration, the first run discarded), keeps
- * the fastest for later paam_rta_analyze_batch calls on this batch, and
- * returns its index (>= 0) or a negative error.  times_ms, if not NULL,
- * receives up to max_out per-configuration times in milliseconds.  It
+ * analysis is run 6 times per configuration, the first run discarded, and
+ * the median of the other 5 kept), keeps the fastest for later
+ * paam_rta_analyze_batch calls on this batch, and returns its index (>= 0)
+ * or a negative error.  times_ms, if not NULL, receives up to max_out
+ * per-configuration median times in milliseconds.  It
  * synchronises `stream` and allocates temporary device outputs.
  */
 int paam_rta_num_launch_configs(void);

@@ -491,20 +491,29 @@ extern "C" int paam_rta_autotune(paam_ctx *ctx, paam_batch *b, const paam_analys
     cudaEventCreate(&e1);
     int best = 0;
     float best_ms = 1e30f;
+    constexpr int kReps = 5; // timed runs per configuration, after one warm-up run
     for (int i = 0; i < kNumLaunchCfgs && rc == PAAM_OK; ++i) {
-        float t_min = 1e30f;
-        for (int rep = 0; rep < 4 && rc == PAAM_OK; ++rep) {
+        float t[kReps + 1] = {};
+        for (int rep = 0; rep <= kReps && rc == PAAM_OK; ++rep) {
             cudaEventRecord(e0, stream);
             rc = paam_enqueue_analysis(b, p, kLaunchCfgs[i], R, st, v, stream, nullptr);
             cudaEventRecord(e1, stream);
             if (cudaEventSynchronize(e1) != cudaSuccess) rc = PAAM_E_CUDA;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0 && ms < t_min) t_min = ms; // the first run warms caches and code
+            cudaEventElapsedTime(&t[rep], e0, e1);
         }
-        if (times_ms && i < max_out) times_ms[i] = t_min;
-        if (t_min < best_ms) {
-            best_ms = t_min;
+        // median of the timed runs (the first warms caches and loads the code): a
+        // configuration that is fast only now and then does not win on one lucky run
+        float *r = t + 1;
+        for (int a = 1; a < kReps; ++a)
+            for (int c = a; c > 0 && r[c] < r[c - 1]; --c) {
+                const float x = r[c];
+                r[c] = r[c - 1];
+                r[c - 1] = x;
+            }
+        const float med = r[kReps / 2];
+        if (times_ms && i < max_out) times_ms[i] = med;
+        if (med < best_ms) {
+            best_ms = med;
             best = i;
         }
     }
