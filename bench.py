@@ -120,8 +120,8 @@ def peaks() -> dict:
 
 # main kernel of each launch configuration (the table in csrc/analyze_fast.cu)
 CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>", 2: "analyze_fast_kernel<16, 32>",
-                 3: "analyze_reg_kernel<16, 1>", 4: "analyze_reg_kernel<4, 4>", 5: "analyze_reg_kernel<16, 2>",
-                 6: "analyze_reg_kernel<32, 1>", 7: "analyze_reg_kernel<8, 2>", 8: "analyze_fast_kernel<4, 16>",
+                 3: "analyze_reg1_kernel<16>", 4: "analyze_reg_kernel<4, 4>", 5: "analyze_reg_kernel<16, 2>",
+                 6: "analyze_reg1_kernel<32>", 7: "analyze_reg_kernel<8, 2>", 8: "analyze_fast_kernel<4, 16>",
                  9: "analyze_fast_kernel<8, 32>", 10: "analyze_reg_kernel<16, 2>", 11: "analyze_reg_kernel<4, 4>"}
 
 
