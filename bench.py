@@ -449,6 +449,29 @@ def search_cpu_baseline(n_sys):
 
 
 # ---------------------------------------------------------------------------
+# several ranks (one GPU each): shards by seed, slowest rank's time
+# ---------------------------------------------------------------------------
+def rank_seed(rank: int) -> int:
+    """Seed of rank's own batch of the workload: each rank analyses different
+    systems of the same shape (weak scaling, no data exchange)."""
+    import paam_gen
+
+    return paam_gen.CONFIGS[WORKLOAD]["seed"] + 1_000_003 * rank
+
+
+def reduce_over_ranks(elapsed_ms: float, n_chain: int, n_sys: int, dist, device) -> tuple:
+    """(slowest rank's time, chains and systems over all ranks); dist None on one rank."""
+    import torch
+
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([n_chain, n_sys], dtype=torch.int64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u[0].item()), int(u[1].item())
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -478,7 +501,7 @@ def run_ours(args):
         return
 
     n_sys = args.n_sys or paam_gen.CONFIGS[WORKLOAD]["n_sys"]
-    seed = paam_gen.CONFIGS[WORKLOAD]["seed"] + 1_000_003 * rank
+    seed = rank_seed(rank)
     sy = paam_gen.generate(WORKLOAD, n_sys=n_sys, seed=seed)
     ctx = pkg.Context(local)
     stream = torch.cuda.Stream(device=local)
@@ -520,12 +543,7 @@ def run_ours(args):
         dist.barrier()
     elapsed_ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
-    t_max = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t_max.item())
-    total_chains = batch.n_chain * world
-    total_sys = batch.n_sys * world
+    elapsed_ms, total_chains, total_sys = reduce_over_ranks(elapsed_ms, batch.n_chain, batch.n_sys, dist, dev)
     value = total_chains * args.steps / (elapsed_ms / 1e3)
     ms_per_step = elapsed_ms / args.steps
 
@@ -571,7 +589,9 @@ def run_ours(args):
         for _ in range(args.e2e_steps):
             e2e_step()
         dt = time.perf_counter() - t0
-        e2e = {"value": batch.n_chain * args.e2e_steps / dt * world, "unit": "chains/s",
+        dt_ms, e2e_chains, _ = reduce_over_ranks(dt * 1e3, batch.n_chain, batch.n_sys, dist, dev)
+        dt = dt_ms / 1e3
+        e2e = {"value": e2e_chains * args.e2e_steps / dt, "unit": "chains/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
                "ms_per_step": dt * 1e3 / args.e2e_steps}
 
