@@ -28,6 +28,10 @@ struct RegMask {
 template <int NMAX>
 struct OwnSmem {
     using Mask = typename RegMask<NMAX>::type;
+    // each chain's keys, read by the whole group as broadcasts in the relations pass
+    int4 key[NMAX];   // {chain priority, executor, core, executor priority}
+    uint4 dv[NMAX];   // {Emax, T - 1, magic, shift}
+    uint2 sm[NMAX];   // {S*, M*}
     Mask hp[NMAX], hpp[NMAX], hps[NMAX];
     uint4 rec[NMAX];  // {D, base = B + E, own = S* + delta blk (capped at D + 1), deps = delta eps}
     uint4 seg[NMAX];  // {Hseg, limit, blk, delta}
@@ -60,30 +64,33 @@ __device__ __forceinline__ V rsum(V v, unsigned mask)
     return v;
 }
 
+// Group reductions.  32-bit ones are one redux.sync over the group's member
+// mask (every lane of a group takes the same path; groups of one warp may
+// reduce at the same time, each over its own mask); 64-bit ones use shuffles.
 template <int G, typename V>
 __device__ __forceinline__ V ror(V v, unsigned mask)
 {
+    if constexpr (sizeof(V) == 4) {
+        return (V)__reduce_or_sync(mask, (unsigned)v);
+    } else {
 #pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) v |= __shfl_xor_sync(mask, v, off, G);
-    return v;
+        for (int off = G / 2; off > 0; off >>= 1) v |= __shfl_xor_sync(mask, v, off, G);
+        return v;
+    }
 }
 
 template <int G>
 __device__ __forceinline__ unsigned rand_(unsigned v, unsigned mask)
 {
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) v &= __shfl_xor_sync(mask, v, off, G);
-    return v;
+    return __reduce_and_sync(mask, v);
 }
 
 template <int G>
 __device__ __forceinline__ uint64_t gsum(uint64_t v, bool narrow, unsigned mask)
 {
     if (narrow) {
-        uint32_t x = v < kNarrow - 1 ? (uint32_t)v : kNarrow - 1;
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) x += __shfl_xor_sync(mask, x, off, G);
-        return x;
+        const uint32_t x = v < kNarrow - 1 ? (uint32_t)v : kNarrow - 1;
+        return __reduce_add_sync(mask, x);
     }
     return rsum<G>(v, mask);
 }
@@ -91,9 +98,7 @@ __device__ __forceinline__ uint64_t gsum(uint64_t v, bool narrow, unsigned mask)
 template <int G>
 __device__ __forceinline__ uint32_t rmax(uint32_t v, unsigned mask)
 {
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(mask, v, off, G));
-    return v;
+    return __reduce_max_sync(mask, v);
 }
 
 // value of slot t / G held by lane t % G, broadcast to the group
@@ -280,13 +285,22 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         Bv[k] = blk[k] = 0;
         hchd[k] = sums[k] = 0;
     }
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        if (!val[k]) continue;
+        const int j = lane + G * k;
+        s.key[j] = make_int4(pr[k], ex[k], co[k], ep[k]);
+        s.dv[j] = make_uint4(Emx[k], tm1[k], mg[k], sh[k]);
+        s.sm[j] = make_uint2(Sv[k], Mv[k]);
+    }
+    __syncwarp(gm);
     for (int t = 0; t < n; ++t) {
-        const int32_t pt = bcast<G, CPL>(pr, t, gm), xt = bcast<G, CPL>(ex, t, gm);
-        const int32_t kt = bcast<G, CPL>(co, t, gm), et = bcast<G, CPL>(ep, t, gm);
-        const uint32_t emt = bcast<G, CPL>(Emx, t, gm);
-        const uint32_t tmt = bcast<G, CPL>(tm1, t, gm), mgt = bcast<G, CPL>(mg, t, gm);
-        const uint32_t sht = bcast<G, CPL>(sh, t, gm), st = bcast<G, CPL>(Sv, t, gm);
-        const uint32_t mt = one_bucket ? bcast<G, CPL>(Mv, t, gm) : 0u;
+        const int4 kt4 = s.key[t];
+        const uint4 dv4 = s.dv[t];
+        const uint2 sm2 = s.sm[t];
+        const int32_t pt = kt4.x, xt = kt4.y, kt = kt4.z, et = kt4.w;
+        const uint32_t emt = dv4.x, tmt = dv4.y, mgt = dv4.z, sht = dv4.w;
+        const uint32_t st = sm2.x, mt = sm2.y;
         const bool ut = (users >> t) & 1;
         const Mask bit = (Mask)1 << t;
 #pragma unroll
