@@ -109,6 +109,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(loaded)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo; architecture otherwise)."""
+    import platform
+
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -184,7 +199,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "step": f"{sample} systems of the workload per step"},
         "cpu_baseline": {"value": val, "unit": "chains/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{sample}-system slices of the {n_sys}-system workload, one per step"},
+                         "sample": f"{sample}-system slices of the {n_sys}-system workload, one per step",
+                         "cpu_model": cpu_model()},
         "e2e": {"value": val, "unit": "chains/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -605,7 +621,12 @@ def run_ours(args):
         ref = oracle.analyze(sy, threads=cores)
         dt = time.perf_counter() - t0
         cpu = {"value": sy.n_chain / dt, "unit": "chains/s", "cores": cores, "kind": "oracle",
-               "sample": f"the whole {sy.n_sys}-system workload, one pass"}
+               "sample": f"the whole {sy.n_sys}-system workload, one pass", "cpu_model": cpu_model()}
+        # one core, on a 50,000-system slice
+        sl = sy.subset(np.arange(min(50_000, sy.n_sys)))
+        t0 = time.perf_counter()
+        oracle.analyze(sl, threads=1)
+        cpu["single_core_value"] = sl.n_chain / (time.perf_counter() - t0)
         # the numbers above come from bit-identical results
         same = bool(np.array_equal(ref["R"], R.cpu().numpy()) and np.array_equal(ref["status"], st.cpu().numpy()))
         cpu["bit_exact_vs_gpu"] = same
