@@ -421,6 +421,34 @@ def gemm_bench(pkg, M, N, K, steps, warmup):
             "err_flag": int(err.item())}
 
 
+def end_to_end_bench(pkg, ctx, n_sys):
+    """Chains spanning several executors (the workload's chains grouped into
+    end-to-end chains of 1-3 sub-chains): the analysis of the sub-chains and
+    the composition of their bounds."""
+    import torch
+
+    import paam_gen
+
+    sy, off, chain, D = paam_gen.split_end_to_end(paam_gen.generate(WORKLOAD, n_sys=n_sys), 11)
+    b = pkg.paam_rta_load_systems(ctx, sy)
+    pkg.paam_rta_autotune(ctx, b, pkg.analysis_opts())
+    R, st, _ = pkg.analyze(ctx, b)
+    t = lambda a: torch.from_numpy(a).cuda()
+    off_d, chain_d, D_d = t(off), t(chain), t(D)
+    Re = torch.empty(len(D), dtype=torch.int64, device="cuda")
+    se = torch.empty(len(D), dtype=torch.uint8, device="cuda")
+    eps_prime = 198_000
+    pkg.paam_rta_end_to_end(ctx, b, off_d, chain_d, D_d, eps_prime, R, st, Re, se)
+    t_an, _ = _timed(lambda: pkg.analyze(ctx, b), 10)
+    t_e2e, _ = _timed(lambda: pkg.paam_rta_end_to_end(ctx, b, off_d, chain_d, D_d, eps_prime, R, st, Re, se), 10)
+    sts = se.cpu().numpy()
+    b.free()
+    return {"systems": sy.n_sys, "sub_chains": sy.n_chain, "end_to_end_chains": len(D),
+            "eps_prime_ns": eps_prime, "analysis_ms": t_an * 1e3, "compose_ms": t_e2e * 1e3,
+            "end_to_end_chains_per_s": len(D) / (t_an + t_e2e),
+            "status_fractions": [float((sts == k).mean()) for k in range(3)]}
+
+
 def infer_bench(pkg, n_sys, steps, warmup):
     """The network's ranking alone (features, 4 layers with the fused score,
     top-k) on the search workload, random weights: what a step of guided search
@@ -639,6 +667,9 @@ def run_ours(args):
             search["cpu_baseline"] = search_cpu_baseline(min(args.search_sys, 2000))
     if rank == 0 and world == 1 and not args.no_surrogate:
         surrogate = surrogate_bench(pkg, ctx, args.train_sys, args.search_sys, args.top_k)
+    e2e_chains = None
+    if rank == 0 and world == 1 and not args.no_search:
+        e2e_chains = end_to_end_bench(pkg, ctx, min(n_sys, 1_000_000))
 
     if rank == 0:
         line = {
@@ -652,7 +683,7 @@ def run_ours(args):
                        "autotune_ms": [round(t, 4) for t in cfg_times]},
             "systems_per_s": total_sys * args.steps / (elapsed_ms / 1e3),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "search": search, "surrogate": surrogate,
+            "clocks": clocks, "search": search, "surrogate": surrogate, "end_to_end": e2e_chains,
         }
         print(json.dumps(line), flush=True)
     batch.free()

@@ -297,6 +297,35 @@ int paam_surrogate_features(paam_ctx *ctx, const paam_batch *batch, const int16_
                             int32_t nmax, int32_t n_buckets, int64_t kappa_ns, void *X, void *stream);
 
 /*
+ * End-to-end bounds of chains that span several executors (Sec. IV-F, the
+ * end-to-end latency of a chain made of sub-chains that run on different
+ * executors): each sub-chain is analysed as a chain of its own executor by
+ * paam_rta_analyze_batch, and the end-to-end bound is the sum of their
+ * response times plus a communication cost per hand-over,
+ *   R* = sum over the m sub-chains of R_c + (m - 1) eps_prime_ns.
+ * (The paper adds one communication cost eps' < eps; it is read here as one
+ * per hand-over between consecutive sub-chains.)
+ *   e2e_off[n_e2e + 1]   device, CSR offsets into e2e_chain (non-decreasing,
+ *                        e2e_off[0] = 0)
+ *   e2e_chain[...]       device, the batch-wide chain indices of each end-to-end
+ *                        chain's sub-chains (0 <= index < n_chain)
+ *   D_e2e[n_e2e]         device, end-to-end deadlines (ns, > 0)
+ *   R, status            device, the outputs of paam_rta_analyze_batch
+ *   R_e2e, status_e2e    device outputs: R* and PAAM_ST_SCHED when every
+ *                        sub-chain is PAAM_ST_SCHED and R* <= D*; else R* = -1
+ *                        and PAAM_ST_DEP if a sub-chain is DEP, otherwise
+ *                        PAAM_ST_OVERRUN (an empty chain is SCHED with R* = 0)
+ * eps_prime_ns is 0..PAAM_MAX_OVERHEAD.  The call synchronises `stream`.
+ * Errors: PAAM_E_INVAL (NULL arrays, n_e2e < 0, a sub-chain index out of
+ * range or decreasing offsets, found on the device), PAAM_E_RANGE (eps'),
+ * PAAM_E_NOMEM, PAAM_E_CUDA.  Out-of-range entries are not read.
+ */
+int paam_rta_end_to_end(paam_ctx *ctx, const paam_batch *batch, int64_t n_e2e, const int64_t *e2e_off,
+                        const int64_t *e2e_chain, const int64_t *D_e2e, int64_t eps_prime_ns,
+                        const int64_t *R, const uint8_t *status, int64_t *R_e2e, uint8_t *status_e2e,
+                        void *stream);
+
+/*
  * Launch configurations.  The analysis has several built-in launch
  * configurations (lanes per system, chain-table size of the first pass, lanes
  * per system for systems with more chains, CTA size); every one produces

@@ -337,4 +337,32 @@ def candidate_ranks(sy: Systems, K: int, seed: int, nmax: int | None = None) -> 
     return out
 
 
+def split_end_to_end(sy: Systems, seed: int, max_sub: int = 3):
+    """Group each system's chains into end-to-end chains of sub-chains (the
+    workload shape of chains that span several executors).
+
+    System s uses one group size k_s, uniform in 1..min(max_sub, executors),
+    and groups consecutive chains; the members of a group get the period of
+    its first chain (deadline D* = that period, also each member's D) and
+    consecutive executors, so each sub-chain runs on its own executor.
+    Executor priorities are left to be derived (criticality-as-priority).
+    Returns (systems, e2e_off, e2e_chain, D_e2e); sub-chains are contiguous.
+    """
+    rng = np.random.default_rng(seed)
+    n = sy.chains_per_system()
+    nx = np.diff(sy.sys_exec_off)
+    k = np.minimum(rng.integers(1, max_sub + 1, size=sy.n_sys), np.maximum(nx, 1))
+    sysid = np.repeat(np.arange(sy.n_sys), n)
+    local = np.arange(sy.n_chain) - sy.sys_chain_off[sysid]
+    kc = k[sysid]
+    first = sy.sys_chain_off[sysid] + (local // kc) * kc
+    T = sy.T[first].copy()
+    ex = ((sy.exec[first].astype(np.int64) + local % kc) % nx[sysid]).astype(np.int32)
+    out = Systems(sy.sys_chain_off, sy.chain_cb_off, sy.cb_seg_off, T, T.copy(), sy.prio, ex, sy.spin, sy.E,
+                  sy.A, sy.acc, sy.sys_exec_off, sy.exec_core, None, dict(sy.meta, e2e_split=int(max_sub)))
+    starts = np.nonzero(local % kc == 0)[0]
+    e2e_off = np.append(starts, sy.n_chain).astype(np.int64)
+    return out, e2e_off, np.arange(sy.n_chain, dtype=np.int64), T[starts].copy()
+
+
 from .tiny import tiny_system, tiny_batch  # noqa: E402  (pure-Python small-integer systems)

@@ -106,6 +106,9 @@ def lib():
             "paam_tc_gemm_bf16": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _c_void_p, _c_void_p]),
             "paam_diag_gelu": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int64, _c_void_p]),
+            "paam_rta_end_to_end": (ctypes.c_int, [_c_void_p, _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p,
+                                                   _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _c_void_p,
+                                                   _c_void_p, _c_void_p]),
             "paam_rta_search_priorities": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
                                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                           _c_void_p, _c_void_p, _c_void_p]),
@@ -126,7 +129,7 @@ def exported_symbols() -> list:
             "paam_tc_gemm_bf16", "paam_rta_search_ordered", "paam_model_create", "paam_model_free",
             "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
             "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
-            "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu"]
+            "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_rta_end_to_end"]
 
 
 def launch_count() -> int:
@@ -313,6 +316,15 @@ def paam_tc_gemm_bf16(A, B, C, err, stream=None):
     N = B.shape[0]
     _check(lib().paam_tc_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), _ptr(err),
                                    _stream_ptr(stream)), "paam_tc_gemm_bf16")
+
+
+def paam_rta_end_to_end(ctx: Context, batch: Batch, e2e_off, e2e_chain, D_e2e, eps_prime: int, R, status,
+                        R_e2e, status_e2e, stream=None):
+    """End-to-end bounds of chains made of sub-chains (device arrays)."""
+    n = int(D_e2e.numel())
+    _check(lib().paam_rta_end_to_end(ctx.handle, batch.handle, n, _ptr(e2e_off), _ptr(e2e_chain), _ptr(D_e2e),
+                                     int(eps_prime), _ptr(R), _ptr(status), _ptr(R_e2e), _ptr(status_e2e),
+                                     _stream_ptr(stream)), "paam_rta_end_to_end")
 
 
 def paam_diag_gelu(z, gelu=None, grad=None, stream=None):
