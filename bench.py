@@ -48,6 +48,9 @@ def parse():
                     help="time only the tensor-core GEMM C[M,N] = A[M,K] B[N,K]^T")
     ap.add_argument("--infer", type=int, default=None, metavar="N_SYS",
                     help="time only the network's ranking of 256 candidate orders of N_SYS search systems")
+    ap.add_argument("--kappa", type=int, default=None, metavar="ITERS",
+                    help="only measure the device preemption cost, ITERS iterations per kernel kind")
+    ap.add_argument("--kappa-iters", type=int, default=300, help="preemption-cost iterations in the full run")
     ap.add_argument("--launch-config", type=int, default=None, help="fixed launch configuration (no autotune)")
     return ap.parse_args()
 
@@ -449,6 +452,34 @@ def end_to_end_bench(pkg, ctx, n_sys):
             "status_fractions": [float((sts == k).mean()) for k in range(3)]}
 
 
+def kappa_bench(pkg, ctx, iters, sy=None):
+    """The device preemption cost between the lowest and highest stream
+    priority (the paper's method, four kernel kinds), and what the largest
+    measured delay, used as kappa, does to the analysis with two buckets."""
+    import torch
+
+    out = {"iterations_per_kernel": iters}
+    worst = 0.0
+    for kind, name in enumerate(pkg.PREEMPTION_KERNELS):
+        d, base = pkg.paam_measure_preemption(kind, iters)
+        out[name] = {"mean_us": float(d.mean()), "max_us": float(d.max()), "stdev_us": float(d.std()),
+                     "alone_us": float(np.median(base))}
+        worst = max(worst, float(d.max()))
+    kappa = int(round(worst * 1e3))
+    out["kappa_ns"] = kappa
+    if sy is not None:
+        b = pkg.paam_rta_load_systems(ctx, sy)
+        fr = {}
+        for k in (0, kappa):
+            R, st, v = pkg.analyze(ctx, b, n_buckets=2, kappa=k)
+            torch.cuda.synchronize()
+            fr[str(k)] = {"sched_chains": float((st == 0).float().mean().item()),
+                          "sched_systems": float(v.float().mean().item())}
+        b.free()
+        out["analysis_n_buckets_2"] = fr
+    return out
+
+
 def infer_bench(pkg, n_sys, steps, warmup):
     """The network's ranking alone (features, 4 layers with the fused score,
     top-k) on the search workload, random weights: what a step of guided search
@@ -542,6 +573,10 @@ def run_ours(args):
     if args.infer:
         if rank == 0:
             print(json.dumps({"infer": infer_bench(pkg, args.infer, args.steps, args.warmup)}), flush=True)
+        return
+    if args.kappa:
+        if rank == 0:
+            print(json.dumps({"kappa": kappa_bench(pkg, pkg.Context(local), args.kappa)}), flush=True)
         return
 
     n_sys = args.n_sys or paam_gen.CONFIGS[WORKLOAD]["n_sys"]
@@ -667,9 +702,11 @@ def run_ours(args):
             search["cpu_baseline"] = search_cpu_baseline(min(args.search_sys, 2000))
     if rank == 0 and world == 1 and not args.no_surrogate:
         surrogate = surrogate_bench(pkg, ctx, args.train_sys, args.search_sys, args.top_k)
-    e2e_chains = None
+    e2e_chains = kappa = None
     if rank == 0 and world == 1 and not args.no_search:
         e2e_chains = end_to_end_bench(pkg, ctx, min(n_sys, 1_000_000))
+        if args.kappa_iters > 0:
+            kappa = kappa_bench(pkg, ctx, args.kappa_iters, sy.subset(np.arange(min(sy.n_sys, 200_000))))
 
     if rank == 0:
         line = {
@@ -683,7 +720,7 @@ def run_ours(args):
                        "autotune_ms": [round(t, 4) for t in cfg_times]},
             "systems_per_s": total_sys * args.steps / (elapsed_ms / 1e3),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "search": search, "surrogate": surrogate, "end_to_end": e2e_chains,
+            "clocks": clocks, "search": search, "surrogate": surrogate, "end_to_end": e2e_chains, "kappa": kappa,
         }
         print(json.dumps(line), flush=True)
     batch.free()

@@ -326,6 +326,22 @@ int paam_rta_end_to_end(paam_ctx *ctx, const paam_batch *batch, int64_t n_e2e, c
                         void *stream);
 
 /*
+ * Device preemption cost kappa (Sec. IV-F; measured by the method of the
+ * paper's GPU preemption-delay benchmark, Sec. V): on `device`, two streams
+ * at the lowest and the highest stream priority each get their own buffers
+ * for kernel `kind` (0 MatMul, 1 Reduction, 2 VectorAdd, 3 Histogram; kernels
+ * of this library).  Each of `iters` iterations launches the kernel on the
+ * low-priority stream and at once on the high-priority stream, times the
+ * high-priority one with stream events, then times it again alone;
+ *   delay_us[i] = (with the low-priority kernel running) - (alone), in us,
+ *   base_us[i]  = the time alone (optional, may be NULL).
+ * delay_us is host memory of `iters` floats.  Synchronises the device;
+ * allocates and frees device memory.  Errors: PAAM_E_INVAL (kind outside
+ * 0..3, iters < 1, NULL delay_us), PAAM_E_NOMEM, PAAM_E_CUDA.
+ */
+int paam_measure_preemption(int device, int kind, int iters, float *delay_us, float *base_us);
+
+/*
  * Launch configurations.  The analysis has several built-in launch
  * configurations (lanes per system, chain-table size of the first pass, lanes
  * per system for systems with more chains, CTA size); every one produces

@@ -106,6 +106,8 @@ def lib():
             "paam_tc_gemm_bf16": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _c_void_p, _c_void_p]),
             "paam_diag_gelu": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int64, _c_void_p]),
+            "paam_measure_preemption": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_void_p,
+                                                       _c_void_p]),
             "paam_rta_end_to_end": (ctypes.c_int, [_c_void_p, _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p,
                                                    _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p, _c_void_p,
                                                    _c_void_p, _c_void_p]),
@@ -129,7 +131,8 @@ def exported_symbols() -> list:
             "paam_tc_gemm_bf16", "paam_rta_search_ordered", "paam_model_create", "paam_model_free",
             "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
             "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
-            "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_rta_end_to_end"]
+            "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_rta_end_to_end",
+            "paam_measure_preemption"]
 
 
 def launch_count() -> int:
@@ -325,6 +328,18 @@ def paam_rta_end_to_end(ctx: Context, batch: Batch, e2e_off, e2e_chain, D_e2e, e
     _check(lib().paam_rta_end_to_end(ctx.handle, batch.handle, n, _ptr(e2e_off), _ptr(e2e_chain), _ptr(D_e2e),
                                      int(eps_prime), _ptr(R), _ptr(status), _ptr(R_e2e), _ptr(status_e2e),
                                      _stream_ptr(stream)), "paam_rta_end_to_end")
+
+
+PREEMPTION_KERNELS = ("MatMul", "Reduction", "VectorAdd", "Histogram")
+
+
+def paam_measure_preemption(kind: int, iters: int, device: int = 0) -> tuple:
+    """Per-iteration preemption delays and baselines in microseconds (numpy)."""
+    delay = np.zeros(iters, np.float32)
+    base = np.zeros(iters, np.float32)
+    _check(lib().paam_measure_preemption(int(device), int(kind), int(iters), delay.ctypes.data, base.ctypes.data),
+           "paam_measure_preemption")
+    return delay, base
 
 
 def paam_diag_gelu(z, gelu=None, grad=None, stream=None):

@@ -49,3 +49,17 @@ def test_end_to_end_rejects_bad_index():
     with pytest.raises(pkg.PaamError):
         pkg.paam_rta_end_to_end(ctx(), b, off, chain, D, 0, R, st, Re, se)
     b.free()
+
+
+def test_preemption_measurement_runs_every_kernel_kind():
+    """The preemption-cost measurement: finite per-iteration delays and
+    positive baselines for each of the four kernel kinds; bad arguments are
+    refused before any device work."""
+    import paper_2404_06452_gb300 as pkg
+
+    for kind in range(4):
+        delay, base = pkg.paam_measure_preemption(kind, 20)
+        assert np.all(np.isfinite(delay)) and np.all(base > 0), (kind, delay, base)
+        assert np.all(delay > -base)  # the contended run cannot be shorter than nothing
+    with pytest.raises(pkg.PaamError):
+        pkg.paam_measure_preemption(4, 10)
