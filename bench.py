@@ -148,6 +148,11 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
 # workload in launch configuration 3 (analyze_reg1_kernel<16>): 937.04 MB.
 # Valid only while that kernel is unchanged and the autotuner picks it.
 TRAFFIC_PER_SYSTEM = {3: 937.043e6 / 500_000}
+# Executed warp-instructions per system of the same kernel and capture
+# (smsp__inst_executed.sum / 500,000 systems): the instruction-issue side of
+# the kernel, against the issue peak of 152 SMs x 4 schedulers x 1 per clock.
+WARP_INST_PER_SYSTEM = {3: 838.404456e6 / 500_000}
+ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions / s at the 2070 MHz maximum SM clock
 
 
 def algorithmic_bytes(sy) -> int:
@@ -636,6 +641,12 @@ def run_ours(args):
                 "frac": achieved / pk["hbm_gbs"], "traffic": None if traffic is None else traffic * sy.n_sys,
                 "traffic_src": "ncu capture of 500k systems, scaled per system" if traffic else None,
                 "peak_src": pk["src"],
+                "issue": None if cfg_index not in WARP_INST_PER_SYSTEM else {
+                    "bound": "issue", "unit": "warp-instructions/s",
+                    "achieved": WARP_INST_PER_SYSTEM[cfg_index] * sy.n_sys / (kern_ms / 1e3),
+                    "peak": ISSUE_PEAK,
+                    "frac": WARP_INST_PER_SYSTEM[cfg_index] * sy.n_sys / (kern_ms / 1e3) / ISSUE_PEAK,
+                    "note": "executed (not algorithmic) instructions per system, from the ncu capture"},
                 "kernel": CONFIG_KERNEL.get(cfg_index, "analysis kernel"),
                 "algorithmic_bytes_per_launch": alg}
 
