@@ -64,12 +64,25 @@ def _c(a, dt):
     return None if a is None else np.ascontiguousarray(a, dtype=dt)
 
 
+MAX_ACC = 8  # accelerators per system the oracle handles (R1: one server each)
+
+
+def _acc(sy):
+    acc = getattr(sy, "acc", None)
+    if acc is None or len(acc) == 0:
+        return None
+    acc = np.ascontiguousarray(acc, dtype=np.int32)
+    if acc.min() < 0 or acc.max() >= MAX_ACC:
+        raise ValueError(f"accelerator index outside 0..{MAX_ACC - 1}")
+    return acc
+
+
 def _arrays(sy):
     return dict(
         sys_chain_off=_c(sy.sys_chain_off, np.int64), chain_cb_off=_c(sy.chain_cb_off, np.int64),
         cb_seg_off=_c(sy.cb_seg_off, np.int64), T=_c(sy.T, np.int64), D=_c(sy.D, np.int64),
         prio=_c(sy.prio, np.int32), exec=_c(sy.exec, np.int32), spin=_c(sy.spin, np.uint8),
-        E=_c(sy.E, np.int64), A=_c(sy.A, np.int64), sys_exec_off=_c(sy.sys_exec_off, np.int64),
+        E=_c(sy.E, np.int64), A=_c(sy.A, np.int64), acc=_acc(sy), sys_exec_off=_c(sy.sys_exec_off, np.int64),
         exec_core=_c(sy.exec_core, np.int32), exec_prio=_c(sy.exec_prio, np.int32),
     )
 
@@ -102,12 +115,12 @@ def analyze(sy, n_buckets: int = 1, eps: int = 0, kappa: int = 0, blocking_mode:
     wk = np.zeros(ns, np.int64) if work else None
     f = lib.oracle_analyze
     f.restype = None
-    f.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 13 + [
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 14 + [
         ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32] + [ctypes.c_void_p] * 5
 
     def run(r):
         f(r[0], r[1], _p(a["sys_chain_off"]), _p(a["chain_cb_off"]), _p(a["cb_seg_off"]), _p(a["T"]),
-          _p(a["D"]), _p(a["prio"]), _p(a["exec"]), _p(a["spin"]), _p(a["E"]), _p(a["A"]),
+          _p(a["D"]), _p(a["prio"]), _p(a["exec"]), _p(a["spin"]), _p(a["E"]), _p(a["A"]), _p(a["acc"]),
           _p(a["sys_exec_off"]), _p(a["exec_core"]), _p(a["exec_prio"]), int(n_buckets), int(eps),
           int(kappa), int(blocking_mode), _p(R), _p(st), _p(verdict), _p(ax), _p(wk))
 
@@ -147,7 +160,7 @@ def search(sy, ranks: np.ndarray, n_buckets: int = 1, eps: int = 0, kappa: int =
     nc = len(a["T"])
     f = lib.oracle_search
     f.restype = None
-    f.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 12 + [
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 13 + [
         ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
         ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 4
 
@@ -155,7 +168,7 @@ def search(sy, ranks: np.ndarray, n_buckets: int = 1, eps: int = 0, kappa: int =
         Rs = np.zeros(nc, np.int64)
         sts = np.zeros(nc, np.uint8)
         f(r[0], r[1], _p(a["sys_chain_off"]), _p(a["chain_cb_off"]), _p(a["cb_seg_off"]), _p(a["T"]),
-          _p(a["D"]), _p(a["prio"]), _p(a["exec"]), _p(a["spin"]), _p(a["E"]), _p(a["A"]),
+          _p(a["D"]), _p(a["prio"]), _p(a["exec"]), _p(a["spin"]), _p(a["E"]), _p(a["A"]), _p(a["acc"]),
           _p(a["sys_exec_off"]), _p(a["exec_core"]), int(n_buckets), int(eps), int(kappa), int(blocking_mode),
           _p(ranks),
           K, nmax, 1 if stop_at_first else 0, _p(cand_ok), _p(first_ok), _p(Rs), _p(sts))

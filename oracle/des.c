@@ -18,11 +18,12 @@
  *   - a callback with eta segments runs its CPU time E split into eta + 1
  *     parts around the segments; each segment is a request to the accelerator
  *     server followed by eps units of client-side CPU overhead (Sec. IV-F);
- *   - the server maps accelerator-using chains into n buckets by descending
- *     priority, evenly (rule R2); within a bucket requests run
- *     non-preemptively in chain-priority order (R3); a higher bucket
- *     preempts a lower one (R4); a request occupies the accelerator for
- *     A + 2 kappa units (preemption cost charged in full);
+ *   - each accelerator has its own server (R1); a server maps the chains
+ *     using its accelerator into n buckets by descending priority, evenly
+ *     (R2); within a bucket requests run non-preemptively in chain-priority
+ *     order (R3); a higher bucket preempts a lower one (R4); a request
+ *     occupies its accelerator for A + 2 kappa units (preemption cost charged
+ *     in full);
  *   - a spinning client occupies its core while its request is handled; a
  *     suspending one releases the core but still holds its executor.
  */
@@ -35,12 +36,13 @@
 #define DES_MAXSEG 64
 #define DES_MAXX 8
 #define DES_MAXJOBS 64
+#define DES_MAXACC 4
 
 enum { PH_NONE = 0, PH_READY, PH_CPU, PH_ACCEL, PH_EPS };
 
 typedef struct {
     /* static */
-    int64_t T, prio, spin, exec, bucket;
+    int64_t T, prio, spin, exec, bucket[DES_MAXACC];
     int32_t cb_lo, cb_n;
     /* dynamic */
     int64_t next_rel;
@@ -54,6 +56,7 @@ typedef struct {
     int64_t rem;        /* remaining units of the current CPU / eps phase */
     int64_t acc_rem;    /* remaining accelerator units of the current request */
     int32_t acc_started;
+    int32_t req_acc;    /* the accelerator of the current request */
 } sim_chain;
 
 typedef struct {
@@ -63,6 +66,8 @@ typedef struct {
     const int32_t *nseg;
     const int32_t *seg_lo;
     const int64_t *A;   /* per segment (simulated execution time) */
+    const int32_t *acc; /* per segment: its accelerator */
+    int32_t n_acc;
     const int32_t *exec_core, *exec_prio;
     sim_chain ch[DES_MAXN];
     int32_t busy[DES_MAXX]; /* chain holding the executor, -1 idle */
@@ -99,25 +104,23 @@ static int32_t core_runner(const sim_t *s, int32_t core)
     return best;
 }
 
-/* request the accelerator currently serves, or -1 */
-static int32_t accel_pick(sim_t *s)
+/* the request accelerator u currently serves, or -1 */
+static int32_t accel_pick(sim_t *s, int32_t u)
 {
+#define WAITS(c) (s->ch[c].active && s->ch[c].phase == PH_ACCEL && s->ch[c].req_acc == u)
     int64_t best_b = INT64_MAX;
     for (int32_t c = 0; c < s->n; ++c)
-        if (s->ch[c].active && s->ch[c].phase == PH_ACCEL && s->ch[c].bucket < best_b)
-            best_b = s->ch[c].bucket;
+        if (WAITS(c) && s->ch[c].bucket[u] < best_b) best_b = s->ch[c].bucket[u];
     if (best_b == INT64_MAX) return -1;
     for (int32_t c = 0; c < s->n; ++c) /* an in-progress request keeps its bucket's worker */
-        if (s->ch[c].active && s->ch[c].phase == PH_ACCEL && s->ch[c].bucket == best_b &&
-            s->ch[c].acc_started)
-            return c;
+        if (WAITS(c) && s->ch[c].bucket[u] == best_b && s->ch[c].acc_started) return c;
     int32_t pick = -1;
     for (int32_t c = 0; c < s->n; ++c)
-        if (s->ch[c].active && s->ch[c].phase == PH_ACCEL && s->ch[c].bucket == best_b &&
-            (pick < 0 || s->ch[c].prio > s->ch[pick].prio))
+        if (WAITS(c) && s->ch[c].bucket[u] == best_b && (pick < 0 || s->ch[c].prio > s->ch[pick].prio))
             pick = c;
     s->ch[pick].acc_started = 1;
     return pick;
+#undef WAITS
 }
 
 /* move chain c past any finished phase; returns 1 if something changed */
@@ -145,6 +148,7 @@ static int advance(sim_t *s, int32_t c, int64_t now, int64_t *max_resp)
             if (h->part < s->nseg[cbg]) { /* next: accelerator request of segment `part` */
                 h->phase = PH_ACCEL;
                 h->acc_rem = s->A[s->seg_lo[cbg] + h->part] + 2 * s->kappa;
+                h->req_acc = s->acc ? s->acc[s->seg_lo[cbg] + h->part] : 0;
                 h->acc_started = 0;
             } else { /* callback done */
                 s->busy[h->exec] = -1;
@@ -241,8 +245,10 @@ static int run_once(sim_t *s, const int64_t *offset, int64_t rel_end, int64_t t_
                     changed = 1;
                 }
             }
-            int32_t a = accel_pick(s);
-            if (a >= 0 && s->ch[a].acc_rem == 0) changed |= advance(s, a, t, max_resp);
+            for (int32_t u = 0; u < s->n_acc; ++u) {
+                int32_t a = accel_pick(s, u);
+                if (a >= 0 && s->ch[a].acc_rem == 0) changed |= advance(s, a, t, max_resp);
+            }
             if (!changed) break;
         }
         for (int32_t c = 0; c < s->n; ++c)
@@ -257,8 +263,10 @@ static int run_once(sim_t *s, const int64_t *offset, int64_t rel_end, int64_t t_
             if ((h->phase == PH_CPU || h->phase == PH_EPS) && h->rem > 0) h->rem -= 1;
             /* a spinning client burns the unit without progress */
         }
-        int32_t a = accel_pick(s);
-        if (a >= 0 && s->ch[a].acc_rem > 0) s->ch[a].acc_rem -= 1;
+        for (int32_t u = 0; u < s->n_acc; ++u) { /* each accelerator serves its own requests */
+            int32_t a = accel_pick(s, u);
+            if (a >= 0 && s->ch[a].acc_rem > 0) s->ch[a].acc_rem -= 1;
+        }
     }
     for (int32_t c = 0; c < s->n; ++c) { /* unfinished work: report at least the elapsed time */
         sim_chain *h = &s->ch[c];
@@ -283,7 +291,7 @@ static int run_once(sim_t *s, const int64_t *offset, int64_t rel_end, int64_t t_
  */
 int des_explore(int32_t n, const int64_t *T, const int32_t *prio, const int32_t *exec,
                 const uint8_t *spin, const int32_t *cb_n, const int64_t *E, const int32_t *nseg,
-                const int64_t *A, int32_t nx, const int32_t *exec_core, const int32_t *exec_prio,
+                const int64_t *A, const int32_t *acc, int32_t nx, const int32_t *exec_core, const int32_t *exec_prio,
                 int32_t n_buckets, int64_t eps, int64_t kappa, int64_t t_limit_extra,
                 int32_t all_variants, int64_t *max_resp)
 {
@@ -317,15 +325,30 @@ int des_explore(int32_t n, const int64_t *T, const int32_t *prio, const int32_t 
         }
     }
     if (nsg > DES_MAXSEG) return -2;
-    /* rule R2: users ranked by descending chain priority, n evenly sized groups */
-    int32_t users = 0;
-    for (int32_t c = 0; c < n; ++c) users += segs_of[c] > 0 ? 1 : 0;
-    for (int32_t c = 0; c < n; ++c) {
-        int32_t r = 0;
-        for (int32_t k = 0; k < n; ++k)
-            if (segs_of[k] > 0 && prio[k] > prio[c]) r += 1;
-        s.ch[c].bucket = segs_of[c] > 0 ? ((int64_t)r * n_buckets) / users : INT64_MAX;
+    s.acc = acc;
+    s.n_acc = 1;
+    for (int32_t q = 0; acc && q < nsg; ++q) {
+        if (acc[q] < 0 || acc[q] >= DES_MAXACC) return -2;
+        if (acc[q] + 1 > s.n_acc) s.n_acc = acc[q] + 1;
     }
+    /* rule R2 per accelerator: its users ranked by descending chain priority,
+     * n evenly sized groups */
+    for (int32_t u = 0; u < s.n_acc; ++u) {
+        int32_t uses[DES_MAXN], users = 0;
+        for (int32_t c = 0; c < n; ++c) {
+            uses[c] = 0;
+            for (int32_t j = s.ch[c].cb_lo; j < s.ch[c].cb_lo + s.ch[c].cb_n; ++j)
+                for (int32_t q = seg_lo[j]; q < seg_lo[j] + nseg[j]; ++q) uses[c] |= (acc ? acc[q] : 0) == u;
+            users += uses[c];
+        }
+        for (int32_t c = 0; c < n; ++c) {
+            int32_t r = 0;
+            for (int32_t k = 0; k < n; ++k)
+                if (uses[k] && prio[k] > prio[c]) r += 1;
+            s.ch[c].bucket[u] = uses[c] ? ((int64_t)r * n_buckets) / users : INT64_MAX;
+        }
+    }
+    (void)segs_of;
     int64_t Ev[DES_MAXCB], Av[DES_MAXSEG];
     s.E = Ev;
     s.A = Av;

@@ -14,6 +14,11 @@ SCHED, OVERRUN, DEP = 0, 1, 2
 INF = None
 
 
+def _seg(seg):
+    # a segment entry: A (accelerator 0) or an (A, accelerator) pair
+    return (seg, 0) if isinstance(seg, int) else (int(seg[0]), int(seg[1]))
+
+
 def _mu(t: int, T: int) -> int:
     # Lemma 1 (Eq. 2): ceil(t / T) + 1
     return -(-t // T) + 1
@@ -40,39 +45,52 @@ def scan_system(sysd: dict, n_buckets: int = 1, eps: int = 0, kappa: int = 0):
     eprio = [ex[c["exec"]]["prio"] for c in ch]
     E = [sum(e for e, _ in c["cbs"]) for c in ch]
     Emax = [max([e for e, _ in c["cbs"]], default=0) for c in ch]
-    segs = [[a + 2 * kappa for _, ss in c["cbs"] for a in ss] for c in ch]  # A* (Sec. IV-F)
+    # segments as (A*, accelerator); each accelerator has its own server (rule R1)
+    segs = [[(a + 2 * kappa, u) for _, ss in c["cbs"] for a, u in map(_seg, ss)] for c in ch]  # A* (Sec. IV-F)
     delta = [len(s) for s in segs]
-    S = [sum(s) for s in segs]
-    M = [max(s, default=0) for s in segs]
-
-    users = sorted([c for c in range(n) if delta[c] > 0], key=lambda c: -prio[c])
-    bucket = {c: (i * n_buckets) // len(users) for i, c in enumerate(users)}
-    blk = [max([M[l] for l in users if prio[l] < prio[c] and bucket[l] == bucket.get(c)], default=0)
-           for c in range(n)]
+    accs = sorted({u for s in segs for _, u in s})
+    S = {u: [sum(a for a, v in s if v == u) for s in segs] for u in accs}
+    dl = {u: [sum(1 for _, v in s if v == u) for s in segs] for u in accs}
+    M = {u: [max([a for a, v in s if v == u], default=0) for s in segs] for u in accs}
+    blk, hps = {}, {}
+    for u in accs:
+        users = sorted([c for c in range(n) if dl[u][c] > 0], key=lambda c: -prio[c])
+        bucket = {c: (i * n_buckets) // len(users) for i, c in enumerate(users)}
+        blk[u] = [max([M[u][l] for l in users if prio[l] < prio[c] and bucket[l] == bucket.get(c)], default=0)
+                  for c in range(n)]
+        hps[u] = [[h for h in users if prio[h] > prio[c]] for c in range(n)]
     B = [max([Emax[l] for l in range(n) if xe[l] == xe[c] and prio[l] < prio[c]], default=0)
          for c in range(n)]
-    hps = [[h for h in users if prio[h] > prio[c]] for c in range(n)]
     hp = [[h for h in range(n) if xe[h] == xe[c] and prio[h] > prio[c]] for c in range(n)]
     hpp = [[h for h in range(n) if xe[h] != xe[c] and core[h] == core[c] and eprio[h] > eprio[c]]
            for c in range(n)]
 
-    # Lemma 2 / Eq. 3 for every segment, summed; None if some segment exceeds D_c
-    Hseg = []
-    for c in range(n):
-        tot = 0
-        for a in segs[c]:
-            h = _least_t(lambda t, a=a, c=c: a + blk[c] + sum(_mu(t, T[k]) * S[k] for k in hps[c]), D[c])
-            if h is None:
-                tot = None
-                break
-            tot += h
-        Hseg.append(tot)
+    # Lemma 2 / Eq. 3 for every segment, summed per accelerator; None if some
+    # segment on that accelerator exceeds D_c
+    Hseg = {u: [] for u in accs}
+    for u in accs:
+        for c in range(n):
+            tot = 0
+            for a, v in segs[c]:
+                if v != u:
+                    continue
+                h = _least_t(lambda t, a=a, c=c, u=u: a + blk[u][c] + sum(_mu(t, T[k]) * S[u][k] for k in hps[u][c]),
+                             D[c])
+                if h is None:
+                    tot = None
+                    break
+                tot += h
+            Hseg[u].append(tot)
 
     def Hstar(c, t):
         if delta[c] == 0:
             return 0
-        per_chain = S[c] + delta[c] * blk[c] + sum(_mu(t, T[k]) * S[k] for k in hps[c])  # Eq. 4
-        h = per_chain if Hseg[c] is None else min(Hseg[c], per_chain)
+        h = 0
+        for u in accs:  # one term per accelerator the chain uses (R1)
+            if dl[u][c] == 0:
+                continue
+            per_chain = S[u][c] + dl[u][c] * blk[u][c] + sum(_mu(t, T[k]) * S[u][k] for k in hps[u][c])  # Eq. 4
+            h += per_chain if Hseg[u][c] is None else min(Hseg[u][c], per_chain)
         return h + delta[c] * eps  # Eq. 1
 
     R = [None] * n

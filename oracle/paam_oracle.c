@@ -45,6 +45,7 @@
 enum { ST_SCHED = 0, ST_OVERRUN = 1, ST_DEP = 2, ST_ITERCAP = 3 };
 
 #define O_INF INT64_MAX
+#define O_MAXACC 8 /* accelerators per system handled here */
 
 /* diagnostic counters (test infrastructure): fixed-point iterations per system */
 static __thread int64_t g_seg_iters, g_chain_iters;
@@ -59,10 +60,13 @@ typedef struct {
     int64_t eprio; /* priority of that executor */
     int64_t spin;  /* 1: busy-waits during accelerator requests */
     int64_t seg_lo, seg_hi;
-    /* step 1 */
+    /* step 1 (totals over the chain's segments) */
     int64_t E, Emax, delta, S, M;
     /* steps 2-5 */
     int64_t bucket, blk, B, Hseg;
+    /* the same per accelerator (rule R1: one server per accelerator, analysed
+     * independently); with one accelerator, index 0 equals the fields above */
+    int64_t dA[O_MAXACC], SA[O_MAXACC], MA[O_MAXACC], bucketA[O_MAXACC], blkA[O_MAXACC], HsegA[O_MAXACC];
     /* step 6 */
     int64_t R, Hstar;
     int64_t status, done;
@@ -74,33 +78,39 @@ static int64_t ceil_div(int64_t t, int64_t T) { return t / T + (t % T != 0 ? 1 :
 /* Lemma 1 (Eq. 2): at most ceil(t / T) + 1 arrivals in any interval t */
 static int64_t mu(int64_t t, int64_t T) { return ceil_div(t, T) + 1; }
 
-/* Eq. 4 for chain c evaluated at window t */
-static int64_t H_chain(const chain_t *ch, int64_t n, int64_t c, int64_t t, int64_t *work)
+/* Eq. 4 for chain c's requests to accelerator a, evaluated at window t */
+static int64_t H_chain(const chain_t *ch, int64_t n, int64_t c, int64_t a, int64_t t, int64_t *work)
 {
-    int64_t h = ch[c].S + ch[c].delta * ch[c].blk;
+    int64_t h = ch[c].SA[a] + ch[c].dA[a] * ch[c].blkA[a];
     for (int64_t k = 0; k < n; ++k) {
-        if (ch[k].delta > 0 && ch[k].prio > ch[c].prio) { /* k in hps of every segment of c */
-            h += mu(t, ch[k].T) * ch[k].S;
+        if (ch[k].dA[a] > 0 && ch[k].prio > ch[c].prio) { /* k in hps of every segment of c on a */
+            h += mu(t, ch[k].T) * ch[k].SA[a];
             if (work) *work += 1;
         }
     }
     return h;
 }
 
-/* H_c(t) = min(per-segment sum of Eq. 3, Eq. 4 at t); H*_c = H_c + delta_c eps (Eq. 1) */
+/* H_c(t) = sum over the accelerators c uses of min(per-segment sum of Eq. 3,
+ * Eq. 4 at t) (one accelerator: the minimum itself);
+ * H*_c = H_c + delta_c eps (Eq. 1) */
 static int64_t H_star(const chain_t *ch, int64_t n, int64_t c, int64_t t, int64_t eps, int64_t *work)
 {
     if (ch[c].delta == 0) return 0;
-    int64_t hc = H_chain(ch, n, c, t, work);
-    int64_t h = ch[c].Hseg < hc ? ch[c].Hseg : hc;
+    int64_t h = 0;
+    for (int64_t a = 0; a < O_MAXACC; ++a) {
+        if (ch[c].dA[a] == 0) continue;
+        const int64_t hc = H_chain(ch, n, c, a, t, work);
+        h += ch[c].HsegA[a] < hc ? ch[c].HsegA[a] : hc;
+    }
     return h + ch[c].delta * eps;
 }
 
 static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_t *chain_cb_off,
                            const int64_t *cb_seg_off, const int64_t *T, const int64_t *D,
                            const int32_t *prio, const int32_t *exec, const uint8_t *spin,
-                           const int64_t *E, const int64_t *A, const int64_t *sys_exec_off,
-                           const int32_t *exec_core, const int32_t *exec_prio,
+                           const int64_t *E, const int64_t *A, const int32_t *acc,
+                           const int64_t *sys_exec_off, const int32_t *exec_core, const int32_t *exec_prio,
                            const int16_t *rank, int32_t n_buckets, int64_t eps, int64_t kappa,
                            int32_t blocking_mode, int64_t *R_out, uint8_t *st_out, uint8_t *verdict,
                            int64_t *aux, int64_t *work_out)
@@ -141,35 +151,43 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
             if (E[b] > ch[c].Emax) ch[c].Emax = E[b];
             for (int64_t q = cb_seg_off[b]; q < cb_seg_off[b + 1]; ++q) {
                 const int64_t a_star = A[q] + 2 * kappa;
+                const int64_t u = acc ? acc[q] : 0; /* the accelerator of this segment */
                 ch[c].delta += 1;
                 ch[c].S += a_star;
                 if (a_star > ch[c].M) ch[c].M = a_star;
+                ch[c].dA[u] += 1;
+                ch[c].SA[u] += a_star;
+                if (a_star > ch[c].MA[u]) ch[c].MA[u] = a_star;
             }
         }
     }
 
     /* step 2: buckets -- accelerator users split into n evenly sized groups,
      * highest priorities first (Sec. IV-C; rule R2) */
-    int64_t n_users = 0;
-    for (int64_t c = 0; c < n; ++c) n_users += ch[c].delta > 0 ? 1 : 0;
-    for (int64_t c = 0; c < n; ++c) {
-        ch[c].bucket = -1;
-        if (ch[c].delta == 0) continue;
-        int64_t r = 0;
-        for (int64_t k = 0; k < n; ++k)
-            if (ch[k].delta > 0 && ch[k].prio > ch[c].prio) r += 1;
-        ch[c].bucket = r * (int64_t)n_buckets / n_users;
+    for (int64_t a = 0; a < O_MAXACC; ++a) { /* each accelerator's server has its own buckets (R1) */
+        int64_t n_users = 0;
+        for (int64_t c = 0; c < n; ++c) n_users += ch[c].dA[a] > 0 ? 1 : 0;
+        for (int64_t c = 0; c < n; ++c) {
+            ch[c].bucketA[a] = -1;
+            if (ch[c].dA[a] == 0) continue;
+            int64_t r = 0;
+            for (int64_t k = 0; k < n; ++k)
+                if (ch[k].dA[a] > 0 && ch[k].prio > ch[c].prio) r += 1;
+            ch[c].bucketA[a] = r * (int64_t)n_buckets / n_users;
+        }
     }
 
     /* step 3: the longest request of a lower-priority chain in the same bucket
      * (rules R2-R3; the max term of Eq. 3 and Eq. 4) */
     for (int64_t c = 0; c < n; ++c) {
-        ch[c].blk = 0;
-        if (ch[c].delta == 0) continue;
-        for (int64_t l = 0; l < n; ++l)
-            if (ch[l].delta > 0 && ch[l].prio < ch[c].prio && ch[l].bucket == ch[c].bucket &&
-                ch[l].M > ch[c].blk)
-                ch[c].blk = ch[l].M;
+        for (int64_t a = 0; a < O_MAXACC; ++a) {
+            ch[c].blkA[a] = 0;
+            if (ch[c].dA[a] == 0) continue;
+            for (int64_t l = 0; l < n; ++l)
+                if (ch[l].dA[a] > 0 && ch[l].prio < ch[c].prio && ch[l].bucketA[a] == ch[c].bucketA[a] &&
+                    ch[l].MA[a] > ch[c].blkA[a])
+                    ch[c].blkA[a] = ch[l].MA[a];
+        }
     }
 
     /* step 4: non-preemptive blocking by one callback of a lower-priority chain
@@ -187,20 +205,21 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
     const int64_t n_q = n > 0 ? ch[n - 1].seg_hi - q_sys : 0;
     int64_t *hq = (int64_t *)calloc((size_t)(n_q > 0 ? n_q : 1), sizeof(int64_t));
     for (int64_t c = 0; c < n; ++c) {
-        ch[c].Hseg = 0;
+        for (int64_t a = 0; a < O_MAXACC; ++a) ch[c].HsegA[a] = 0;
         for (int64_t q = ch[c].seg_lo; q < ch[c].seg_hi; ++q) {
             const int64_t a_star = A[q] + 2 * kappa;
-            int64_t h = a_star + ch[c].blk; /* the first two terms */
+            const int64_t u = acc ? acc[q] : 0;
+            int64_t h = a_star + ch[c].blkA[u]; /* the first two terms */
             int64_t it = 0;
             for (;;) {
                 if (h > ch[c].D) {
                     h = O_INF;
                     break;
                 }
-                int64_t nh = a_star + ch[c].blk;
+                int64_t nh = a_star + ch[c].blkA[u];
                 for (int64_t k = 0; k < n; ++k) {
-                    if (ch[k].delta > 0 && ch[k].prio > ch[c].prio) {
-                        nh += mu(h, ch[k].T) * ch[k].S;
+                    if (ch[k].dA[u] > 0 && ch[k].prio > ch[c].prio) {
+                        nh += mu(h, ch[k].T) * ch[k].SA[u];
                         work += 1;
                     }
                 }
@@ -213,10 +232,21 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                 }
             }
             hq[q - q_sys] = h;
-            if (h == O_INF || ch[c].Hseg == O_INF)
-                ch[c].Hseg = O_INF;
+            if (h == O_INF || ch[c].HsegA[u] == O_INF)
+                ch[c].HsegA[u] = O_INF;
             else
-                ch[c].Hseg += h;
+                ch[c].HsegA[u] += h;
+        }
+        /* per-chain summaries (for the diagnostic output): with one accelerator
+         * these are that accelerator's values */
+        ch[c].Hseg = 0;
+        ch[c].blk = 0;
+        ch[c].bucket = -1;
+        for (int64_t a = 0; a < O_MAXACC; ++a) {
+            if (ch[c].dA[a] == 0) continue;
+            ch[c].Hseg = (ch[c].Hseg == O_INF || ch[c].HsegA[a] == O_INF) ? O_INF : ch[c].Hseg + ch[c].HsegA[a];
+            if (ch[c].blkA[a] > ch[c].blk) ch[c].blk = ch[c].blkA[a];
+            if (ch[c].bucket < 0) ch[c].bucket = ch[c].bucketA[a];
         }
     }
 
@@ -283,8 +313,12 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
             /* start: B_c + E_c + H*_c with the interference part of Eq. 4 empty */
             int64_t h0 = 0;
             if (ch[c].delta > 0) {
-                int64_t own = ch[c].S + ch[c].delta * ch[c].blk;
-                h0 = (ch[c].Hseg < own ? ch[c].Hseg : own) + ch[c].delta * eps;
+                for (int64_t a = 0; a < O_MAXACC; ++a) {
+                    if (ch[c].dA[a] == 0) continue;
+                    const int64_t own = ch[c].SA[a] + ch[c].dA[a] * ch[c].blkA[a];
+                    h0 += ch[c].HsegA[a] < own ? ch[c].HsegA[a] : own;
+                }
+                h0 += ch[c].delta * eps;
             }
             int64_t R = ch[c].B + ch[c].E + h0;
             int64_t it = 0;
@@ -354,7 +388,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
 void oracle_analyze_iters(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
                           const int64_t *chain_cb_off, const int64_t *cb_seg_off, const int64_t *T,
                           const int64_t *D, const int32_t *prio, const int32_t *exec,
-                          const uint8_t *spin, const int64_t *E, const int64_t *A,
+                          const uint8_t *spin, const int64_t *E, const int64_t *A, const int32_t *acc,
                           const int64_t *sys_exec_off, const int32_t *exec_core,
                           const int32_t *exec_prio, int32_t n_buckets, int64_t eps, int64_t kappa,
                           int32_t blocking_mode, int64_t *R, uint8_t *status, int64_t *seg_iters,
@@ -363,7 +397,7 @@ void oracle_analyze_iters(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
     for (int64_t s = lo; s < hi; ++s) {
         g_seg_iters = 0;
         g_chain_iters = 0;
-        analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A,
+        analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A, acc,
                        sys_exec_off, exec_core, exec_prio, NULL, n_buckets, eps, kappa, blocking_mode, R,
                        status, NULL, NULL, NULL);
         seg_iters[s] = g_seg_iters;
@@ -382,14 +416,14 @@ void oracle_analyze_iters(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
 void oracle_analyze(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
                     const int64_t *chain_cb_off, const int64_t *cb_seg_off, const int64_t *T,
                     const int64_t *D, const int32_t *prio, const int32_t *exec,
-                    const uint8_t *spin, const int64_t *E, const int64_t *A,
+                    const uint8_t *spin, const int64_t *E, const int64_t *A, const int32_t *acc,
                     const int64_t *sys_exec_off, const int32_t *exec_core,
                     const int32_t *exec_prio, int32_t n_buckets, int64_t eps, int64_t kappa,
                     int32_t blocking_mode, int64_t *R, uint8_t *status, uint8_t *verdict, int64_t *aux,
                     int64_t *work)
 {
     for (int64_t s = lo; s < hi; ++s)
-        analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A,
+        analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A, acc,
                        sys_exec_off, exec_core, exec_prio, NULL, n_buckets, eps, kappa, blocking_mode, R,
                        status, verdict, aux, work);
 }
@@ -403,7 +437,7 @@ void oracle_analyze(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
 void oracle_search(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
                    const int64_t *chain_cb_off, const int64_t *cb_seg_off, const int64_t *T,
                    const int64_t *D, const int32_t *prio, const int32_t *exec, const uint8_t *spin,
-                   const int64_t *E, const int64_t *A, const int64_t *sys_exec_off,
+                   const int64_t *E, const int64_t *A, const int32_t *acc, const int64_t *sys_exec_off,
                    const int32_t *exec_core, int32_t n_buckets, int64_t eps, int64_t kappa,
                    int32_t blocking_mode, const int16_t *ranks, int32_t K, int32_t nmax, int32_t stop_at_first,
                    uint8_t *cand_ok, int32_t *first_ok, int64_t *R_scratch, uint8_t *st_scratch)
@@ -413,7 +447,7 @@ void oracle_search(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
         for (int32_t k = 0; k < K; ++k) {
             uint8_t v = 0;
             analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E,
-                           A, sys_exec_off, exec_core, NULL, ranks + (s * (int64_t)K + k) * nmax,
+                           A, acc, sys_exec_off, exec_core, NULL, ranks + (s * (int64_t)K + k) * nmax,
                            n_buckets, eps, kappa, blocking_mode, R_scratch, st_scratch, NULL, NULL, NULL);
             v = 1;
             for (int64_t c = sys_chain_off[s]; c < sys_chain_off[s + 1]; ++c)

@@ -11,11 +11,17 @@ import random
 import numpy as np
 
 
+def seg_parts(seg):
+    """(A, accelerator) of a segment entry: an int A (accelerator 0) or a pair."""
+    return (seg, 0) if isinstance(seg, int) else (int(seg[0]), int(seg[1]))
+
+
 def tiny_system(rng: random.Random, n_max: int = 3, cb_max: int = 2, x_max: int = 2,
                 exec_per_core: int = 2, periods=(4, 6, 8, 12), e_max: int = 3, a_max: int = 3,
                 p_seg: float = 0.5, p_spin: float = 0.5, implicit_deadline: bool = False,
-                n_min: int = 1, seg_max: int = 1):
-    """One system as a dict of Python lists (local indices)."""
+                n_min: int = 1, seg_max: int = 1, n_acc: int = 1):
+    """One system as a dict of Python lists (local indices).  With n_acc > 1
+    each segment is an (A, accelerator) pair, the accelerator uniform."""
     n = rng.randint(n_min, n_max)
     nx = rng.randint(1, x_max)
     prios = list(range(n))
@@ -29,6 +35,8 @@ def tiny_system(rng: random.Random, n_max: int = 3, cb_max: int = 2, x_max: int 
         for _ in range(ncb):
             E = rng.randint(0, e_max)
             segs = [rng.randint(0, a_max) for _ in range(seg_max) if rng.random() < p_seg]
+            if n_acc > 1:
+                segs = [(a, rng.randrange(n_acc)) for a in segs]
             cbs.append((E, segs))
         chains.append(dict(T=T, D=D, prio=prios[c], exec=rng.randrange(nx),
                            spin=1 if rng.random() < p_spin else 0, cbs=cbs))
@@ -52,8 +60,9 @@ def to_systems(dicts):
             ex.append(ch["exec"]); spin.append(ch["spin"])
             for (e, segs) in ch["cbs"]:
                 E.append(e)
-                for a in segs:
-                    A.append(a); acc.append(0)
+                for sg in segs:
+                    a, u = seg_parts(sg)
+                    A.append(a); acc.append(u)
                 so.append(len(A))
             cbo.append(len(E))
         sc.append(len(T))
