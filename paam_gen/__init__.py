@@ -108,6 +108,9 @@ def _load():
         lib.paam_gen_perms.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
         lib.paam_gen_perms.restype = None
+        lib.paam_gen_assign_wfd.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 5 + [
+            ctypes.c_int32, ctypes.c_void_p]
+        lib.paam_gen_assign_wfd.restype = None
         _lib = lib
         return lib
 
@@ -335,6 +338,24 @@ def candidate_ranks(sy: Systems, K: int, seed: int, nmax: int | None = None) -> 
     if K > 1:
         out[sysid, 1, local] = ranks_by((local, sy.D))
     return out
+
+
+def assign_accelerators(sy: Systems, n_units: int, threads: int | None = None) -> Systems:
+    """The same systems with their accelerator segments spread over n_units
+    units of the accelerator by worst-fit decreasing utilisation (A / T), per
+    system, as the PAAM server assigns them at registration."""
+    assert 1 <= n_units <= 64
+    lib = _load()
+    acc = np.zeros(len(sy.A), np.int32)
+    threads = threads or min(32, os.cpu_count() or 1)
+    bounds = np.linspace(0, sy.n_sys, threads + 1).astype(np.int64)
+    ranges = [(int(bounds[i]), int(bounds[i + 1])) for i in range(threads) if bounds[i] < bounds[i + 1]]
+    arrs = [np.ascontiguousarray(a, dtype=np.int64) for a in (sy.sys_chain_off, sy.chain_cb_off, sy.cb_seg_off,
+                                                                sy.T, sy.A)]
+    with ThreadPoolExecutor(len(ranges) or 1) as ex:
+        list(ex.map(lambda r: lib.paam_gen_assign_wfd(r[0], r[1], *[_ptr(a) for a in arrs], int(n_units),
+                                                      _ptr(acc)), ranges))
+    return Systems(**{**sy.__dict__, "acc": acc, "meta": dict(sy.meta, accelerator_units=int(n_units))})
 
 
 def split_end_to_end(sy: Systems, seed: int, max_sub: int = 3):

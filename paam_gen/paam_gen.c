@@ -18,6 +18,7 @@
  * threads.
  */
 #include <math.h>
+#include <stdlib.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -283,5 +284,50 @@ void paam_gen_perms(uint64_t seed, int64_t lo, int64_t hi, int32_t K, int32_t fi
                 o[j] = t;
             }
         }
+    }
+}
+
+/* Assignment of accelerator segments to n_units units of the accelerator,
+ * per system, by worst-fit decreasing (the bin-packing heuristic the PAAM
+ * server applies at client registration): segments in decreasing order of
+ * utilisation A / T of their chain (ties: lower segment index first), each to
+ * the unit with the least utilisation so far (ties: the lower unit).  Writes
+ * acc[q] for the segments of systems [lo, hi).  n_units <= 64. */
+void paam_gen_assign_wfd(int64_t lo, int64_t hi, const int64_t *sys_chain_off, const int64_t *chain_cb_off,
+                         const int64_t *cb_seg_off, const int64_t *T, const int64_t *A, int32_t n_units,
+                         int32_t *acc)
+{
+    double load[64];
+    for (int64_t s = lo; s < hi; ++s) {
+        const int64_t c0 = sys_chain_off[s], c1 = sys_chain_off[s + 1];
+        if (c1 == c0) continue;
+        const int64_t q0 = cb_seg_off[chain_cb_off[c0]], q1 = cb_seg_off[chain_cb_off[c1]];
+        const int64_t nq = q1 - q0;
+        if (nq <= 0) continue;
+        double *u = (double *)malloc((size_t)nq * sizeof(double));
+        int64_t *ord = (int64_t *)malloc((size_t)nq * sizeof(int64_t));
+        for (int64_t c = c0; c < c1; ++c)
+            for (int64_t q = cb_seg_off[chain_cb_off[c]]; q < cb_seg_off[chain_cb_off[c + 1]]; ++q)
+                u[q - q0] = (double)A[q] / (double)T[c];
+        for (int64_t i = 0; i < nq; ++i) ord[i] = i;
+        for (int64_t i = 1; i < nq; ++i) { /* insertion sort: decreasing u, stable */
+            const int64_t x = ord[i];
+            int64_t j = i;
+            while (j > 0 && u[ord[j - 1]] < u[x]) {
+                ord[j] = ord[j - 1];
+                --j;
+            }
+            ord[j] = x;
+        }
+        for (int32_t k = 0; k < n_units; ++k) load[k] = 0.0;
+        for (int64_t i = 0; i < nq; ++i) {
+            int32_t best = 0;
+            for (int32_t k = 1; k < n_units; ++k)
+                if (load[k] < load[best]) best = k;
+            load[best] += u[ord[i]];
+            acc[q0 + ord[i]] = best;
+        }
+        free(u);
+        free(ord);
     }
 }

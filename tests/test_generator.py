@@ -85,3 +85,30 @@ def test_candidate_ranks():
     ref = oracle.search(sy, r[:, :1], threads=4)
     a = oracle.analyze(sy, derive_exec_prio=True, threads=4)
     assert np.array_equal(ref["cand_ok"][:, 0], a["verdict"])
+
+
+def test_wfd_assignment_hand_case_and_balance():
+    import numpy as np
+
+    from paam_gen import tiny
+
+    # one system: chain periods 10 and 20; segment utilisations 4/10, 1/10, 6/20, 5/20
+    d = dict(chains=[dict(T=10, D=10, prio=1, exec=0, spin=0, cbs=[(1, [4, 1])]),
+                     dict(T=20, D=20, prio=0, exec=0, spin=0, cbs=[(1, [6]), (1, [5])])],
+             execs=[dict(core=0, prio=1)])
+    out = g.assign_accelerators(tiny.to_systems([d]), 2)
+    # decreasing: 0.4 (seg 0) -> unit 0; 0.3 (seg 2) -> unit 1; 0.25 (seg 3) -> unit 1 (0.3 < 0.4);
+    # 0.1 (seg 1) -> unit 0 (0.4 < 0.55)
+    assert out.acc.tolist() == [0, 0, 1, 1]
+    sy = g.generate("cfg3", n_sys=300)
+    for units in (2, 3, 5):
+        acc = g.assign_accelerators(sy, units).acc
+        for s in range(sy.n_sys):
+            c0, c1 = sy.sys_chain_off[s], sy.sys_chain_off[s + 1]
+            q0, q1 = sy.cb_seg_off[sy.chain_cb_off[c0]], sy.cb_seg_off[sy.chain_cb_off[c1]]
+            if q1 == q0:
+                continue
+            chain_of = np.repeat(np.arange(c0, c1), np.diff(sy.cb_seg_off[sy.chain_cb_off[c0:c1 + 1]]))
+            u = sy.A[q0:q1] / sy.T[chain_of]
+            load = np.bincount(acc[q0:q1], weights=u, minlength=units)
+            assert load.max() - load.min() <= u.max() + 1e-12
