@@ -51,6 +51,7 @@ extern "C" {
 
 #define PAAM_MAX_CHAINS 64        /* chains per system                           */
 #define PAAM_MAX_TIME (1LL << 40) /* largest T, D, E, A accepted (about 18 min)  */
+#define PAAM_MAX_ACC 4            /* accelerators per batch (indices 0..3)        */
 #define PAAM_MAX_OVERHEAD (1LL << 32) /* largest eps, kappa accepted             */
 
 typedef struct paam_ctx paam_ctx;
@@ -71,8 +72,12 @@ typedef struct paam_model paam_model;
  *   spin[c]        1 if the chain busy-waits on accelerator requests, else 0
  *   E[b]           CPU WCET of callback b (all its CPU segments), >= 0
  *   A[q]           WCET of accelerator segment q, >= 0
- *   acc[q]         accelerator of segment q; NULL or all 0 (one accelerator
- *                  per system in this build, else PAAM_E_UNSUPPORTED)
+ *   acc[q]         accelerator of segment q, 0 .. PAAM_MAX_ACC - 1 (NULL: all
+ *                  0).  Each accelerator has its own server (rule R1) and is
+ *                  analysed on its own: buckets, same-bucket blocking and hps
+ *                  are per accelerator, and H_c sums the per-accelerator
+ *                  handling times.  A batch that uses a second accelerator
+ *                  is analysed by the exact int64 kernel (slower)
  *   exec_core[x]   CPU core of executor x, >= 0
  *   exec_prio[x]   executor (process) priority, larger = higher, distinct among
  *                  executors of one core; NULL = derived as the highest chain
@@ -145,7 +150,8 @@ const char *paam_strerror(int code);
  * PAAM_E_RANGE when N * (ceil(Dmax / Tmin) + 1) * Cmax + Base could exceed
  * 2^62 for some system (the largest value any fixed-point iterate of Eqs. 3-6
  * can take with eps, kappa <= PAAM_MAX_OVERHEAD), so that no int64 sum
- * overflows; PAAM_E_UNSUPPORTED for acc != 0; PAAM_E_NOMEM / PAAM_E_CUDA.
+ * overflows; PAAM_E_INVAL for an accelerator index outside 0..PAAM_MAX_ACC-1;
+ * PAAM_E_NOMEM / PAAM_E_CUDA.
  * On error *out is NULL and nothing is leaked.
  */
 int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *view, void *stream,

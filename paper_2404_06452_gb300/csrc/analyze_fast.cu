@@ -543,7 +543,9 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     if (!small || !bigfn) return PAAM_E_INVAL;
     int k = 0;
     const int64_t items = p.K > 0 ? b->n_sys * (int64_t)p.K : b->n_sys;
-    if (p.blocking_mode == 1) { // the safe blocking term needs every segment bound: the int64 kernel only
+    // the safe blocking term needs every segment bound, and several accelerators need
+    // per-accelerator tables: both run the int64 kernel for every system
+    if (p.blocking_mode == 1 || b->acc) {
         const int rc = paam_launch_wide(b, p, R, status, verdict, nullptr, nullptr, items, stream);
         if (n_kernels) *n_kernels = 1;
         return rc;

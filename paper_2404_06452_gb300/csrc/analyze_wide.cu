@@ -15,13 +15,30 @@ namespace {
 
 constexpr int64_t kInf = INT64_MAX;
 
-template <int MAXN>
+// NACC accelerators (rule R1: one server each, analysed on its own); the
+// per-accelerator tables hold, for each chain, its requests to that
+// accelerator only.  delta is the chain's total number of segments.
+template <int MAXN, int NACC>
 struct SysSmem {
-    int64_t T[MAXN], D[MAXN], E[MAXN], S[MAXN], Hs[MAXN], B[MAXN], blk[MAXN], Hseg[MAXN];
-    int64_t Emax[MAXN], M[MAXN], seglo[MAXN], hold[MAXN];
-    int32_t prio[MAXN], eprio[MAXN], delta[MAXN], core[MAXN], exec[MAXN], bucket[MAXN];
+    int64_t T[MAXN], D[MAXN], E[MAXN], Hs[MAXN], B[MAXN];
+    int64_t Emax[MAXN], seglo[MAXN], hold[MAXN];
+    int64_t S[MAXN][NACC], M[MAXN][NACC], blk[MAXN][NACC], Hseg[MAXN][NACC];
+    int32_t prio[MAXN], eprio[MAXN], delta[MAXN], core[MAXN], exec[MAXN];
+    int32_t dA[MAXN][NACC], bucket[MAXN][NACC];
     uint8_t spin[MAXN], status[MAXN], order[MAXN];
 };
+
+// accelerator of segment q (indices were checked against PAAM_MAX_ACC at load)
+template <int NACC>
+__device__ __forceinline__ int acc_of(const BatchDev &b, int64_t q)
+{
+    if constexpr (NACC == 1) {
+        return 0;
+    } else {
+        const int u = b.acc ? b.acc[q] : 0;
+        return u < NACC ? u : NACC - 1;
+    }
+}
 
 template <int G>
 __device__ __forceinline__ unsigned group_mask()
@@ -53,9 +70,9 @@ __device__ __forceinline__ int group_or(int v, unsigned mask)
 // Lemma 1 (Eq. 2): arrivals in a window t >= 0 are at most ceil(t / T) + 1
 __device__ __forceinline__ int64_t arrivals(int64_t t, int64_t T) { return (t + T - 1) / T + 1; }
 
-template <int G, int MAXN>
+template <int G, int MAXN, int NACC>
 __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64_t item,
-                               SysSmem<MAXN> &s, int lane, unsigned gmask, int64_t *__restrict__ R_out,
+                               SysSmem<MAXN, NACC> &s, int lane, unsigned gmask, int64_t *__restrict__ R_out,
                                uint8_t *__restrict__ st_out, uint8_t *__restrict__ verdict)
 {
     int64_t sys;
@@ -93,22 +110,32 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
         s.core[c] = b.exec_core[x0 + x];
         s.eprio[c] = xprio ? xprio[x0 + x] : 0;
         const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
-        int64_t E = 0, Emax = 0, S = 0, M = 0;
+        int64_t E = 0, Emax = 0;
         for (int64_t cb = cb0; cb < cb1; ++cb) {
             const int64_t e = b.E[cb];
             E += e;
             Emax = e > Emax ? e : Emax;
         }
+        int64_t S[NACC], M[NACC];
+        int32_t dl[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) S[a] = M[a] = dl[a] = 0;
         const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
         for (int64_t q = q0; q < q1; ++q) {
             const int64_t a = b.A[q] + kappa2;
-            S += a;
-            M = a > M ? a : M;
+            const int u = acc_of<NACC>(b, q);
+            S[u] += a;
+            M[u] = a > M[u] ? a : M[u];
+            dl[u] += 1;
         }
         s.E[c] = E;
         s.Emax[c] = Emax;
-        s.S[c] = S;
-        s.M[c] = M;
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+            s.S[c][a] = S[a];
+            s.M[c][a] = M[a];
+            s.dA[c][a] = dl[a];
+        }
         s.delta[c] = (int32_t)(q1 - q0);
         s.seglo[c] = q0;
     }
@@ -128,8 +155,12 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     }
 
     // ---- executor priorities, buckets (R2), blocking terms ----------------
-    int n_users = 0;
-    for (int k = 0; k < n; ++k) n_users += s.delta[k] > 0;
+    int n_users[NACC];
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) {
+        n_users[a] = 0;
+        for (int k = 0; k < n; ++k) n_users[a] += s.dA[k][a] > 0;
+    }
     for (int c = lane; c < n; c += G) {
         if (!xprio) { // criticality-as-priority: highest chain priority on the executor
             int32_t best = INT32_MIN;
@@ -137,25 +168,35 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
                 if (s.exec[k] == s.exec[c] && s.prio[k] > best) best = s.prio[k];
             s.eprio[c] = best;
         }
-        // bucket of c: rank among accelerator users, split into n evenly sized groups
-        int32_t bucket = -1;
-        if (s.delta[c] > 0) {
-            int r = 0;
-            for (int k = 0; k < n; ++k) r += (s.delta[k] > 0 && s.prio[k] > s.prio[c]);
-            bucket = (int32_t)((int64_t)r * p.n_buckets / n_users);
+        // bucket of c at each accelerator: rank among that accelerator's users,
+        // split into n evenly sized groups
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+            int32_t bucket = -1;
+            if (s.dA[c][a] > 0) {
+                int r = 0;
+                for (int k = 0; k < n; ++k) r += (s.dA[k][a] > 0 && s.prio[k] > s.prio[c]);
+                bucket = (int32_t)((int64_t)r * p.n_buckets / n_users[a]);
+            }
+            s.bucket[c][a] = bucket;
         }
-        s.bucket[c] = bucket;
     }
     __syncwarp(gmask);
     for (int c = lane; c < n; c += G) {
-        const int32_t bucket_c = s.bucket[c];
-        int64_t blk = 0, B = 0;
+        int64_t blk[NACC], B = 0;
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) blk[a] = 0;
         for (int l = 0; l < n; ++l) {
             if (s.prio[l] >= s.prio[c]) continue;
             if (s.exec[l] == s.exec[c] && s.Emax[l] > B) B = s.Emax[l]; // Lemma 4
-            if (bucket_c >= 0 && s.bucket[l] == bucket_c && s.M[l] > blk) blk = s.M[l]; // R2-R3
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) { // R2-R3, at each accelerator
+                const int32_t bucket_c = s.bucket[c][a];
+                if (bucket_c >= 0 && s.bucket[l][a] == bucket_c && s.M[l][a] > blk[a]) blk[a] = s.M[l][a];
+            }
         }
-        s.blk[c] = blk;
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) s.blk[c][a] = blk[a];
         s.B[c] = B;
         // position in an order that puts every needed H*_h first:
         // executor priority, then chain priority, both descending
@@ -172,37 +213,51 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     // of (Lemma 2 bound + eps), infinite when a segment has no bound.
     const bool safe = p.blocking_mode == 1;
     for (int c = lane; c < n; c += G) {
-        int64_t Hseg = 0, hold = 0;
-        const int64_t Dc = s.D[c], blk = s.blk[c];
+        int64_t Hseg[NACC], hold = 0;
+        bool any_inf = false; // some segment of the chain has no bound
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) Hseg[a] = 0;
+        const int64_t Dc = s.D[c];
         const int32_t pc = s.prio[c];
         const int64_t g = c0 + c;
         const int64_t cb1 = b.chain_cb_off[g + 1];
-        for (int64_t cb = b.chain_cb_off[g]; cb < cb1 && Hseg != kInf; ++cb) {
+        // with one accelerator nothing after an unbounded segment matters
+        for (int64_t cb = b.chain_cb_off[g]; cb < cb1 && !(NACC == 1 && any_inf); ++cb) {
             int64_t t = b.E[cb];
             const int64_t q1 = b.cb_seg_off[cb + 1];
-            for (int64_t q = b.cb_seg_off[cb]; q < q1 && Hseg != kInf; ++q) {
-                const int64_t a = b.A[q] + kappa2;
+            for (int64_t q = b.cb_seg_off[cb]; q < q1; ++q) {
+                const int u = acc_of<NACC>(b, q);
+                if (Hseg[u] == kInf) { // this accelerator's sum is already unbounded
+                    any_inf = true;
+                    continue;
+                }
+                const int64_t a = b.A[q] + kappa2, blk = s.blk[c][u];
                 int64_t h = a + blk;
+                bool inf = false;
                 for (;;) {
                     if (h > Dc) {
-                        Hseg = kInf;
+                        inf = true;
                         break;
                     }
                     int64_t nh = a + blk;
-                    for (int k = 0; k < n; ++k)
-                        if (s.delta[k] > 0 && s.prio[k] > pc) nh += arrivals(h, s.T[k]) * s.S[k];
+                    for (int k = 0; k < n; ++k) // hps at this segment's accelerator
+                        if (s.dA[k][u] > 0 && s.prio[k] > pc) nh += arrivals(h, s.T[k]) * s.S[k][u];
                     if (nh == h) break; // each step raises some ceil(h/T_k): at most n*(D/Tmin+1) steps
                     h = nh;
                 }
-                if (Hseg != kInf) {
-                    Hseg += h;
+                if (inf) {
+                    Hseg[u] = kInf;
+                    any_inf = true;
+                } else {
+                    Hseg[u] += h;
                     t += h + eps;
                 }
             }
             if (safe && t > hold) hold = t;
         }
-        s.Hseg[c] = Hseg;
-        s.hold[c] = Hseg == kInf ? kInf : hold;
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) s.Hseg[c][a] = Hseg[a];
+        s.hold[c] = any_inf ? kInf : hold;
     }
     __syncwarp(gmask);
     if (safe) { // B_c: the longest hold of a lower-priority chain on the same executor
@@ -234,16 +289,23 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
         if (!dep_bad && s.B[c] == kInf) { // unbounded safe blocking
             st = PAAM_ST_OVERRUN;
         } else if (!dep_bad) {
-            const int64_t Dc = s.D[c], Bc = s.B[c], Ec = s.E[c], Sc = s.S[c], Hseg = s.Hseg[c];
+            const int64_t Dc = s.D[c], Bc = s.B[c], Ec = s.E[c];
             const int64_t dc = s.delta[c];
-            const int64_t own = Sc + dc * s.blk[c];
             const int64_t deps = dc * eps;
-            // start: B + E + H* with the interference part of Eq. 4 empty
-            int64_t Rc = Bc + Ec + (dc > 0 ? (Hseg < own ? Hseg : own) + deps : 0);
+            int64_t own[NACC], h0 = 0;
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) {
+                own[a] = s.S[c][a] + (int64_t)s.dA[c][a] * s.blk[c][a];
+                if (s.dA[c][a] > 0) h0 += s.Hseg[c][a] < own[a] ? s.Hseg[c][a] : own[a];
+            }
+            // start: B + E + H* with the interference parts of Eq. 4 empty
+            int64_t Rc = Bc + Ec + (dc > 0 ? h0 + deps : 0);
             st = PAAM_ST_OVERRUN;
             for (;;) {
                 if (Rc > Dc) break;
-                int64_t cpu = 0, acc = 0;
+                int64_t cpu = 0, acc[NACC];
+#pragma unroll
+                for (int a = 0; a < NACC; ++a) acc[a] = 0;
                 for (int h = lane; h < n; h += G) {
                     if (h == c) continue;
                     const int64_t m = arrivals(Rc, s.T[h]);
@@ -252,15 +314,22 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
                     } else if (s.core[h] == cc && s.eprio[h] > ep) {          // hpp(c)
                         cpu += m * (s.E[h] + (s.spin[h] ? s.Hs[h] : (int64_t)s.delta[h] * eps));
                     }
-                    if (s.delta[h] > 0 && s.prio[h] > pc) acc += m * s.S[h]; // Eq. 4
+                    if (s.prio[h] > pc)
+#pragma unroll
+                        for (int a = 0; a < NACC; ++a)
+                            if (s.dA[h][a] > 0) acc[a] += m * s.S[h][a]; // Eq. 4 at accelerator a
                 }
                 cpu = group_sum<G>(cpu, gmask);
-                acc = group_sum<G>(acc, gmask);
                 int64_t hs = 0;
-                if (dc > 0) {
-                    const int64_t hch = own + acc;
-                    hs = (Hseg < hch ? Hseg : hch) + deps; // Eq. 1 with min(Eq. 3, Eq. 4)
+#pragma unroll
+                for (int a = 0; a < NACC; ++a) {
+                    acc[a] = group_sum<G>(acc[a], gmask);
+                    if (s.dA[c][a] > 0) { // Eq. 1 with min(Eq. 3, Eq. 4), summed over accelerators (R1)
+                        const int64_t hch = own[a] + acc[a];
+                        hs += s.Hseg[c][a] < hch ? s.Hseg[c][a] : hch;
+                    }
                 }
+                if (dc > 0) hs += deps;
                 const int64_t Rn = Bc + Ec + hs + cpu;
                 if (Rn == Rc) {
                     st = PAAM_ST_SCHED;
@@ -297,7 +366,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
 
 // Systems are either all of the batch (list == nullptr) or the list
 // list[0 .. *count).
-template <int G, int MAXN>
+template <int G, int MAXN, int NACC>
 __global__ void __launch_bounds__(256) analyze_wide_kernel(BatchDev b, AnalysisParams p, int64_t *R,
                                                            uint8_t *st, uint8_t *verdict,
                                                            const int32_t *list, const int32_t *count)
@@ -306,26 +375,28 @@ __global__ void __launch_bounds__(256) analyze_wide_kernel(BatchDev b, AnalysisP
     const int groups = blockDim.x / G;
     const int grp = threadIdx.x / G;
     const int lane = threadIdx.x % G;
-    SysSmem<MAXN> &s = reinterpret_cast<SysSmem<MAXN> *>(smem_raw)[grp];
+    SysSmem<MAXN, NACC> &s = reinterpret_cast<SysSmem<MAXN, NACC> *>(smem_raw)[grp];
     const unsigned gmask = group_mask<G>();
     const int64_t n = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n; i += (int64_t)gridDim.x * groups) {
         const int64_t item = list ? (int64_t)list[i] : i;
-        analyze_system<G, MAXN>(b, p, item, s, lane, gmask, R, st, verdict);
+        analyze_system<G, MAXN, NACC>(b, p, item, s, lane, gmask, R, st, verdict);
     }
 }
 
 } // namespace
 
-int paam_launch_wide(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st,
-                     uint8_t *verdict, const int32_t *list, const int32_t *count, int64_t max_items,
-                     cudaStream_t stream)
+namespace {
+
+template <int NACC>
+int launch_wide_n(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                  const int32_t *list, const int32_t *count, int64_t max_items, cudaStream_t stream)
 {
     constexpr int G = 32, MAXN = 64;
     const int threads = 256;
     const int groups = threads / G;
-    const size_t smem = sizeof(SysSmem<MAXN>) * groups;
-    auto kern = analyze_wide_kernel<G, MAXN>;
+    const size_t smem = sizeof(SysSmem<MAXN, NACC>) * groups;
+    auto kern = analyze_wide_kernel<G, MAXN, NACC>;
     PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -337,4 +408,14 @@ int paam_launch_wide(const paam_batch *bt, const AnalysisParams &p, int64_t *R, 
     kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, list, count);
     PAAM_CUDA_TRY(cudaGetLastError());
     return PAAM_OK;
+}
+
+} // namespace
+
+int paam_launch_wide(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st,
+                     uint8_t *verdict, const int32_t *list, const int32_t *count, int64_t max_items,
+                     cudaStream_t stream)
+{
+    if (bt->acc) return launch_wide_n<PAAM_MAX_ACC>(bt, p, R, st, verdict, list, count, max_items, stream);
+    return launch_wide_n<1>(bt, p, R, st, verdict, list, count, max_items, stream);
 }

@@ -109,7 +109,7 @@ __global__ void validate_kernel(ValidateArgs a)
 {
     const BatchDev &b = a.b;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long lmax[ST_COUNT] = {0, 0, 0, 0, 0};
+    unsigned long long lmax[ST_COUNT] = {};
     int32_t nmax = 0, xmax = 0;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < b.n_sys; s += stride) {
         if (s == 0) { // global sentinels
@@ -150,7 +150,6 @@ __global__ void validate_kernel(ValidateArgs a)
         // chains, callbacks, segments; magnitudes for the range check
         double Dmax = 0.0, Tmin = 1e300, Cmax = 0.0, Base = 0.0, Emax_sys = 0.0, Mmax_sys = 0.0;
         const double OV = (double)PAAM_MAX_OVERHEAD;
-        bool unsupported = false;
         for (int64_t c = c0; c < c1 && !bad; ++c) {
             const int64_t T = b.T[c], D = b.D[c];
             if (T <= 0 || T > PAAM_MAX_TIME || D <= 0 || D > T || b.spin[c] > 1 || b.exec[c] < 0 ||
@@ -183,7 +182,14 @@ __global__ void validate_kernel(ValidateArgs a)
                         bad = true;
                         break;
                     }
-                    if (a.acc && a.acc[q] != 0) unsupported = true;
+                    if (a.acc) { // one server per accelerator (R1), up to PAAM_MAX_ACC of them
+                        const int32_t u = a.acc[q];
+                        if (u < 0 || u >= PAAM_MAX_ACC) {
+                            bad = true;
+                            break;
+                        }
+                        lmax[ST_ACCMAX] = max(lmax[ST_ACCMAX], (unsigned long long)u);
+                    }
                     const double as = (double)av + 2.0 * OV;
                     Sc += as;
                     dc += 1.0;
@@ -207,10 +213,6 @@ __global__ void validate_kernel(ValidateArgs a)
         }
         if (bad) {
             fail(a.err, PAAM_E_INVAL, s);
-            continue;
-        }
-        if (unsupported) {
-            fail(a.err, PAAM_E_UNSUPPORTED, s);
             continue;
         }
         if (n > 0) {
@@ -381,6 +383,7 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
     }
     b->max_chains = h_err[2];
     b->max_exec = h_err[3];
+    b->acc = b->stats[ST_ACCMAX] > 0 ? acc_dev : nullptr; // kept only when a second accelerator is used
     *out = b;
     return PAAM_OK;
 }

@@ -74,7 +74,7 @@ __device__ __forceinline__ bool cand_pruned(const AnalysisParams &p, int64_t sys
 
 // Batch-wide maxima recorded by validation; they decide which kernels an
 // analysis needs (the 32-bit fast path covers every system when they fit).
-enum { ST_TMAX = 0, ST_DMAX, ST_ECMAX, ST_SCMAX, ST_DELTAMAX, ST_COUNT };
+enum { ST_TMAX = 0, ST_DMAX, ST_ECMAX, ST_SCMAX, ST_DELTAMAX, ST_ACCMAX, ST_COUNT };
 
 struct paam_ctx {
     int device;
@@ -93,6 +93,7 @@ struct paam_batch {
     int64_t *sys_chain_off, *chain_cb_off, *cb_seg_off, *T, *D, *E, *A, *sys_exec_off;
     int32_t *prio, *exec, *exec_core, *exec_prio; // exec_prio NULL => derived
     uint8_t *spin;
+    int32_t *acc; // accelerator of each segment; NULL when every segment uses accelerator 0
     int32_t max_chains; // largest chain count of any system
     int32_t max_exec;
     unsigned long long stats[ST_COUNT];
@@ -130,6 +131,7 @@ struct BatchDev {
     const int32_t *__restrict__ exec_core;
     const int32_t *__restrict__ exec_prio;
     const uint8_t *__restrict__ spin;
+    const int32_t *__restrict__ acc; // NULL: one accelerator
 };
 
 inline BatchDev batch_dev(const paam_batch *b)
@@ -149,6 +151,7 @@ inline BatchDev batch_dev(const paam_batch *b)
     d.exec_core = b->exec_core;
     d.exec_prio = b->exec_prio;
     d.spin = b->spin;
+    d.acc = b->acc;
     return d;
 }
 

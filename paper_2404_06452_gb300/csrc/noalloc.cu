@@ -125,6 +125,7 @@ extern "C" int paam_rta_analyze_noalloc(const paam_systems_view *v, const paam_a
     b.max_chains = herr[2];
     b.max_exec = herr[3];
     for (int i = 0; i < ST_COUNT; ++i) b.stats[i] = hstats[i];
+    b.acc = hstats[ST_ACCMAX] > 0 ? (int32_t *)v->acc : nullptr;
 
     AnalysisParams p = {};
     p.n_buckets = o->n_buckets;

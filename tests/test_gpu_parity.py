@@ -135,8 +135,8 @@ def test_invalid_inputs_rejected():
     _expect_error(mod(lambda d: d["chains"][1].update(exec=3)), -1)    # executor out of range
     _expect_error(mod(lambda d: d["chains"][0].update(cbs=[(-1, [])])), -1)  # negative WCET
     sy = mod(lambda d: None)
-    sy.acc = np.ones_like(sy.acc)
-    _expect_error(sy, -6)                                              # second accelerator
+    sy.acc = np.full_like(sy.acc, 4)
+    _expect_error(sy, -1)                                              # accelerator index past PAAM_MAX_ACC
     big = mod(lambda d: d["chains"][0].update(T=2**40, D=2**40, cbs=[(2**40, [2**40] * 8)]))
     _expect_error(big, -2)                                             # int64 range
     _expect_error(mod(lambda d: None), -2, eps=2**33)                  # eps above the cap
