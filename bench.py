@@ -113,9 +113,16 @@ class ClockSampler:
 
 
 def cpu_model() -> str:
-    """The host CPU's model name (Linux /proc/cpuinfo; architecture otherwise)."""
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; architecture otherwise)."""
     import platform
 
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip().lower() == "model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
@@ -485,6 +492,28 @@ def kappa_bench(pkg, ctx, iters, sy=None):
     return out
 
 
+def accelerators_bench(pkg, ctx, n_sys, units=3):
+    """The workload with its accelerator segments spread over `units` units by
+    worst-fit decreasing (one server per unit, rule R1): analysed by the
+    exact int64 kernel with per-accelerator tables."""
+    import torch
+
+    import paam_gen
+
+    base = paam_gen.generate(WORKLOAD, n_sys=n_sys)
+    out = {"systems": n_sys, "units": units}
+    for k, sy in (("1", base), (str(units), paam_gen.assign_accelerators(base, units))):
+        b = pkg.paam_rta_load_systems(ctx, sy)
+        pkg.paam_rta_autotune(ctx, b, pkg.analysis_opts())
+        R, st, v = pkg.analyze(ctx, b)
+        t, _ = _timed(lambda: pkg.analyze(ctx, b), 5)
+        torch.cuda.synchronize()
+        out[k] = {"ms": t * 1e3, "chains_per_s": sy.n_chain / t,
+                  "sched_chains": float((st == 0).float().mean().item())}
+        b.free()
+    return out
+
+
 def infer_bench(pkg, n_sys, steps, warmup):
     """The network's ranking alone (features, 4 layers with the fused score,
     top-k) on the search workload, random weights: what a step of guided search
@@ -713,9 +742,10 @@ def run_ours(args):
             search["cpu_baseline"] = search_cpu_baseline(min(args.search_sys, 2000))
     if rank == 0 and world == 1 and not args.no_surrogate:
         surrogate = surrogate_bench(pkg, ctx, args.train_sys, args.search_sys, args.top_k)
-    e2e_chains = kappa = None
+    e2e_chains = kappa = accel = None
     if rank == 0 and world == 1 and not args.no_search:
         e2e_chains = end_to_end_bench(pkg, ctx, min(n_sys, 1_000_000))
+        accel = accelerators_bench(pkg, ctx, min(n_sys, 1_000_000))
         if args.kappa_iters > 0:
             kappa = kappa_bench(pkg, ctx, args.kappa_iters, sy.subset(np.arange(min(sy.n_sys, 200_000))))
 
@@ -731,7 +761,7 @@ def run_ours(args):
                        "autotune_ms": [round(t, 4) for t in cfg_times]},
             "systems_per_s": total_sys * args.steps / (elapsed_ms / 1e3),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clocks, "search": search, "surrogate": surrogate, "end_to_end": e2e_chains, "kappa": kappa,
+            "clocks": clocks, "search": search, "surrogate": surrogate, "end_to_end": e2e_chains, "kappa": kappa, "accelerators": accel,
         }
         print(json.dumps(line), flush=True)
     batch.free()
