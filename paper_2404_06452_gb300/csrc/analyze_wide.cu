@@ -26,6 +26,10 @@ struct SysSmem {
     int32_t prio[MAXN], eprio[MAXN], delta[MAXN], core[MAXN], exec[MAXN];
     int32_t dA[MAXN][NACC], bucket[MAXN][NACC];
     uint8_t spin[MAXN], status[MAXN], order[MAXN];
+    // ceil(t / T) by multiply and shift when the system's periods and deadlines
+    // are below 2^30 (every window the loops test is at most a deadline)
+    uint32_t tm1[MAXN], mg[MAXN];
+    uint8_t sh[MAXN];
 };
 
 // accelerator of segment q (indices were checked against PAAM_MAX_ACC at load)
@@ -60,6 +64,14 @@ __device__ __forceinline__ int64_t group_sum(int64_t v, unsigned mask)
 }
 
 template <int G>
+__device__ __forceinline__ int group_and(int v, unsigned mask)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v &= __shfl_xor_sync(mask, v, off);
+    return v;
+}
+
+template <int G>
 __device__ __forceinline__ int group_or(int v, unsigned mask)
 {
 #pragma unroll
@@ -69,6 +81,16 @@ __device__ __forceinline__ int group_or(int v, unsigned mask)
 
 // Lemma 1 (Eq. 2): arrivals in a window t >= 0 are at most ceil(t / T) + 1
 __device__ __forceinline__ int64_t arrivals(int64_t t, int64_t T) { return (t + T - 1) / T + 1; }
+
+// The same for 0 <= t <= D < 2^30 and T < 2^30: t + T - 1 < 2^31, and with
+// m = ceil(2^(31 + l) / T), l = ceil(log2 T), floor(x / T) = (x m) >> (31 + l)
+// for every x < 2^31 (Granlund and Montgomery 1994, Theorem 4.2 with N = 31).
+template <int MAXN, int NACC>
+__device__ __forceinline__ int64_t arrivals_of(const SysSmem<MAXN, NACC> &s, int k, int64_t t, bool fast)
+{
+    if (fast) return (int64_t)((((uint64_t)((uint32_t)t + s.tm1[k])) * s.mg[k]) >> s.sh[k]) + 1;
+    return arrivals(t, s.T[k]);
+}
 
 template <int G, int MAXN, int NACC>
 __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64_t item,
@@ -92,10 +114,20 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     // ---- chain aggregates (Sec. II-C; A* = A + 2 kappa) -------------------
     int rank_bad = 0;
     unsigned long long rbits = 0;
+    int small = 1; // every period and deadline of the system below 2^30
     for (int c = lane; c < n; c += G) {
         const int64_t g = c0 + c;
         s.T[c] = b.T[g];
         s.D[c] = b.D[g];
+        if (b.T[g] < (1ll << 30) && b.D[g] < (1ll << 30)) {
+            const uint32_t Tu = (uint32_t)b.T[g];
+            const uint32_t l = Tu > 1 ? 32u - (uint32_t)__clz(Tu - 1u) : 0u;
+            s.mg[c] = (uint32_t)(((1ull << (31 + l)) + Tu - 1u) / Tu);
+            s.sh[c] = (uint8_t)(31 + l);
+            s.tm1[c] = Tu - 1u;
+        } else {
+            small = 0;
+        }
         if (rank_row) { // candidate priority order: rank 0 is the highest priority
             const int r = rank_row[c];
             if (r < 0 || r >= n) rank_bad = 1;
@@ -140,6 +172,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
         s.seglo[c] = q0;
     }
     __syncwarp(gmask);
+    const bool fast = group_and<G>(small, gmask) != 0;
     if (rank_row) { // a candidate must be a permutation of 0..n-1
         rank_bad = group_or<G>(rank_bad, gmask);
         for (int off = G / 2; off > 0; off >>= 1) rbits |= __shfl_xor_sync(gmask, rbits, off);
@@ -241,7 +274,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
                     }
                     int64_t nh = a + blk;
                     for (int k = 0; k < n; ++k) // hps at this segment's accelerator
-                        if (s.dA[k][u] > 0 && s.prio[k] > pc) nh += arrivals(h, s.T[k]) * s.S[k][u];
+                        if (s.dA[k][u] > 0 && s.prio[k] > pc) nh += arrivals_of(s, k, h, fast) * s.S[k][u];
                     if (nh == h) break; // each step raises some ceil(h/T_k): at most n*(D/Tmin+1) steps
                     h = nh;
                 }
@@ -308,7 +341,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
                 for (int a = 0; a < NACC; ++a) acc[a] = 0;
                 for (int h = lane; h < n; h += G) {
                     if (h == c) continue;
-                    const int64_t m = arrivals(Rc, s.T[h]);
+                    const int64_t m = arrivals_of(s, h, Rc, fast);
                     if (s.exec[h] == ec) {
                         if (s.prio[h] > pc) cpu += m * (s.E[h] + s.Hs[h]); // hp(c)
                     } else if (s.core[h] == cc && s.eprio[h] > ep) {          // hpp(c)
