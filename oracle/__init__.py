@@ -181,3 +181,41 @@ def search(sy, ranks: np.ndarray, n_buckets: int = 1, eps: int = 0, kappa: int =
         with ThreadPoolExecutor(len(rs)) as ex:
             list(ex.map(run, rs))
     return dict(cand_ok=cand_ok, first_ok=first_ok)
+
+
+def audsley(sy, nmax: int | None = None, n_buckets: int = 1, eps: int = 0, kappa: int = 0,
+            blocking_mode: int = 0, threads: int = 1):
+    """Audsley-style greedy priority seed, lowest level first (see
+    ``oracle_audsley`` in ``paam_oracle.c``).  Returns ranks [S, nmax] (int16,
+    0 = highest priority, -1 beyond each system's chains)."""
+    lib = _lib("paam_oracle")
+    a = _arrays(sy)
+    S = len(a["sys_chain_off"]) - 1
+    counts = np.diff(a["sys_chain_off"])
+    if nmax is None:
+        nmax = int(counts.max()) if S else 1
+    if S and nmax < int(counts.max()):
+        raise ValueError("nmax below the largest chain count")
+    ranks = np.full((S, nmax), -1, np.int16)
+    nc = len(a["T"])
+    f = lib.oracle_audsley
+    f.restype = None
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 13 + [
+        ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32] + [ctypes.c_void_p] * 3
+
+    def run(r):
+        Rs = np.zeros(nc, np.int64)
+        sts = np.zeros(nc, np.uint8)
+        f(r[0], r[1], _p(a["sys_chain_off"]), _p(a["chain_cb_off"]), _p(a["cb_seg_off"]), _p(a["T"]),
+          _p(a["D"]), _p(a["prio"]), _p(a["exec"]), _p(a["spin"]), _p(a["E"]), _p(a["A"]), _p(a["acc"]),
+          _p(a["sys_exec_off"]), _p(a["exec_core"]), int(n_buckets), int(eps), int(kappa), int(blocking_mode),
+          int(nmax), _p(ranks), _p(Rs), _p(sts))
+
+    rs = _ranges(S, threads)
+    if len(rs) <= 1:
+        for r in rs:
+            run(r)
+    else:
+        with ThreadPoolExecutor(len(rs)) as ex:
+            list(ex.map(run, rs))
+    return ranks

@@ -460,3 +460,65 @@ void oracle_search(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
         }
     }
 }
+
+/*
+ * Audsley-style priority seed (a reading: the paper assigns priorities by
+ * hand, and its admission test of Sec. IV-A is not OPA-compatible because
+ * bucket ranks, blocking and the DEP rule depend on the whole order).
+ *
+ * For each system of n chains, ranks are given from the lowest priority up:
+ * at level l = n-1, n-2, ..., 0 each unassigned chain c is tried in index
+ * order.  The trial order keeps the ranks already given (all below l), puts c
+ * at rank l and the other unassigned chains at ranks 0..l-1 in
+ * deadline-monotonic order (D ascending, ties by index).  The first c that is
+ * schedulable (status SCHED) in the exact analysis of the trial order, with
+ * derived executor priorities, takes rank l.  If none is, the unassigned chain
+ * with the largest D (ties: highest index) takes it, so that a system where
+ * no chain ever passes gets the deadline-monotonic order.  ranks_out[s*nmax + c] is
+ * the rank of chain c (0 = highest), -1 beyond the system's chains.
+ */
+void oracle_audsley(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
+                    const int64_t *chain_cb_off, const int64_t *cb_seg_off, const int64_t *T,
+                    const int64_t *D, const int32_t *prio, const int32_t *exec, const uint8_t *spin,
+                    const int64_t *E, const int64_t *A, const int32_t *acc, const int64_t *sys_exec_off,
+                    const int32_t *exec_core, int32_t n_buckets, int64_t eps, int64_t kappa,
+                    int32_t blocking_mode, int32_t nmax, int16_t *ranks_out, int64_t *R_scratch,
+                    uint8_t *st_scratch)
+{
+    for (int64_t s = lo; s < hi; ++s) {
+        const int64_t c0 = sys_chain_off[s], n = sys_chain_off[s + 1] - c0;
+        int16_t *rank = ranks_out + s * (int64_t)nmax;
+        int16_t *trial = (int16_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int16_t));
+        for (int64_t c = 0; c < nmax; ++c) rank[c] = -1;
+        for (int64_t level = n - 1; level >= 0; --level) {
+            int64_t chosen = -1;
+            for (int64_t c = 0; c < n && chosen < 0; ++c) {
+                if (rank[c] >= 0) continue;
+                for (int64_t k = 0; k < n; ++k) {
+                    if (rank[k] >= 0) {
+                        trial[k] = rank[k];
+                    } else if (k == c) {
+                        trial[k] = (int16_t)level;
+                    } else { /* position among the other unassigned chains, deadline-monotonic */
+                        int64_t pos = 0;
+                        for (int64_t u = 0; u < n; ++u)
+                            if (u != c && u != k && rank[u] < 0 &&
+                                (D[c0 + u] < D[c0 + k] || (D[c0 + u] == D[c0 + k] && u < k)))
+                                pos += 1;
+                        trial[k] = (int16_t)pos;
+                    }
+                }
+                analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A, acc,
+                               sys_exec_off, exec_core, NULL, trial, n_buckets, eps, kappa, blocking_mode,
+                               R_scratch, st_scratch, NULL, NULL, NULL);
+                if (st_scratch[c0 + c] == ST_SCHED) chosen = c;
+            }
+            if (chosen < 0) { /* no chain passes: the largest deadline goes lowest */
+                for (int64_t c = 0; c < n; ++c)
+                    if (rank[c] < 0 && (chosen < 0 || D[c0 + c] >= D[c0 + chosen])) chosen = c;
+            }
+            rank[chosen] = (int16_t)level;
+        }
+        free(trial);
+    }
+}
