@@ -238,19 +238,33 @@ def _timed(fn, reps=1):
     return (time.perf_counter() - t0) / reps, out
 
 
+def search_candidates(pkg, ctx, sy, b, cfg):
+    """The search workload's SEARCH_K candidate orders per system, on the
+    device: slot 0 the Audsley-style seed computed by the library on the GPU,
+    slot 1 deadline-monotonic, slots 2.. seeded random permutations.  Returns
+    (ranks, seconds the seed took)."""
+    import torch
+
+    import paam_gen
+
+    ranks = paam_gen.candidate_ranks(sy, SEARCH_K, paam_gen.CONFIGS[cfg]["seed"] + 7)
+    r = torch.from_numpy(ranks).cuda()
+    pkg.audsley_order(ctx, b, r.shape[2])  # warm-up
+    t, seed = _timed(lambda: pkg.audsley_order(ctx, b, r.shape[2]))
+    r[:, 0, :] = seed
+    return r, t
+
+
 def search_bench(pkg, ctx, n_sys):
     """Exhaustive and early-exit exact search on the specified search workload
     (cfg4) and on its sparse-executor variant (cfg4s)."""
-    import torch
-
     import paam_gen
 
     out = {}
     for cfg in ("cfg4", "cfg4s"):
         sy = paam_gen.generate(cfg, n_sys=n_sys)
-        ranks = paam_gen.candidate_ranks(sy, SEARCH_K, paam_gen.CONFIGS[cfg]["seed"] + 7)
         b = pkg.paam_rta_load_systems(ctx, sy)
-        r = torch.from_numpy(ranks).cuda()
+        r, t_seed = search_candidates(pkg, ctx, sy, b, cfg)
         pkg.search(ctx, b, r)  # warm-up
         t_x, (first, cand) = _timed(lambda: pkg.search(ctx, b, r), 3)
         t_e, (first_e, _) = _timed(lambda: pkg.search(ctx, b, r, stop_at_first=True, want_cand_ok=False), 3)
@@ -263,6 +277,9 @@ def search_bench(pkg, ctx, n_sys):
             "candidate_analyses_per_s": sy.n_sys * SEARCH_K / t_x,
             "systems_with_schedulable_order": float((first.cpu().numpy() >= 0).mean()),
             "schedulable_candidates": float(cand_np.mean()),
+            "audsley_seed_ms": t_seed * 1e3,
+            "audsley_seed_admitted": float(cand_np[:, 0].mean()),
+            "deadline_monotonic_admitted": float(cand_np[:, 1].mean()),
         }
         b.free()
     return out
@@ -338,9 +355,8 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
     # the search workload: SEARCH_K candidate orders per system
     K = SEARCH_K
     sy = paam_gen.generate("cfg4s", n_sys=n_search)
-    ranks = paam_gen.candidate_ranks(sy, K, paam_gen.CONFIGS["cfg4s"]["seed"] + 7)
     b = pkg.paam_rta_load_systems(ctx, sy)
-    r = torch.from_numpy(ranks).cuda()
+    r, _ = search_candidates(pkg, ctx, sy, b, "cfg4s")
     opts = pkg.analysis_opts()
     pkg.search(ctx, b, r)
     t_ex, (first_x, cand_x) = _timed(lambda: pkg.search(ctx, b, r), 3)
@@ -550,6 +566,7 @@ def search_cpu_baseline(n_sys):
     sy = paam_gen.generate("cfg4s", n_sys=n_sys)
     ranks = paam_gen.candidate_ranks(sy, SEARCH_K, paam_gen.CONFIGS["cfg4s"]["seed"] + 7)
     cores = os.cpu_count() or 1
+    ranks[:, 0, :] = oracle.audsley(sy, nmax=ranks.shape[2], threads=cores)  # slot 0 as on the GPU, untimed
     t0 = time.perf_counter()
     oracle.search(sy, ranks, threads=cores)
     dt = time.perf_counter() - t0

@@ -228,6 +228,42 @@ int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *batch, const paam_a
                             int32_t stop_at_first, uint8_t *cand_ok, int32_t *first_ok, void *stream);
 
 /*
+ * Audsley-style priority seed: a candidate order for the search, built from
+ * the lowest priority level up with the exact analysis (Theorem 1) as the
+ * test.  The paper assigns priorities by hand; this greedy is a reading of
+ * Audsley's lowest-level-first assignment for a test that is not
+ * OPA-compatible (bucket ranks, blocking and the DEP rule depend on the whole
+ * order), so it is a seed for the search, not an optimum.
+ *
+ * For a system of n chains, at level l = n-1 down to 0 each unassigned chain
+ * c is tried in index order: the chains already placed keep their ranks (all
+ * below l), c takes rank l and the other unassigned chains ranks 0..l-1 in
+ * deadline-monotonic order (D ascending, ties by index).  The first c that is
+ * schedulable in the exact analysis of that order (executor priorities
+ * derived from it) takes level l; if none is, the unassigned chain with the
+ * largest D (ties: highest index) does.
+ *
+ *   opts                   as for the analysis (n_buckets, eps, kappa,
+ *                          blocking_mode); the batch's own priorities are
+ *                          not used.
+ *   nmax                   row length of ranks_out, >= the batch's largest
+ *                          chain count.
+ *   ranks_out[n_sys][nmax] device int16: rank of chain c of system s (0 =
+ *                          highest priority), -1 beyond the system's chains;
+ *                          a row is a candidate row of
+ *                          paam_rta_search_priorities.
+ *
+ * Every trial of every system at one level is analysed in one launch of the
+ * exact int64 kernel, which stops each trial once chain c is done.  Scratch
+ * is taken from the stream's pool (at most about 512 MB; larger batches run
+ * in system chunks).  The call synchronises `stream`.  Errors: PAAM_E_INVAL
+ * (bad sizes or options), PAAM_E_RANGE (eps/kappa above the cap),
+ * PAAM_E_STATE (a batch of another context), PAAM_E_NOMEM, PAAM_E_CUDA.
+ */
+int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *batch, const paam_analysis_opts *opts, int32_t nmax,
+                           int16_t *ranks_out, void *stream);
+
+/*
  * Surrogate ranking model (not in the paper: it serves the priority search).
  * A multilayer perceptron 1024 -> 256 -> 256 -> 256 -> 64 (GELU hidden
  * layers, bf16 weights for bf16 tensor-core GEMMs with fp32 accumulation,

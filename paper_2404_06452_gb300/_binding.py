@@ -114,6 +114,8 @@ def lib():
             "paam_rta_search_priorities": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
                                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                           _c_void_p, _c_void_p, _c_void_p]),
+            "paam_rta_audsley_order": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), ctypes.c_int32,
+                                                      _c_void_p, _c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -132,7 +134,7 @@ def exported_symbols() -> list:
             "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
             "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
             "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_rta_end_to_end",
-            "paam_measure_preemption"]
+            "paam_measure_preemption", "paam_rta_audsley_order"]
 
 
 def launch_count() -> int:
@@ -311,6 +313,14 @@ def paam_rta_search_priorities(ctx: Context, batch: Batch, opts: AnalysisOpts, r
     _check(lib().paam_rta_search_priorities(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(ranks), int(K),
                                             int(nmax), 1 if stop_at_first else 0, _ptr(cand_ok), _ptr(first_ok),
                                             _stream_ptr(stream)), "paam_rta_search_priorities")
+
+
+def paam_rta_audsley_order(ctx: Context, batch: Batch, opts: AnalysisOpts, ranks_out, stream=None):
+    """Audsley-style seed order of every system into ``ranks_out`` ([S, nmax]
+    int16 device tensor; rank 0 highest, -1 beyond each system's chains)."""
+    nmax = ranks_out.shape[1]
+    _check(lib().paam_rta_audsley_order(ctx.handle, batch.handle, ctypes.byref(opts), int(nmax), _ptr(ranks_out),
+                                        _stream_ptr(stream)), "paam_rta_audsley_order")
 
 
 def paam_tc_gemm_bf16(A, B, C, err, stream=None):

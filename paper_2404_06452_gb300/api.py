@@ -56,3 +56,15 @@ def search(ctx: B.Context, batch: B.Batch, ranks, n_buckets: int = 1, eps: int =
                                  stop_at_first,
                                  cand_ok, first_ok, stream=stream)
     return first_ok, cand_ok
+
+
+def audsley_order(ctx: B.Context, batch: B.Batch, nmax: int, n_buckets: int = 1, eps: int = 0, kappa: int = 0,
+                  blocking_mode: int = 0, stream=None):
+    """Run ``paam_rta_audsley_order``; returns the seed ranks as a torch
+    tensor [S, nmax] (int16, rank 0 highest, -1 beyond each system's chains)."""
+    import torch
+
+    ranks = torch.empty((batch.n_sys, nmax), dtype=torch.int16, device=torch.device("cuda", ctx.device))
+    B.paam_rta_audsley_order(ctx, batch, B.analysis_opts(n_buckets, eps, kappa, blocking_mode), ranks,
+                             stream=stream)
+    return ranks

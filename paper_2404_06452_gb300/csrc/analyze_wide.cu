@@ -109,6 +109,9 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     const int64_t x0 = b.sys_exec_off[sys];
     const int64_t kappa2 = 2 * p.kappa, eps = p.eps;
     const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.Kc + cand_of(p, sys, cand)) * p.nmax : nullptr;
+    // target mode: the candidate's verdict is the status of this one chain
+    const int tgt = (p.K > 0 && p.target) ? (int)p.target[sys * p.Kc + cand_of(p, sys, cand)] : -1;
+    if (p.K > 0 && p.target && (tgt < 0 || tgt >= n)) return;
     const int32_t *xprio = p.K > 0 ? nullptr : b.exec_prio; // candidates: criticality-as-priority
 
     // ---- chain aggregates (Sec. II-C; A* = A + 2 kappa) -------------------
@@ -382,6 +385,12 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
             R_out[c0 + c] = R;
             st_out[c0 + c] = st;
         }
+        if (c == tgt) break; // chains after the target cannot change its result
+    }
+    if (tgt >= 0) {
+        if (lane == 0) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = (uint8_t)(s.status[tgt] == PAAM_ST_SCHED);
+        __syncwarp(gmask);
+        return;
     }
     int ok = 1;
     for (int c = lane; c < n; c += G) ok &= s.status[c] == PAAM_ST_SCHED;
@@ -421,11 +430,10 @@ __global__ void __launch_bounds__(256) analyze_wide_kernel(BatchDev b, AnalysisP
 
 namespace {
 
-template <int NACC>
-int launch_wide_n(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+template <int G, int MAXN, int NACC>
+int launch_wide_g(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                   const int32_t *list, const int32_t *count, int64_t max_items, cudaStream_t stream)
 {
-    constexpr int G = 32, MAXN = 64;
     const int threads = 256;
     const int groups = threads / G;
     const size_t smem = sizeof(SysSmem<MAXN, NACC>) * groups;
@@ -441,6 +449,17 @@ int launch_wide_n(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uin
     kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, list, count);
     PAAM_CUDA_TRY(cudaGetLastError());
     return PAAM_OK;
+}
+
+// batches of at most 16 chains per system: 16 lanes and 16-chain tables, so
+// that no lane idles in the loops over chains
+template <int NACC>
+int launch_wide_n(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                  const int32_t *list, const int32_t *count, int64_t max_items, cudaStream_t stream)
+{
+    if (bt->max_chains <= 16)
+        return launch_wide_g<16, 16, NACC>(bt, p, R, st, verdict, list, count, max_items, stream);
+    return launch_wide_g<32, 64, NACC>(bt, p, R, st, verdict, list, count, max_items, stream);
 }
 
 } // namespace

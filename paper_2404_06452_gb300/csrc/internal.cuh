@@ -45,6 +45,12 @@ struct AnalysisParams {
     uint8_t *cand_ok;
     int32_t *first_ok;
     int32_t *err;
+    // Target mode (exact int64 kernel only; the Audsley-style seed): with
+    // target set, candidate (system, c) is decided by one chain,
+    // target[system * Kc + c] (-1: skip the item): cand_ok receives whether
+    // that chain is schedulable, the analysis stops once it is done, and
+    // first_ok is not touched.
+    const int16_t *target;
 };
 
 // Item i of a launch: system index and candidate index (0 outside candidate mode).
