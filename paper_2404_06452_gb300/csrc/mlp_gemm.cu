@@ -302,24 +302,59 @@ constexpr int kPersistThreads = 576; // warp 0 TMA, warp 1 TMEM + MMA, warps 2..
 constexpr int kPersistEpiWarps = kPersistThreads / 32 - 2;
 constexpr int kPersistStages = 4;
 
+// Output staging of the TMA-store epilogue: one 32 x 32 bf16 block per
+// epilogue warp (its 32 rows, 32 columns), 64-byte swizzled.
+constexpr int kStageBytes = 32 * 32 * 2;
+
 template <int BN>
 struct PersistSmem {
     static constexpr int W_BYTES = 256 * BN * 2; // K up to 256
     static constexpr int A_BYTES = BM * BK * 2;
-    static constexpr int TILES = W_BYTES + kPersistStages * A_BYTES;
+    static constexpr int STAGE_BYTES = kPersistEpiWarps * kStageBytes;
+    static constexpr int BIAS_BYTES = BN * 4;
+    static constexpr int TILES = W_BYTES + kPersistStages * A_BYTES + STAGE_BYTES + BIAS_BYTES;
     static constexpr int TOTAL = TILES + 256 + 1024;
 };
 
-template <int BN>
+// Bias, GELU and bf16 packing of 32 accumulator columns col0.. of this
+// thread's row, then the row's 64 bytes into the warp's staging block: the
+// 16-byte piece k of row r sits at piece k ^ ((r >> 1) & 3), the 64-byte
+// swizzle the tensor map of the store names.
+__device__ __forceinline__ void stage_gelu_row(const float *bias_s, int col0, const uint32_t (&v)[32],
+                                               uint8_t *stage, int lane)
+{
+    uint32_t packed[16];
+    const float2 *b2 = reinterpret_cast<const float2 *>(bias_s + col0);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float2 bb = b2[i];
+        const __nv_bfloat162 h =
+            __floats2bfloat162_rn(gelu(__uint_as_float(v[2 * i]) + bb.x), gelu(__uint_as_float(v[2 * i + 1]) + bb.y));
+        packed[i] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    uint8_t *row = stage + lane * 64;
+    const int sw = (lane >> 1) & 3;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        *reinterpret_cast<uint4 *>(row + ((k ^ sw) << 4)) =
+            make_uint4(packed[4 * k], packed[4 * k + 1], packed[4 * k + 2], packed[4 * k + 3]);
+}
+
+// TMA_OUT: the epilogue is bias + GELU into H through the staging blocks and
+// TMA stores (every column of the tile valid); otherwise epilogue_chunk.
+template <int BN, bool TMA_OUT>
 __global__ void __launch_bounds__(kPersistThreads, 1)
     tc_layer_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                               int kb_total, int m_tiles, TcEpilogue ep, int32_t *err)
+                               const __grid_constant__ CUtensorMap tmH, int kb_total, int m_tiles, TcEpilogue ep,
+                               int32_t *err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     using L = PersistSmem<BN>;
     uint8_t *wsm = smem;               // kb_total blocks of [BN][64] bf16, 128-byte swizzled
     uint8_t *asm_a = smem + L::W_BYTES; // A ring
+    uint8_t *stage_all = asm_a + kPersistStages * L::A_BYTES; // epilogue output blocks (1024-byte aligned)
+    float *bias_s = (float *)(stage_all + L::STAGE_BYTES);
     uint64_t *full = (uint64_t *)(smem + L::TILES);
     uint64_t *empty = full + kPersistStages;
     uint64_t *acc_full = empty + kPersistStages;
@@ -354,6 +389,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         tc::tmem_alloc(tmem_slot, kCols);
         tc::tmem_relinquish();
     }
+    if constexpr (TMA_OUT) // the bias, once per CTA (the TMA-store epilogue reads it from here)
+        for (int i = threadIdx.x; i < BN; i += blockDim.x) bias_s[i] = ep.bias[i];
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
@@ -417,6 +454,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         tc::mbar_wait(fin, 0, kWaitNs);
     } else if (warp >= 2) { // ---- epilogue: one output row per thread, a quarter of the columns per warp
         const int q = warp & 3, cg = (warp - 2) >> 2;
+        uint8_t *stage = stage_all + (warp - 2) * kStageBytes;
         int i = 0;
         for (int tile = blockIdx.x; tile < m_tiles; tile += gridDim.x, ++i) {
             const int b = i & 1;
@@ -426,18 +464,32 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
                 break;
             }
             tc::fence_after_sync();
-            const int row = tile * BM + 32 * q + lane;
+            const int row0 = tile * BM + 32 * q;
 #pragma unroll 1
             for (int c = cg; c < BN / 32; c += 4) {
                 uint32_t v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + 32 * c), v);
                 tc::tmem_wait_ld();
-                epilogue_chunk(ep, row, 32 * c, v);
+                if constexpr (TMA_OUT) {
+                    // the warp's previous store has read its staging block
+                    if (lane == 0) tc::bulk_wait_read_all();
+                    __syncwarp();
+                    stage_gelu_row(bias_s, 32 * c, v, stage, lane);
+                    tc::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0 && row0 < ep.M) { // rows past M are clipped by the tensor map
+                        tc::tma_store_2d(&tmH, stage, 32 * c, row0);
+                        tc::bulk_commit();
+                    }
+                } else {
+                    epilogue_chunk(ep, row0 + lane, 32 * c, v);
+                }
             }
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&acc_empty[b]);
         }
+        if (TMA_OUT && lane == 0) tc::bulk_wait_all(); // stores complete before shared memory is released
     }
     __syncthreads();
     if (warp == 0 && lane == 0 && *abort_flag) {
@@ -531,19 +583,39 @@ static int sm_count()
     return cache[dev];
 }
 
+// bf16 row-major output [rows][ld] with cols valid columns, 32 x 32 boxes,
+// 64-byte swizzle (the epilogue's staging layout); rows past `rows` are not written
+bool make_store_map(CUtensorMap *m, const __nv_bfloat16 *base, int rows, int cols, int ld)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {32, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN>
 int launch_persistent(const TcGemm &g, int32_t *err, cudaStream_t stream)
 {
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, mh;
     if (!make_map(&ma, g.A, g.a_rows, g.K, g.lda, BM) || !make_map(&mb, g.B, g.b_rows, g.K, g.ldb, BN))
         return PAAM_E_CUDA;
+    // the TMA-store epilogue: bias + GELU into H only, every column of the tile valid, H 16-byte aligned rows
+    int tma_out = g.ep.mode == TC_EPI_BIAS_GELU && !g.ep.Z && !g.ep.HT && g.ep.H && g.ep.bias && g.ep.N == BN &&
+                  g.ep.ldh % 8 == 0 && ((uintptr_t)g.ep.H & 15) == 0;
+    if (tma_out && !make_store_map(&mh, g.ep.H, g.ep.M, g.ep.N, g.ep.ldh)) tma_out = 0;
+    if (!tma_out) mh = ma; // unused
     const int m_tiles = (g.ep.M + BM - 1) / BM;
     const int n_sm = sm_count();
     const int grid = m_tiles < n_sm ? m_tiles : (n_sm > 0 ? n_sm : 1);
     const int smem = PersistSmem<BN>::TOTAL;
-    PAAM_CUDA_TRY(cudaFuncSetAttribute(tc_layer_persistent_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem));
-    tc_layer_persistent_kernel<BN><<<grid, kPersistThreads, smem, stream>>>(ma, mb, g.K / BK, m_tiles, g.ep, err);
+    auto kern = tma_out ? tc_layer_persistent_kernel<BN, true> : tc_layer_persistent_kernel<BN, false>;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    kern<<<grid, kPersistThreads, smem, stream>>>(ma, mb, mh, g.K / BK, m_tiles, g.ep, err);
     PAAM_CUDA_TRY(cudaGetLastError());
     paam_count_launch();
     return PAAM_OK;

@@ -136,6 +136,41 @@ def test_infer_and_predict_scores_match_oracle_network():
     m.free()
 
 
+def test_infer_at_scale_matches_oracle_network():
+    """100,000 candidate rows (a ragged last 128-row tile) take the persistent
+    weight-stationary layers with the TMA-store epilogue; sampled systems'
+    scores follow the float64 network."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    p = _random_params(5)
+    m = pkg.Model.create(ctx(), 3)
+    m.set_params(p)
+    sy = g.generate("cfg4s", n_sys=400)
+    K = 250
+    ranks = g.candidate_ranks(sy, K, 12)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    r = torch.from_numpy(ranks).cuda()
+    ranked = torch.empty((sy.n_sys, 4), dtype=torch.int32, device="cuda")
+    scores = torch.empty((sy.n_sys, K), dtype=torch.float32, device="cuda")
+    pkg.paam_surrogate_infer(ctx(), m, b, r, 4, ranked, scores)
+    torch.cuda.synchronize()
+    got = scores.cpu().numpy()
+    idx = np.r_[0:8, 196:204, 392:400]  # first, middle and last rows of the batch
+    sub = sy.subset(idx)
+    n = sub.chains_per_system()
+    Y = _oracle_net(p, _bf16_round(ofeat.features(sub, ranks[idx]))).reshape(len(idx), K, 64)
+    want = np.stack([np.maximum(Y[s, :, :n[s]].max(axis=1), 0.0) for s in range(len(idx))])
+    assert np.all(np.abs(got[idx] - want) <= 3e-2 * (np.abs(want) + 1.0)), np.abs(got[idx] - want).max()
+    # the ranking is the score order
+    rk = ranked.cpu().numpy()
+    for s in range(sy.n_sys):
+        assert np.all(np.diff(got[s, rk[s]]) >= 0)
+    b.free()
+    m.free()
+
+
 def _random_params(seed):
     rng = np.random.default_rng(seed)
     out = []
