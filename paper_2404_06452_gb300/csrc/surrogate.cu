@@ -345,6 +345,10 @@ extern "C" int paam_model_set_params(paam_model *m, const float *host)
 // ---------------------------------------------------------------------------
 namespace {
 
+// Rows of one inference chunk at most (about 2.3 KB of scratch per row for
+// systems of up to 16 chains, 3.8 KB for 64)
+constexpr int64_t kInferRows = (int64_t)1 << 22;
+
 struct Work {
     int rows;
     void *block;
@@ -353,12 +357,14 @@ struct Work {
     int32_t *err;
 };
 
-int work_alloc(Work &w, int rows, bool train, cudaStream_t s)
+// xw: columns of the input buffer Xb (the full 1024 for training; inference
+// stores only the columns its batch can fill)
+int work_alloc(Work &w, int rows, bool train, cudaStream_t s, int xw = XW)
 {
     w = Work{};
     w.rows = rows;
     const size_t r = (size_t)rows;
-    size_t bytes = 2 * r * XW * (train ? 2 : 1) + 3 * 2 * r * 256 * (train ? 6 : 1) + 4 * r * 64 * (train ? 2 : 1) +
+    size_t bytes = 2 * r * xw * (train ? 2 : 1) + 3 * 2 * r * 256 * (train ? 6 : 1) + 4 * r * 64 * (train ? 2 : 1) +
                    2 * 2 * r * 64 + 64 * 256;
     if (cudaMallocAsync(&w.block, bytes, s) != cudaSuccess) {
         cudaGetLastError();
@@ -370,8 +376,8 @@ int work_alloc(Work &w, int rows, bool train, cudaStream_t s)
         p += (n + 255) & ~(size_t)255;
         return q;
     };
-    w.Xb = (__nv_bfloat16 *)take(2 * r * XW);
-    if (train) w.XbT = (__nv_bfloat16 *)take(2 * r * XW);
+    w.Xb = (__nv_bfloat16 *)take(2 * r * xw);
+    if (train) w.XbT = (__nv_bfloat16 *)take(2 * r * xw);
     for (int l = 0; l < 3; ++l) {
         w.H[l] = (__nv_bfloat16 *)take(2 * r * 256);
         if (train) {
@@ -645,13 +651,17 @@ extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const pa
     if (b->n_sys == 0) return PAAM_OK;
     PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream_;
-    // candidates are scored in chunks of whole systems, at most ~256k rows at a time
-    int64_t chunk = (262144 + K - 1) / K;
-    if (chunk > b->n_sys) chunk = b->n_sys;
+    // candidates are scored in equal chunks of whole systems of at most about
+    // kInferRows rows: each chunk pays a fixed cost (launches, the weight load
+    // of every persistent CTA, the last tile's epilogue running alone), so
+    // chunks are as large as the scratch allows
+    const int64_t total = b->n_sys * (int64_t)K;
+    const int64_t n_chunks = (total + kInferRows - 1) / kInferRows;
+    const int64_t chunk = (b->n_sys + n_chunks - 1) / n_chunks;
     const int rows = (int)(chunk * K);
     const int kx = input_width(b);
     Work w;
-    int rc = work_alloc(w, rows, false, s);
+    int rc = work_alloc(w, rows, false, s, kx);
     if (rc != PAAM_OK) return rc;
     float *sc = scores;
     void *tmp = nullptr;
@@ -697,10 +707,11 @@ extern "C" int paam_surrogate_predict(paam_ctx *ctx, const paam_model *m, const 
     if (b->n_sys == 0) return PAAM_OK;
     PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = (cudaStream_t)stream_;
-    const int64_t chunk = b->n_sys < 262144 ? b->n_sys : 262144;
+    const int64_t n_chunks = (b->n_sys + kInferRows - 1) / kInferRows;
+    const int64_t chunk = (b->n_sys + n_chunks - 1) / n_chunks;
     const int kx = input_width(b);
     Work w;
-    int rc = work_alloc(w, (int)chunk, false, s);
+    int rc = work_alloc(w, (int)chunk, false, s, kx);
     if (rc != PAAM_OK) return rc;
     if (cudaMemsetAsync(w.err, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
     for (int64_t s0 = 0; s0 < b->n_sys && rc == PAAM_OK; s0 += chunk) {

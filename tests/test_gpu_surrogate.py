@@ -171,6 +171,37 @@ def test_infer_at_scale_matches_oracle_network():
     m.free()
 
 
+def test_infer_in_two_chunks_matches_oracle_network():
+    """5.12M candidate rows run as two chunks of whole systems; systems on both
+    sides of the boundary, and the last ones, follow the float64 network."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    p = _random_params(6)
+    m = pkg.Model.create(ctx(), 4)
+    m.set_params(p)
+    sy = g.generate("cfg1", n_sys=20_000)
+    K = 256
+    ranks = g.candidate_ranks(sy, K, 13)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    r = torch.from_numpy(ranks).cuda()
+    ranked = torch.empty((sy.n_sys, 2), dtype=torch.int32, device="cuda")
+    scores = torch.empty((sy.n_sys, K), dtype=torch.float32, device="cuda")
+    pkg.paam_surrogate_infer(ctx(), m, b, r, 2, ranked, scores)
+    torch.cuda.synchronize()
+    got = scores.cpu().numpy()
+    idx = np.r_[9_994:10_006, 19_994:20_000]
+    sub = sy.subset(idx)
+    n = sub.chains_per_system()
+    Y = _oracle_net(p, _bf16_round(ofeat.features(sub, ranks[idx]))).reshape(len(idx), K, 64)
+    want = np.stack([np.maximum(Y[s, :, :n[s]].max(axis=1), 0.0) for s in range(len(idx))])
+    assert np.all(np.abs(got[idx] - want) <= 3e-2 * (np.abs(want) + 1.0)), np.abs(got[idx] - want).max()
+    assert np.all(np.isfinite(got))
+    b.free()
+    m.free()
+
+
 def _random_params(seed):
     rng = np.random.default_rng(seed)
     out = []
