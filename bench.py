@@ -225,6 +225,9 @@ def run_reference(args):
 # priority search (256 candidate orders per system) and the surrogate
 # ---------------------------------------------------------------------------
 SEARCH_K = 256
+# guided search: the two heuristic seeds (slots 0 and 1) are always confirmed,
+# the network ranks the rest
+SEARCH_PINNED = 2
 
 
 def _timed(fn, reps=1):
@@ -367,11 +370,11 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
     first = torch.empty(S, dtype=torch.int32, device="cuda")
     cand = torch.empty((S, K), dtype=torch.uint8, device="cuda")
 
-    def infer(order):
-        pkg.paam_surrogate_infer(ctx, model, b, r, order.shape[1], order)
+    def infer(order, pinned=SEARCH_PINNED):
+        pkg.paam_surrogate_infer(ctx, model, b, r, order.shape[1], order, n_pinned=pinned)
 
-    def guided(order, stop_at_first, cand_ok):
-        infer(order)
+    def guided(order, stop_at_first, cand_ok, pinned=SEARCH_PINNED):
+        infer(order, pinned)
         pkg.paam_rta_search_ordered(ctx, b, opts, r, order, stop_at_first, cand_ok, first)
         return first
 
@@ -385,6 +388,9 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
     has = fx >= 0
     false_accepts = int(np.sum(cg & ~cx))
     recall = float((fg[has] >= 0).mean()) if has.any() else None
+    # the network alone (no pinned seeds) under the same budget
+    guided(order_k, False, cand, 0)
+    recall_net = float((first.cpu().numpy()[has] >= 0).mean()) if has.any() else None
     # the same confirmation budget spent on the first k slots, and on k random slots
     slot_recall = float(cx[:, :top_k][has].any(axis=1).mean()) if has.any() else None
     rng = np.random.default_rng(3)
@@ -394,7 +400,8 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
     guided(order_all, True, None)
     t_fb, _ = _timed(lambda: guided(order_all, True, None), 3)
     fb_same = bool(np.array_equal(first.cpu().numpy() >= 0, has))
-    # recall of the network's ranking at other budgets (an admissible order among the first k)
+    # recall of the network's own ranking (no pinned seeds) at other budgets
+    infer(order_all, 0)
     ranked_all = order_all.cpu().numpy()
     ok_in_rank = np.take_along_axis(cx, ranked_all, 1)
     recall_at = {str(k): float(ok_in_rank[:, :k][has].any(axis=1).mean()) for k in (1, 2, 4, 8, 16, 32, 64)
@@ -409,10 +416,12 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
         "workload": f"cfg4s: {S} systems x {K} candidate orders",
         "exhaustive_systems_per_s": S / t_ex, "exhaustive_ms": t_ex * 1e3,
         "early_exit_systems_per_s": S / t_ee, "early_exit_ms": t_ee * 1e3,
-        "top_k": top_k, "guided_systems_per_s": S / t_g, "guided_ms": t_g * 1e3,
+        "top_k": top_k, "pinned_seed_slots": SEARCH_PINNED,
+        "guided_systems_per_s": S / t_g, "guided_ms": t_g * 1e3,
         "speedup_vs_exhaustive": t_ex / t_g, "speedup_vs_early_exit": t_ee / t_g,
         "infer_ms": t_inf * 1e3, "infer_tflops": flops_row * S * K / t_inf / 1e12,
-        "false_accepts": false_accepts, "recall": recall, "recall_first_k_slots": slot_recall,
+        "false_accepts": false_accepts, "recall": recall, "recall_network_only": recall_net,
+        "recall_first_k_slots": slot_recall,
         "recall_random_k": rand_recall, "recall_at_k": recall_at,
         "fallback": {"systems_per_s": S / t_fb, "ms": t_fb * 1e3, "same_verdicts_as_exhaustive": fb_same,
                      "speedup_vs_exhaustive": t_ex / t_fb, "speedup_vs_early_exit": t_ee / t_fb},

@@ -282,7 +282,9 @@ int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *batch, const paam_an
  * paam_rta_search_priorities) by its largest predicted R / D and writes the
  * top_k candidate indices per system in increasing score to ranked
  * ([n_sys][top_k] device int32); scores ([n_sys][K] device float) optional.
- * Synchronises `stream`.
+ * The first n_pinned candidate slots of every system (0 <= n_pinned <= K,
+ * e.g. heuristic seeds) are ranked first, in slot order, ahead of every
+ * scored candidate; their scores are still written.  Synchronises `stream`.
  *
  * paam_surrogate_predict: per-chain predictions ([n_sys][64] device float) of
  * the batch's own priority orders.
@@ -317,8 +319,8 @@ int paam_model_load(paam_ctx *ctx, const char *path, paam_model **out);
 int paam_surrogate_train(paam_ctx *ctx, const paam_batch *batch, const int64_t *R, const uint8_t *status,
                          const paam_train_opts *opts, paam_model **model);
 int paam_surrogate_infer(paam_ctx *ctx, const paam_model *model, const paam_batch *batch, const int16_t *ranks,
-                         int32_t K, int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t top_k,
-                         int32_t *ranked, float *scores, void *stream);
+                         int32_t K, int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t n_pinned,
+                         int32_t top_k, int32_t *ranked, float *scores, void *stream);
 int paam_surrogate_predict(paam_ctx *ctx, const paam_model *model, const paam_batch *batch, int32_t n_buckets,
                            int64_t kappa_ns, float *pred, void *stream);
 int paam_surrogate_grad(paam_ctx *ctx, paam_model *model, const void *X, const float *L, int32_t rows,

@@ -95,7 +95,7 @@ def lib():
                                                     P(_c_void_p)]),
             "paam_surrogate_infer": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
                                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
-                                                    _c_void_p, _c_void_p, _c_void_p]),
+                                                    ctypes.c_int32, _c_void_p, _c_void_p, _c_void_p]),
             "paam_surrogate_predict": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
                                                       ctypes.c_int64, _c_void_p, _c_void_p]),
             "paam_surrogate_grad": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
@@ -430,11 +430,13 @@ def paam_surrogate_train(ctx: Context, batch: Batch, R, status, opts: TrainOpts,
 
 
 def paam_surrogate_infer(ctx: Context, model: Model, batch: Batch, ranks, top_k: int, ranked, scores=None,
-                         n_buckets: int = 1, kappa: int = 0, stream=None):
+                         n_buckets: int = 1, kappa: int = 0, stream=None, n_pinned: int = 0):
+    """Rank the candidates ``ranks`` ([S, K, nmax]) by the network's score into
+    ``ranked`` ([S, top_k]); the first ``n_pinned`` slots rank ahead of all."""
     S, K, nmax = ranks.shape
     _check(lib().paam_surrogate_infer(ctx.handle, model.handle, batch.handle, _ptr(ranks), int(K), int(nmax),
-                                      int(n_buckets), int(kappa), int(top_k), _ptr(ranked), _ptr(scores),
-                                      _stream_ptr(stream)), "paam_surrogate_infer")
+                                      int(n_buckets), int(kappa), int(n_pinned), int(top_k), _ptr(ranked),
+                                      _ptr(scores), _stream_ptr(stream)), "paam_surrogate_infer")
 
 
 def paam_surrogate_predict(ctx: Context, model: Model, batch: Batch, pred, n_buckets: int = 1, kappa: int = 0,

@@ -155,8 +155,10 @@ __global__ void to_bf16_kernel(const float *W, int64_t n, int rows, int cols, __
     }
 }
 
-// ---- per system: the top_k candidates in increasing score (ties: lower index)
-__global__ void topk_kernel(const float *score, int64_t n_sys, int32_t K, int32_t top_k, int32_t *ranked)
+// ---- per system: the top_k candidates in increasing score (ties: lower
+// index), the first n_pinned candidate slots ahead of every scored one
+__global__ void topk_kernel(const float *score, int64_t n_sys, int32_t K, int32_t n_pinned, int32_t top_k,
+                            int32_t *ranked)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t sys = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -170,7 +172,7 @@ __global__ void topk_kernel(const float *score, int64_t n_sys, int32_t K, int32_
         float best_s = INFINITY;
         int best_i = 0x7fffffff;
         for (int k = lane; k < K; k += 32) {
-            const float v = isnan(s[k]) ? INFINITY : s[k];
+            const float v = k < n_pinned ? -INFINITY : (isnan(s[k]) ? INFINITY : s[k]);
             const bool after = v > last_s || (v == last_s && k > last_i);
             if (after && (v < best_s || (v == best_s && k < best_i))) {
                 best_s = v;
@@ -639,12 +641,13 @@ extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const in
 // inference
 // ---------------------------------------------------------------------------
 extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const paam_batch *b, const int16_t *ranks,
-                                    int32_t K, int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t top_k,
-                                    int32_t *ranked, float *scores, void *stream_)
+                                    int32_t K, int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t n_pinned,
+                                    int32_t top_k, int32_t *ranked, float *scores, void *stream_)
 {
     if (!ctx || !m || !b || (b->n_sys > 0 && (!ranks || !ranked))) return PAAM_E_INVAL;
     if (m->ctx != ctx || b->ctx != ctx) return PAAM_E_STATE;
-    if (K < 1 || top_k < 1 || top_k > K || nmax < b->max_chains || n_buckets < 1 || kappa_ns < 0 ||
+    if (K < 1 || top_k < 1 || top_k > K || n_pinned < 0 || n_pinned > K || nmax < b->max_chains || n_buckets < 1 ||
+        kappa_ns < 0 ||
         kappa_ns > PAAM_MAX_OVERHEAD)
         return PAAM_E_INVAL;
     if (b->max_chains > NCH) return PAAM_E_UNSUPPORTED;
@@ -684,7 +687,7 @@ extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const pa
         if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, kx, false, s, &so);
     }
     if (rc == PAAM_OK) {
-        topk_kernel<<<(unsigned)((b->n_sys + 7) / 8), 256, 0, s>>>(sc, b->n_sys, K, top_k, ranked);
+        topk_kernel<<<(unsigned)((b->n_sys + 7) / 8), 256, 0, s>>>(sc, b->n_sys, K, n_pinned, top_k, ranked);
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
         paam_count_launch();
     }

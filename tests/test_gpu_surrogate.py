@@ -297,6 +297,12 @@ def test_infer_ranks_by_score_and_guided_search_is_exact():
     sc = scores.cpu().numpy()
     want = np.argsort(sc, axis=1, kind="stable")[:, :top]
     assert np.array_equal(ranked.cpu().numpy(), want)
+    # pinned seed slots come first, in slot order, then the scored ones
+    pinned = torch.empty_like(ranked)
+    pkg.paam_surrogate_infer(ctx(), m, b, r, top, pinned, n_pinned=3)
+    torch.cuda.synchronize()
+    rest = 3 + np.argsort(sc[:, 3:], axis=1, kind="stable")[:, :top - 3]
+    assert np.array_equal(pinned.cpu().numpy(), np.concatenate([np.tile([0, 1, 2], (sy.n_sys, 1)), rest], axis=1))
     # guided search: confirm the top candidates exactly
     first = torch.empty(sy.n_sys, dtype=torch.int32, device="cuda")
     cand = torch.empty((sy.n_sys, K), dtype=torch.uint8, device="cuda")
