@@ -718,15 +718,9 @@ def run_ours(args):
         d2h = hR.numel() * 8 + hst.numel() + hv.numel()
 
         def e2e_step():
-            b = pkg.paam_rta_load_systems(ctx, pinned, stream=stream, is_device=False)
-            pkg.paam_rta_set_launch_config(b, cfg_index)
-            pkg.paam_rta_analyze_batch(ctx, b, opts, R, st, verdict, stream=stream)
-            with torch.cuda.stream(stream):
-                hR.copy_(R, non_blocking=True)
-                hst.copy_(st, non_blocking=True)
-                hv.copy_(verdict, non_blocking=True)
-            stream.synchronize()
-            b.free()
+            # one call: chunked host-to-device copies overlapped with validation,
+            # analysis and the copies of R, status and verdict back to the host
+            pkg.paam_rta_analyze_host(ctx, pinned, opts, hR, hst, hv, launch_config=cfg_index)
 
         e2e_step()
         torch.cuda.synchronize()

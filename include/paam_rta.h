@@ -228,6 +228,34 @@ int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *batch, const paam_a
                             int32_t stop_at_first, uint8_t *cand_ok, int32_t *first_ok, void *stream);
 
 /*
+ * The analysis of a batch held in host memory (paam_rta_load_systems +
+ * paam_rta_analyze_batch + copies of the results, in one call), pipelined:
+ * the batch is split into chunks of whole systems, and the host-to-device
+ * copy of chunk c + 1 runs while chunk c is validated and analysed and the
+ * results of earlier chunks are copied back.  The results are those of
+ * paam_rta_analyze_batch on the same systems (Theorem 1, Eq. 6).
+ *
+ *   v               host view (is_device = 0); page-locked memory lets the
+ *                   copies run asynchronously, other host memory works but
+ *                   serialises them.  Validated as by paam_rta_load_systems,
+ *                   chunk by chunk.
+ *   launch_config   index of a launch configuration
+ *                   (paam_rta_num_launch_configs), or -1 for the default.
+ *   chunk_systems   systems per chunk, or <= 0 for about 128 MB of input
+ *                   per chunk.
+ *   R, status       host [n_chain]; verdict host [n_sys], optional.
+ *
+ * Device memory for the whole batch is taken from the device's memory pool
+ * for the duration of the call.  Returns when every result is on the host.
+ * Errors: those of paam_rta_load_systems (PAAM_E_INVAL with the first bad
+ * chunk; no result of it or a later chunk is written), PAAM_E_RANGE,
+ * PAAM_E_NOMEM, PAAM_E_CUDA.
+ */
+int paam_rta_analyze_host(paam_ctx *ctx, const paam_systems_view *v, const paam_analysis_opts *opts,
+                          int32_t launch_config, int64_t chunk_systems, int64_t *R, uint8_t *status,
+                          uint8_t *verdict);
+
+/*
  * Audsley-style priority seed: a candidate order for the search, built from
  * the lowest priority level up with the exact analysis (Theorem 1) as the
  * test.  The paper assigns priorities by hand; this greedy is a reading of

@@ -116,6 +116,8 @@ def lib():
                                                           _c_void_p, _c_void_p, _c_void_p]),
             "paam_rta_audsley_order": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), ctypes.c_int32,
                                                       _c_void_p, _c_void_p]),
+            "paam_rta_analyze_host": (ctypes.c_int, [_c_void_p, P(SystemsView), P(AnalysisOpts), ctypes.c_int32,
+                                                     ctypes.c_int64, _c_void_p, _c_void_p, _c_void_p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -134,7 +136,7 @@ def exported_symbols() -> list:
             "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
             "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
             "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_rta_end_to_end",
-            "paam_measure_preemption", "paam_rta_audsley_order"]
+            "paam_measure_preemption", "paam_rta_audsley_order", "paam_rta_analyze_host"]
 
 
 def launch_count() -> int:
@@ -313,6 +315,18 @@ def paam_rta_search_priorities(ctx: Context, batch: Batch, opts: AnalysisOpts, r
     _check(lib().paam_rta_search_priorities(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(ranks), int(K),
                                             int(nmax), 1 if stop_at_first else 0, _ptr(cand_ok), _ptr(first_ok),
                                             _stream_ptr(stream)), "paam_rta_search_priorities")
+
+
+def paam_rta_analyze_host(ctx: Context, sy, opts: AnalysisOpts, R, status, verdict=None, launch_config: int = -1,
+                          chunk_systems: int = 0):
+    """Pipelined analysis of host arrays ``sy`` (numpy or page-locked torch
+    CPU tensors) into host outputs ``R`` [n_chain] int64, ``status``
+    [n_chain] uint8 and optionally ``verdict`` [n_sys] uint8."""
+    v, keep = make_view(sy, False)
+    _check(lib().paam_rta_analyze_host(ctx.handle, ctypes.byref(v), ctypes.byref(opts), int(launch_config),
+                                       int(chunk_systems), _ptr(R), _ptr(status), _ptr(verdict)),
+           "paam_rta_analyze_host")
+    del keep
 
 
 def paam_rta_audsley_order(ctx: Context, batch: Batch, opts: AnalysisOpts, ranks_out, stream=None):

@@ -81,6 +81,7 @@ extern "C" void paam_destroy(paam_ctx *c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    paam_host_pipe_release(c);
     cudaFree(c->d_err);
     cudaFree(c->d_stats);
     cudaStreamDestroy(c->capture_stream);
@@ -94,6 +95,11 @@ extern "C" void paam_destroy(paam_ctx *c)
 struct ValidateArgs {
     BatchDev b;
     int64_t n_chain, n_cb, n_seg, n_exec;
+    // index ranges a system's chains, callbacks, segments and executors must
+    // lie in (the whole batch, or the part of it copied so far); sentinels:
+    // also check the first and last offsets of the whole batch
+    ValidateRange r;
+    int sentinels;
     const int32_t *acc;
     int32_t *err; // [0] code, [1] first bad system (min), [2] max chains, [3] max executors
     unsigned long long *stats; // ST_* maxima
@@ -112,7 +118,7 @@ __global__ void validate_kernel(ValidateArgs a)
     unsigned long long lmax[ST_COUNT] = {};
     int32_t nmax = 0, xmax = 0;
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < b.n_sys; s += stride) {
-        if (s == 0) { // global sentinels
+        if (s == 0 && a.sentinels) { // global sentinels
             if (b.sys_chain_off[0] != 0 || b.sys_exec_off[0] != 0 || b.chain_cb_off[0] != 0 ||
                 b.cb_seg_off[0] != 0 || b.sys_chain_off[b.n_sys] != a.n_chain ||
                 b.sys_exec_off[b.n_sys] != a.n_exec || b.chain_cb_off[a.n_chain] != a.n_cb ||
@@ -123,7 +129,8 @@ __global__ void validate_kernel(ValidateArgs a)
         }
         const int64_t c0 = b.sys_chain_off[s], c1 = b.sys_chain_off[s + 1];
         const int64_t x0 = b.sys_exec_off[s], x1 = b.sys_exec_off[s + 1];
-        if (c0 < 0 || c1 < c0 || c1 > a.n_chain || x0 < 0 || x1 < x0 || x1 > a.n_exec) {
+        if (c0 < a.r.chain_lo || c1 < c0 || c1 > a.r.chain_hi || x0 < a.r.exec_lo || x1 < x0 ||
+            x1 > a.r.exec_hi) {
             fail(a.err, PAAM_E_INVAL, s);
             continue;
         }
@@ -160,7 +167,7 @@ __global__ void validate_kernel(ValidateArgs a)
             for (int64_t k = c0; k < c; ++k)
                 if (b.prio[k] == b.prio[c]) bad = true;
             const int64_t b0 = b.chain_cb_off[c], b1 = b.chain_cb_off[c + 1];
-            if (b0 < 0 || b1 < b0 || b1 > a.n_cb) {
+            if (b0 < a.r.cb_lo || b1 < b0 || b1 > a.r.cb_hi) {
                 bad = true;
                 break;
             }
@@ -169,7 +176,7 @@ __global__ void validate_kernel(ValidateArgs a)
             for (int64_t cb = b0; cb < b1 && !bad; ++cb) {
                 const int64_t e = b.E[cb];
                 const int64_t q0 = b.cb_seg_off[cb], q1 = b.cb_seg_off[cb + 1];
-                if (e < 0 || e > PAAM_MAX_TIME || q0 < 0 || q1 < q0 || q1 > a.n_seg) {
+                if (e < 0 || e > PAAM_MAX_TIME || q0 < a.r.seg_lo || q1 < q0 || q1 > a.r.seg_hi) {
                     bad = true;
                     break;
                 }
@@ -246,12 +253,21 @@ __global__ void validate_kernel(ValidateArgs a)
 int paam_launch_validate(const paam_batch *b, const int32_t *acc, int32_t *err, unsigned long long *stats,
                          cudaStream_t stream)
 {
+    const ValidateRange whole = {0, b->n_chain, 0, b->n_cb, 0, b->n_seg, 0, b->n_exec};
+    return paam_launch_validate_range(b, acc, whole, 1, err, stats, stream);
+}
+
+int paam_launch_validate_range(const paam_batch *b, const int32_t *acc, const ValidateRange &r, int sentinels,
+                               int32_t *err, unsigned long long *stats, cudaStream_t stream)
+{
     ValidateArgs a;
     a.b = batch_dev(b);
     a.n_chain = b->n_chain;
     a.n_cb = b->n_cb;
     a.n_seg = b->n_seg;
     a.n_exec = b->n_exec;
+    a.r = r;
+    a.sentinels = sentinels;
     a.acc = acc;
     a.err = err;
     a.stats = stats;

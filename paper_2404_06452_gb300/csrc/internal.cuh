@@ -82,6 +82,16 @@ __device__ __forceinline__ bool cand_pruned(const AnalysisParams &p, int64_t sys
 // analysis needs (the 32-bit fast path covers every system when they fit).
 enum { ST_TMAX = 0, ST_DMAX, ST_ECMAX, ST_SCMAX, ST_DELTAMAX, ST_ACCMAX, ST_COUNT };
 
+// Streams, events and page-locked words of the pipelined host analysis
+// (host_pipeline.cu), created on first use and kept for the context's life.
+struct HostPipe {
+    cudaStream_t in = nullptr, val = nullptr, an = nullptr, out = nullptr;
+    cudaEvent_t *ev = nullptr;
+    int n_ev = 0;
+    void *words = nullptr; // page-locked
+    size_t words_bytes = 0;
+};
+
 struct paam_ctx {
     int device;
     int n_sm;
@@ -89,7 +99,10 @@ struct paam_ctx {
     cudaStream_t capture_stream; // private stream used to capture analysis graphs
     int32_t *d_err;        // validation: [0] code, [1] first bad system, [2] max chains, [3] max executors
     unsigned long long *d_stats; // validation: ST_* maxima
+    HostPipe *pipe;
 };
+
+void paam_host_pipe_release(paam_ctx *ctx); // host_pipeline.cu
 
 // Device copy of a validated batch: the same SoA/CSR arrays as
 // paam_systems_view, all inside one allocation.
@@ -185,6 +198,17 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
 // executors} (initialise to {0, INT32_MAX, 0, 0}), stats = ST_* maxima (zeroed).
 int paam_launch_validate(const paam_batch *b, const int32_t *acc, int32_t *err, unsigned long long *stats,
                          cudaStream_t stream);
+
+// Half-open index ranges the systems of a validation must stay inside.
+struct ValidateRange {
+    int64_t chain_lo, chain_hi, cb_lo, cb_hi, seg_lo, seg_hi, exec_lo, exec_hi;
+};
+
+// The same over the systems of b (which may be a window of a larger batch:
+// offsets stay absolute), each system's indices checked against r; sentinels
+// adds the whole batch's first- and last-offset checks.
+int paam_launch_validate_range(const paam_batch *b, const int32_t *acc, const ValidateRange &r, int sentinels,
+                               int32_t *err, unsigned long long *stats, cudaStream_t stream);
 
 // Exact int64 kernel (analyze_wide.cu) over list[0 .. *count) or, with
 // list == nullptr, over every system.
