@@ -147,18 +147,22 @@ def peaks() -> dict:
 CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>", 2: "analyze_fast_kernel<16, 32>",
                  3: "analyze_reg1_kernel<16>", 4: "analyze_reg_kernel<4, 4>", 5: "analyze_reg_kernel<16, 2>",
                  6: "analyze_reg1_kernel<32>", 7: "analyze_reg_kernel<8, 2>", 8: "analyze_fast_kernel<4, 16>",
-                 9: "analyze_fast_kernel<8, 32>", 10: "analyze_reg_kernel<16, 2>", 11: "analyze_reg_kernel<4, 4>"}
+                 9: "analyze_fast_kernel<8, 32>", 10: "analyze_reg_kernel<16, 2>", 11: "analyze_reg_kernel<4, 4>",
+                 12: "analyze_reg1_kernel<16> (work queue)", 13: "analyze_reg_kernel<8, 2> (work queue)",
+                 14: "analyze_fast_kernel<8, 16> (work queue)", 15: "analyze_reg_kernel<16, 2> (work queue)",
+                 16: "analyze_reg1_kernel<32> (work queue)"}
 
 
 # DRAM read + write per system of the analysis kernel, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of 500,000 systems of this
-# workload in launch configuration 3 (analyze_reg1_kernel<16>): 937.04 MB.
-# Valid only while that kernel is unchanged and the autotuner picks it.
-TRAFFIC_PER_SYSTEM = {3: 937.043e6 / 500_000}
+# workload in launch configuration 12 (analyze_reg1_kernel<16> pulling from
+# the work queue): 956.51 MB.  Valid only while that kernel is unchanged and
+# the autotuner picks it.
+TRAFFIC_PER_SYSTEM = {12: 956.513792e6 / 500_000}
 # Executed warp-instructions per system of the same kernel and capture
 # (smsp__inst_executed.sum / 500,000 systems): the instruction-issue side of
 # the kernel, against the issue peak of 152 SMs x 4 schedulers x 1 per clock.
-WARP_INST_PER_SYSTEM = {3: 838.404456e6 / 500_000}
+WARP_INST_PER_SYSTEM = {12: 880.560887e6 / 500_000}
 ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions / s at the 2070 MHz maximum SM clock
 
 

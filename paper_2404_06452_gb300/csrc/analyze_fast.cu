@@ -449,11 +449,11 @@ __global__ void __launch_bounds__(256) analyze_fast_kernel(BatchDev b, AnalysisP
     FastSmem<MAXN> &s = reinterpret_cast<FastSmem<MAXN> *>(smem_raw)[grp];
     const unsigned gmask = group_mask<G>();
     const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
-    for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n_items; i += (int64_t)gridDim.x * groups) {
+    for_each_item<G>(p, n_items, grp, groups, lane, gmask, [&](int64_t i) {
         const int64_t item = list ? (int64_t)list[i] : i;
         fast_system<G, MAXN>(b, p, item, s, lane, gmask, R, st, verdict, big_list, big_count, wide_list,
                              wide_count);
-    }
+    });
 }
 
 template <int G, int MAXN>
@@ -529,9 +529,12 @@ LaunchFn find_variant(int impl, int G, int maxn)
 
 // Candidate launch configurations the autotuner times (first = default).
 const LaunchCfg kLaunchCfgs[] = {
-    {1, 8, 16, 0, 16, 256},  {0, 8, 16, 0, 16, 256},  {0, 16, 32, 0, 16, 256}, {1, 16, 16, 0, 16, 256},
-    {1, 4, 16, 0, 16, 256},  {1, 16, 32, 1, 32, 256}, {1, 32, 32, 1, 32, 256}, {1, 8, 16, 1, 32, 256},
-    {0, 4, 16, 0, 16, 256},  {0, 8, 32, 0, 32, 256},  {1, 16, 32, 0, 16, 256}, {1, 4, 16, 1, 32, 128},
+    {1, 8, 16, 0, 16, 256, 0},  {0, 8, 16, 0, 16, 256, 0},  {0, 16, 32, 0, 16, 256, 0}, {1, 16, 16, 0, 16, 256, 0},
+    {1, 4, 16, 0, 16, 256, 0},  {1, 16, 32, 1, 32, 256, 0}, {1, 32, 32, 1, 32, 256, 0}, {1, 8, 16, 1, 32, 256, 0},
+    {0, 4, 16, 0, 16, 256, 0},  {0, 8, 32, 0, 32, 256, 0},  {1, 16, 32, 0, 16, 256, 0}, {1, 4, 16, 1, 32, 128, 0},
+    // the same shapes pulling from the work queue, 4 items per fetch
+    {1, 16, 16, 0, 16, 256, 4}, {1, 8, 16, 0, 16, 256, 4},  {0, 8, 16, 0, 16, 256, 4},  {1, 16, 32, 1, 32, 256, 4},
+    {1, 32, 32, 1, 32, 256, 4},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
 
@@ -551,16 +554,26 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
         return rc;
     }
     PAAM_CUDA_TRY(cudaMemsetAsync(b->counts, 0, 2 * sizeof(int32_t), stream));
-    int rc = small(b, p, R, status, verdict, nullptr, nullptr, items, cfg.threads, stream);
+    // per pass: its own work-queue counter, or static shares
+    AnalysisParams pm = p, pb = p, pw = p;
+    pm.queue_batch = pb.queue_batch = pw.queue_batch = 0;
+    if (cfg.queue > 0 && b->queue) {
+        PAAM_CUDA_TRY(cudaMemsetAsync(b->queue, 0, 3 * sizeof(unsigned long long), stream));
+        pm.queue = b->queue;
+        pb.queue = b->queue + 1;
+        pw.queue = b->queue + 2;
+        pm.queue_batch = pb.queue_batch = pw.queue_batch = cfg.queue;
+    }
+    int rc = small(b, pm, R, status, verdict, nullptr, nullptr, items, cfg.threads, stream);
     if (rc != PAAM_OK) return rc;
     ++k;
     if (b->max_chains > cfg.maxn_small) {
-        rc = bigfn(b, p, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
+        rc = bigfn(b, pb, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
         if (rc != PAAM_OK) return rc;
         ++k;
     }
     if (!batch_fits_32(b, p)) {
-        rc = paam_launch_wide(b, p, R, status, verdict, b->list_wide, b->counts + 1, items, stream);
+        rc = paam_launch_wide(b, pw, R, status, verdict, b->list_wide, b->counts + 1, items, stream);
         if (rc != PAAM_OK) return rc;
         ++k;
     }

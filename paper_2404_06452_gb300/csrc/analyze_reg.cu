@@ -504,10 +504,10 @@ __device__ __forceinline__ void reg_items(const BatchDev &b, const AnalysisParam
     OwnSmem<G * CPL> &s = reinterpret_cast<OwnSmem<G * CPL> *>(smem_raw)[grp];
     const unsigned gm = rgroup_mask<G>();
     const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
-    for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n_items; i += (int64_t)gridDim.x * groups) {
+    for_each_item<G>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
         const int64_t item = list ? (int64_t)list[i] : i;
         reg_system<G, CPL>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
-    }
+    });
 }
 
 template <int G, int CPL>

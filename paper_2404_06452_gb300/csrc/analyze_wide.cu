@@ -420,10 +420,10 @@ __global__ void __launch_bounds__(256) analyze_wide_kernel(BatchDev b, AnalysisP
     SysSmem<MAXN, NACC> &s = reinterpret_cast<SysSmem<MAXN, NACC> *>(smem_raw)[grp];
     const unsigned gmask = group_mask<G>();
     const int64_t n = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
-    for (int64_t i = (int64_t)blockIdx.x * groups + grp; i < n; i += (int64_t)gridDim.x * groups) {
+    for_each_item<G>(p, n, grp, groups, lane, gmask, [&](int64_t i) {
         const int64_t item = list ? (int64_t)list[i] : i;
         analyze_system<G, MAXN, NACC>(b, p, item, s, lane, gmask, R, st, verdict);
-    }
+    });
 }
 
 } // namespace

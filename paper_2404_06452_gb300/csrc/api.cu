@@ -378,6 +378,7 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
     b->list_wide = (int32_t *)p;
     p += align_up(list_bytes);
     b->counts = (int32_t *)p;
+    b->queue = (unsigned long long *)(b->counts + 8); // inside the 256-byte counts area
     int32_t h_err[4] = {0, 0x7fffffff, 0, 0};
     if (rc == PAAM_OK && b->n_sys > 0) {
         if (cudaMemcpyAsync(ctx->d_err, h_err, sizeof(h_err), cudaMemcpyHostToDevice, stream) != cudaSuccess ||

@@ -221,6 +221,7 @@ extern "C" int paam_rta_analyze_host(paam_ctx *ctx, const paam_systems_view *v, 
     t.list_wide = (int32_t *)p;
     p += align256(list_bytes);
     t.counts = (int32_t *)p;
+    t.queue = (unsigned long long *)(t.counts + 8);
     p += 256;
     char *wdev = p;
     char *whost = (char *)pl->words;

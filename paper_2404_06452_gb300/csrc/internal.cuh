@@ -45,6 +45,12 @@ struct AnalysisParams {
     uint8_t *cand_ok;
     int32_t *first_ok;
     int32_t *err;
+    // Work queue: with queue_batch > 0 a group takes queue_batch consecutive
+    // items at a time from the device counter *queue (zero at launch) instead
+    // of a fixed grid-stride share, so groups that drew small systems take
+    // more; items are still handed out in increasing order.
+    unsigned long long *queue;
+    int32_t queue_batch;
     // Target mode (exact int64 kernel only; the Audsley-style seed): with
     // target set, candidate (system, c) is decided by one chain,
     // target[system * Kc + c] (-1: skip the item): cand_ok receives whether
@@ -62,6 +68,33 @@ __device__ __forceinline__ void item_of(const AnalysisParams &p, int64_t i, int6
     } else {
         sys = i;
         cand = 0;
+    }
+}
+
+// Items [0, n) of a launch for one group: the static grid-stride share, or
+// batches from the work queue (see AnalysisParams), fetched by the group's
+// first lane and broadcast.  One call site of f, so the system body is
+// inlined once.
+template <int G, typename F>
+__device__ __forceinline__ void for_each_item(const AnalysisParams &p, int64_t n, int grp, int groups, int lane,
+                                              unsigned gmask, F &&f)
+{
+    const bool q = p.queue_batch > 0;
+    int64_t i = q ? 0 : (int64_t)blockIdx.x * groups + grp;
+    int64_t end = q ? 0 : n; // the queue starts with an empty batch
+    const int64_t step = q ? 1 : (int64_t)gridDim.x * groups;
+    for (;;) {
+        if (i >= end) {
+            if (!q) break;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(p.queue, (unsigned long long)p.queue_batch);
+            base = __shfl_sync(gmask, base, 0, G);
+            if ((int64_t)base >= n) break;
+            i = (int64_t)base;
+            end = i + p.queue_batch < n ? i + p.queue_batch : n;
+        }
+        f(i);
+        i += step;
     }
 }
 
@@ -120,6 +153,7 @@ struct paam_batch {
     // [1] systems deferred to the exact int64 kernel, both n_sys long; counts
     int32_t *list_big, *list_wide;
     int32_t *counts; // [0] big, [1] wide
+    unsigned long long *queue; // [3] work-queue counters of the three passes (NULL: none)
     void *block;
     size_t block_bytes;
     int cfg_index; // launch configuration (index into kLaunchCfgs)
@@ -180,6 +214,7 @@ inline BatchDev batch_dev(const paam_batch *b)
 // over systems with more chains (table size 64), CTA size.
 struct LaunchCfg {
     int impl_small, g_small, maxn_small, impl_big, g_big, threads;
+    int queue; // 0: static grid-stride shares; > 0: work queue, items per fetch
 };
 
 // Register-table kernels (analyze_reg.cu): G lanes per system, CPL chains per lane.

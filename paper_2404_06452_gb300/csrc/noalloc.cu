@@ -21,7 +21,7 @@ constexpr int kMaxDevices = 64;
 // [2M, 2M + 2) their counts, [2M + 4, 2M + 8) validation words,
 // [2M + 8, 2M + 8 + 2 * ST_COUNT) batch maxima (64-bit, 8-byte aligned)
 constexpr int kM = PAAM_NOALLOC_MAX_SYS;
-constexpr int kWords = 2 * kM + 8 + 2 * ST_COUNT + 6;
+constexpr int kWords = 2 * kM + 8 + 2 * ST_COUNT + 6 + 6; // ... + three 64-bit work-queue counters
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kWords];
 
@@ -107,6 +107,7 @@ extern "C" int paam_rta_analyze_noalloc(const paam_systems_view *v, const paam_a
     b.list_big = d->scratch;
     b.list_wide = d->scratch + kM;
     b.counts = d->scratch + 2 * kM;
+    b.queue = (unsigned long long *)(d->scratch + 2 * kM + 8 + 2 * ST_COUNT + 6);
     int32_t *err = d->scratch + 2 * kM + 4;
     unsigned long long *stats = (unsigned long long *)(d->scratch + 2 * kM + 8);
 

@@ -77,6 +77,7 @@ extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const
     bs.list_wide = (int32_t *)((char *)tmp + list_bytes);
     bs.counts = (int32_t *)((char *)tmp + 2 * list_bytes);
     int32_t *err = bs.counts + 4;
+    bs.queue = (unsigned long long *)(bs.counts + 8); // bytes 32..55 of the 64-byte tail
     bs.graph = nullptr;
 
     int rc = PAAM_OK;
