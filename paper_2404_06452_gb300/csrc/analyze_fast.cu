@@ -535,6 +535,8 @@ const LaunchCfg kLaunchCfgs[] = {
     // the same shapes pulling from the work queue, 4 items per fetch
     {1, 16, 16, 0, 16, 256, 4}, {1, 8, 16, 0, 16, 256, 4},  {0, 8, 16, 0, 16, 256, 4},  {1, 16, 32, 1, 32, 256, 4},
     {1, 32, 32, 1, 32, 256, 4},
+    // the queue shapes again, handing systems out by increasing chain count
+    {1, 16, 16, 0, 16, 256, 4, 1}, {1, 32, 32, 1, 32, 256, 4, 1}, {1, 8, 16, 0, 16, 256, 4, 1},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
 
@@ -557,6 +559,7 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     // per pass: its own work-queue counter, or static shares
     AnalysisParams pm = p, pb = p, pw = p;
     pm.queue_batch = pb.queue_batch = pw.queue_batch = 0;
+    pm.sys_order = pb.sys_order = pw.sys_order = cfg.binned ? b->sys_order : nullptr;
     if (cfg.queue > 0 && b->queue) {
         PAAM_CUDA_TRY(cudaMemsetAsync(b->queue, 0, 3 * sizeof(unsigned long long), stream));
         pm.queue = b->queue;

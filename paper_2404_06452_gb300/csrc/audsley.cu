@@ -142,6 +142,7 @@ extern "C" int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *b, const 
         sub.n_sys = m;
         sub.sys_chain_off = b->sys_chain_off + s0;
         sub.sys_exec_off = b->sys_exec_off + s0;
+        sub.sys_order = nullptr; // the whole batch's order does not index a chunk
         const BatchDev bd = batch_dev(&sub);
         int16_t *rank = ranks_out + s0 * nmax;
         AnalysisParams p = {};

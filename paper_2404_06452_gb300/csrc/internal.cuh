@@ -51,6 +51,10 @@ struct AnalysisParams {
     // more; items are still handed out in increasing order.
     unsigned long long *queue;
     int32_t queue_batch;
+    // Size binning: with sys_order set, the k-th system handed out is
+    // sys_order[k] (systems sorted by chain count), so the groups that share a
+    // warp analyse systems of one size and stay converged longer.
+    const int32_t *sys_order;
     // Target mode (exact int64 kernel only; the Audsley-style seed): with
     // target set, candidate (system, c) is decided by one chain,
     // target[system * Kc + c] (-1: skip the item): cand_ok receives whether
@@ -69,6 +73,7 @@ __device__ __forceinline__ void item_of(const AnalysisParams &p, int64_t i, int6
         sys = i;
         cand = 0;
     }
+    if (p.sys_order) sys = p.sys_order[sys];
 }
 
 // Items [0, n) of a launch for one group: the static grid-stride share, or
@@ -154,6 +159,7 @@ struct paam_batch {
     int32_t *list_big, *list_wide;
     int32_t *counts; // [0] big, [1] wide
     unsigned long long *queue; // [3] work-queue counters of the three passes (NULL: none)
+    int32_t *sys_order;        // [n_sys] systems by increasing chain count (NULL: not built)
     void *block;
     size_t block_bytes;
     int cfg_index; // launch configuration (index into kLaunchCfgs)
@@ -214,8 +220,12 @@ inline BatchDev batch_dev(const paam_batch *b)
 // over systems with more chains (table size 64), CTA size.
 struct LaunchCfg {
     int impl_small, g_small, maxn_small, impl_big, g_big, threads;
-    int queue; // 0: static grid-stride shares; > 0: work queue, items per fetch
+    int queue;  // 0: static grid-stride shares; > 0: work queue, items per fetch
+    int binned; // 1: hand systems out in order of chain count (batch->sys_order)
 };
+
+// Builds b->sys_order (api.cu): a counting sort of the systems by chain count.
+int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, int32_t *scratch, cudaStream_t stream);
 
 // Register-table kernels (analyze_reg.cu): G lanes per system, CPL chains per lane.
 template <int G, int CPL>
