@@ -551,7 +551,15 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     // the safe blocking term needs every segment bound, and several accelerators need
     // per-accelerator tables: both run the int64 kernel for every system
     if (p.blocking_mode == 1 || b->acc) {
-        const int rc = paam_launch_wide(b, p, R, status, verdict, nullptr, nullptr, items, stream);
+        AnalysisParams pw = p; // the configuration's work distribution and order apply here too
+        pw.queue_batch = 0;
+        pw.sys_order = cfg.binned ? b->sys_order : nullptr;
+        if (cfg.queue > 0 && b->queue) {
+            PAAM_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(unsigned long long), stream));
+            pw.queue = b->queue;
+            pw.queue_batch = cfg.queue;
+        }
+        const int rc = paam_launch_wide(b, pw, R, status, verdict, nullptr, nullptr, items, stream);
         if (n_kernels) *n_kernels = 1;
         return rc;
     }
