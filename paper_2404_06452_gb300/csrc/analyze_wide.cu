@@ -329,10 +329,12 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
             const int64_t dc = s.delta[c];
             const int64_t deps = dc * eps;
             int64_t own[NACC], h0 = 0;
+            bool uses[NACC]; // accelerators chain c requests (the same in every lane of the group)
 #pragma unroll
             for (int a = 0; a < NACC; ++a) {
+                uses[a] = s.dA[c][a] > 0;
                 own[a] = s.S[c][a] + (int64_t)s.dA[c][a] * s.blk[c][a];
-                if (s.dA[c][a] > 0) h0 += s.Hseg[c][a] < own[a] ? s.Hseg[c][a] : own[a];
+                if (uses[a]) h0 += s.Hseg[c][a] < own[a] ? s.Hseg[c][a] : own[a];
             }
             // start: B + E + H* with the interference parts of Eq. 4 empty
             int64_t Rc = Bc + Ec + (dc > 0 ? h0 + deps : 0);
@@ -353,14 +355,14 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
                     if (s.prio[h] > pc)
 #pragma unroll
                         for (int a = 0; a < NACC; ++a)
-                            if (s.dA[h][a] > 0) acc[a] += m * s.S[h][a]; // Eq. 4 at accelerator a
+                            if (uses[a] && s.dA[h][a] > 0) acc[a] += m * s.S[h][a]; // Eq. 4 at accelerator a
                 }
                 cpu = group_sum<G>(cpu, gmask);
                 int64_t hs = 0;
 #pragma unroll
                 for (int a = 0; a < NACC; ++a) {
-                    acc[a] = group_sum<G>(acc[a], gmask);
-                    if (s.dA[c][a] > 0) { // Eq. 1 with min(Eq. 3, Eq. 4), summed over accelerators (R1)
+                    if (uses[a]) { // Eq. 1 with min(Eq. 3, Eq. 4), summed over accelerators (R1)
+                        acc[a] = group_sum<G>(acc[a], gmask);
                         const int64_t hch = own[a] + acc[a];
                         hs += s.Hseg[c][a] < hch ? s.Hseg[c][a] : hch;
                     }
@@ -468,6 +470,11 @@ int paam_launch_wide(const paam_batch *bt, const AnalysisParams &p, int64_t *R, 
                      uint8_t *verdict, const int32_t *list, const int32_t *count, int64_t max_items,
                      cudaStream_t stream)
 {
-    if (bt->acc) return launch_wide_n<PAAM_MAX_ACC>(bt, p, R, st, verdict, list, count, max_items, stream);
+    // tables for as many accelerators as the batch uses (validation recorded the largest index)
+    const unsigned long long used = bt->acc ? bt->stats[ST_ACCMAX] + 1 : 1;
+    static_assert(PAAM_MAX_ACC == 4, "instantiations below cover 1..4 accelerators");
+    if (used >= 4) return launch_wide_n<4>(bt, p, R, st, verdict, list, count, max_items, stream);
+    if (used == 3) return launch_wide_n<3>(bt, p, R, st, verdict, list, count, max_items, stream);
+    if (used == 2) return launch_wide_n<2>(bt, p, R, st, verdict, list, count, max_items, stream);
     return launch_wide_n<1>(bt, p, R, st, verdict, list, count, max_items, stream);
 }
