@@ -7,7 +7,7 @@
 
 // Epilogue applied to each fp32 accumulator tile of the tensor-core GEMM.
 enum TcEpiMode {
-    TC_EPI_STORE_F32 = 0,  // C = acc
+    TC_EPI_STORE_F32 = 0,  // C = acc (with split_stride: split z writes C + z * split_stride)
     TC_EPI_BIAS_GELU = 1,  // Z = bf16(acc + bias); H = bf16(gelu(Z)); HT = H^T (optional)
     TC_EPI_BIAS_F32 = 2,   // C = acc + bias
     TC_EPI_DGELU = 3,      // H = bf16(acc * gelu'(Zin)); HT = H^T (optional)
@@ -34,13 +34,19 @@ struct TcEpilogue {
     const int64_t *sys_off;
     int64_t sys0;
     int rows_per_sys;
+    // TC_EPI_STORE_F32 with splits > 1: each split stores its partial product
+    // into its own [M][ldc] slice, C + split * split_stride (summed afterwards
+    // in a fixed order, so the result does not depend on scheduling)
+    int64_t split_stride;
 };
 
 // C[M, N] (epilogue) = A[M, K] * B[N, K]^T with A, B bf16 row-major, lda/ldb in
 // elements; a_rows / b_rows are the allocated rows of A and B (tiles past them
 // read zeros).  K must be a multiple of 64, lda and ldb multiples of 8, the
 // output N a multiple of 64.  splits > 1 divides K over grid z and needs
-// TC_EPI_ATOMIC_F32.  err receives PAAM_E_TIMEOUT if a bounded wait expired.
+// TC_EPI_ATOMIC_F32, or TC_EPI_STORE_F32 with a split_stride.  bn (0: chosen
+// from N) asks for a column-tile width of 64, 128 or 256 dividing N.  err
+// receives PAAM_E_TIMEOUT if a bounded wait expired.
 struct TcGemm {
     const __nv_bfloat16 *A;
     int lda, a_rows;
@@ -48,6 +54,7 @@ struct TcGemm {
     int ldb, b_rows;
     int K, splits;
     TcEpilogue ep;
+    int bn;
 };
 
 int tc_gemm(const TcGemm &g, int32_t *err, cudaStream_t stream);

@@ -265,12 +265,14 @@ __global__ void __launch_bounds__(kGemmThreads, 2) tc_gemm_kernel(const __grid_c
         }
         tc::fence_after_sync();
         if (ok) {
+            TcEpilogue e = ep; // a split of a split-K product stores into its own slice
+            if (ep.split_stride) e.C = ep.C + (int64_t)blockIdx.z * ep.split_stride;
 #pragma unroll 1
             for (int c = half * (BN / 64); c < (half + 1) * (BN / 64); ++c) {
                 uint32_t v[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * c), v);
                 tc::tmem_wait_ld();
-                epilogue_chunk(ep, row, n0 + 32 * c, v);
+                epilogue_chunk(e, row, n0 + 32 * c, v);
             }
         }
         tc::fence_before_sync();
@@ -624,7 +626,12 @@ int launch_persistent(const TcGemm &g, int32_t *err, cudaStream_t stream)
 int tc_gemm(const TcGemm &g, int32_t *err, cudaStream_t stream)
 {
     if (g.K <= 0 || g.K % BK || g.lda % 8 || g.ldb % 8 || g.ep.N % 64 || g.ep.M <= 0) return PAAM_E_INVAL;
-    if (g.splits > 1 && g.ep.mode != TC_EPI_ATOMIC_F32) return PAAM_E_INVAL;
+    if (g.splits > 1 && g.ep.mode != TC_EPI_ATOMIC_F32 && !(g.ep.mode == TC_EPI_STORE_F32 && g.ep.split_stride > 0))
+        return PAAM_E_INVAL;
+    if (g.ep.split_stride && (g.ep.mode != TC_EPI_STORE_F32 || g.splits < 1)) return PAAM_E_INVAL;
+    if (g.bn && ((g.bn != 64 && g.bn != 128 && g.bn != 256) || g.ep.N % g.bn)) return PAAM_E_INVAL;
+    if (g.bn == 64) return launch_bn_depth<64>(g, err, stream);
+    if (g.bn == 128) return launch_bn_depth<128>(g, err, stream);
     // one column tile, short K, many row tiles: weights stay resident, epilogue overlaps MMA
     if (g.splits <= 1 && g.K <= 256 && g.b_rows == g.ep.N && g.ep.M >= 4 * BM * sm_count()) {
         if (g.ep.N == 256) return launch_persistent<256>(g, err, stream);

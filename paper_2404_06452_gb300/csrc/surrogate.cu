@@ -59,19 +59,17 @@ __global__ void labels_kernel(BatchDev b, const int64_t *R, const uint8_t *statu
     }
 }
 
-// ---- minibatch gather: rows idx[r] (-1 = padding) of X, L into Xb, XbT, Lb;
-// counts the valid labels into *count
+// ---- minibatch gather: rows idx[r] (-1 = padding) of X, L into Xb, Lb (16
+// bytes per thread and load); counts the valid labels into *count
 __global__ void gather_kernel(const __nv_bfloat16 *X, const float *L, const int64_t *idx, int rows,
-                              __nv_bfloat16 *Xb, __nv_bfloat16 *XbT, float *Lb, float *count)
+                              __nv_bfloat16 *Xb, float *Lb, float *count)
 {
     const int r = blockIdx.x;
     if (r >= rows) return;
     const int64_t src = idx[r];
-    for (int k = threadIdx.x; k < XW; k += blockDim.x) {
-        const __nv_bfloat16 v = src >= 0 ? X[src * XW + k] : __float2bfloat16_rn(0.0f);
-        Xb[(int64_t)r * XW + k] = v;
-        XbT[(int64_t)k * rows + r] = v;
-    }
+    const uint4 *x4 = reinterpret_cast<const uint4 *>(X + (src >= 0 ? src : 0) * XW);
+    uint4 *o4 = reinterpret_cast<uint4 *>(Xb + (int64_t)r * XW);
+    for (int k = threadIdx.x; k < XW / 8; k += blockDim.x) o4[k] = src >= 0 ? x4[k] : make_uint4(0, 0, 0, 0);
     float cnt = 0.0f;
     for (int c = threadIdx.x; c < NCH; c += blockDim.x) {
         const float y = src >= 0 ? L[src * NCH + c] : -1.0f;
@@ -84,7 +82,7 @@ __global__ void gather_kernel(const __nv_bfloat16 *X, const float *L, const int6
 
 // ---- masked mean-squared error and its gradient
 __global__ void loss_kernel(const float *Y, const float *Lb, int rows, const float *count, __nv_bfloat16 *dY,
-                            __nv_bfloat16 *dYT, float *loss_sum)
+                            float *loss_sum)
 {
     const float inv = 1.0f / fmaxf(*count, 1.0f);
     float acc = 0.0f;
@@ -94,22 +92,39 @@ __global__ void loss_kernel(const float *Y, const float *Lb, int rows, const flo
         const float y = Lb[i];
         const float d = y >= 0.0f ? Y[i] - y : 0.0f;
         acc += d * d;
-        const __nv_bfloat16 g = __float2bfloat16_rn(2.0f * d * inv);
-        const int64_t r = i / NCH, c = i % NCH;
-        dY[i] = g;
-        dYT[c * rows + r] = g;
+        dY[i] = __float2bfloat16_rn(2.0f * d * inv);
     }
+    // one atomic per block: warp sums, then the block's warps
+    __shared__ float part[32];
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, acc * inv);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(loss_sum, t * inv);
+    }
 }
 
-// ---- bias gradients: row sums of a [rows][cols] bf16 matrix (one block per row)
+// ---- bias gradients: row sums of a [rows][cols] bf16 matrix (one block per
+// row; cols a multiple of 8; eight values per 16-byte load, four loads in
+// flight per thread)
 __global__ void rowsum_kernel(const __nv_bfloat16 *A, int cols, float *out)
 {
     __shared__ float part[8];
     float acc = 0.0f;
-    const __nv_bfloat16 *a = A + (int64_t)blockIdx.x * cols;
-    for (int k = threadIdx.x; k < cols; k += blockDim.x) acc += __bfloat162float(a[k]);
+    const uint4 *a = reinterpret_cast<const uint4 *>(A + (int64_t)blockIdx.x * cols);
+    const int n8 = cols / 8;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < n8; k += blockDim.x) {
+        const uint4 v = a[k];
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = __bfloat1622float2(h[i]);
+            acc += f.x + f.y;
+        }
+    }
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -120,26 +135,68 @@ __global__ void rowsum_kernel(const __nv_bfloat16 *A, int cols, float *out)
     }
 }
 
-// ---- AdamW (decoupled weight decay on weights only); refreshes the bf16 copies
-__global__ void adamw_kernel(float *W, float *m, float *v, float *g, int64_t n, int rows, int cols, float lr,
-                             float b1, float b2, float eps, float wd, float c1, float c2, __nv_bfloat16 *Wb,
-                             __nv_bfloat16 *WbT)
+// ---- out[c][r] = in[r][c] for a [rows][cols] bf16 matrix, through 32 x 32
+// shared-memory tiles (coalesced reads and writes); blocks of 32 x 8 threads
+__global__ void transpose_kernel(const __nv_bfloat16 *in, int rows, int cols, __nv_bfloat16 *out)
+{
+    __shared__ unsigned short t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const unsigned short *src = reinterpret_cast<const unsigned short *>(in);
+    unsigned short *dst = reinterpret_cast<unsigned short *>(out);
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[i][threadIdx.x] = src[(int64_t)r * cols + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[(int64_t)c * rows + r] = t[threadIdx.x][i];
+    }
+}
+
+// ---- g[i] += sum over the split slices of part[z][i], in split order
+__global__ void splitk_reduce_kernel(const float *part, int64_t n, int z, float *g)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.0f - b1) * gi;
-        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        float w = W[i];
-        w -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w);
-        W[i] = w;
-        g[i] = 0.0f;
-        if (Wb) {
+        float acc = 0.0f;
+        for (int k = 0; k < z; ++k) acc += part[(int64_t)k * n + i];
+        g[i] += acc;
+    }
+}
+
+// ---- AdamW (decoupled weight decay on weights only); refreshes the bf16 copies
+// All of a model's parameter blocks in one AdamW launch: block k covers
+// indices [off[k], off[k + 1]) of the concatenation.
+struct AdamSegs {
+    float *W[8], *m[8], *v[8], *g[8];
+    __nv_bfloat16 *Wb[8], *WbT[8];
+    int64_t off[9];
+    int rows[8], cols[8];
+    float wd[8];
+    int n;
+};
+
+__global__ void adamw_all_kernel(AdamSegs a, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.off[a.n]; t += stride) {
+        int k = 0;
+        while (k + 1 < a.n && t >= a.off[k + 1]) ++k;
+        const int64_t i = t - a.off[k];
+        const float gi = a.g[k][i];
+        const float mi = b1 * a.m[k][i] + (1.0f - b1) * gi;
+        const float vi = b2 * a.v[k][i] + (1.0f - b2) * gi * gi;
+        a.m[k][i] = mi;
+        a.v[k][i] = vi;
+        float w = a.W[k][i];
+        w -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + a.wd[k] * w);
+        a.W[k][i] = w;
+        a.g[k][i] = 0.0f;
+        if (a.Wb[k]) {
             const __nv_bfloat16 wb = __float2bfloat16_rn(w);
-            Wb[i] = wb;
-            if (WbT) WbT[(i % cols) * rows + i / cols] = wb;
+            a.Wb[k][i] = wb;
+            if (a.WbT[k]) a.WbT[k][(i % a.cols[k]) * a.rows[k] + i / a.cols[k]] = wb;
         }
     }
 }
@@ -356,18 +413,55 @@ struct Work {
     void *block;
     __nv_bfloat16 *Xb, *XbT, *Z[3], *H[3], *HT[3], *dY, *dYT, *dZ[3], *dZT[3];
     float *Lb, *Y, *count, *loss;
+    float *part; // split-K slices of a weight gradient (training)
     int32_t *err;
 };
 
+// Weight-gradient GEMMs dW = dT x in^T contract over the minibatch rows: K is
+// split so that the tiles times the splits cover the SMs about once, with at
+// least two 64-row steps per split; each split stores its own slice and the
+// slices are summed in order (deterministic, no atomics).
+struct DwPlan {
+    int bn, splits, z; // column tile, splits asked for, slices the launch writes
+};
+
+DwPlan dw_plan(int out, int in, int rows, int n_sm)
+{
+    DwPlan d;
+    d.bn = in >= 1024 ? 256 : 64;
+    const int tiles = ((out + 127) / 128) * (in / d.bn);
+    const int kb = rows / 64;
+    int sp = n_sm / tiles;
+    if (sp > kb / 2) sp = kb / 2;
+    if (sp < 1) sp = 1;
+    d.splits = sp;
+    const int per = (kb + sp - 1) / sp;
+    d.z = (kb + per - 1) / per;
+    return d;
+}
+
+size_t dw_part_floats(int rows, int n_sm)
+{
+    size_t m = 0;
+    for (int l = 0; l < 4; ++l) {
+        const int out = l == 3 ? 64 : 256, in = l == 0 ? XW : 256;
+        const DwPlan d = dw_plan(out, in, rows, n_sm);
+        const size_t f = (size_t)d.z * out * in;
+        m = f > m ? f : m;
+    }
+    return m;
+}
+
 // xw: columns of the input buffer Xb (the full 1024 for training; inference
 // stores only the columns its batch can fill)
-int work_alloc(Work &w, int rows, bool train, cudaStream_t s, int xw = XW)
+int work_alloc(Work &w, int rows, bool train, cudaStream_t s, int xw = XW, int n_sm = 0)
 {
     w = Work{};
     w.rows = rows;
     const size_t r = (size_t)rows;
+    const size_t part = train ? 4 * dw_part_floats(rows, n_sm > 0 ? n_sm : 1) : 0;
     size_t bytes = 2 * r * xw * (train ? 2 : 1) + 3 * 2 * r * 256 * (train ? 6 : 1) + 4 * r * 64 * (train ? 2 : 1) +
-                   2 * 2 * r * 64 + 64 * 256;
+                   2 * 2 * r * 64 + 64 * 256 + part + 256;
     if (cudaMallocAsync(&w.block, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return PAAM_E_NOMEM;
@@ -395,10 +489,21 @@ int work_alloc(Work &w, int rows, bool train, cudaStream_t s, int xw = XW)
         w.dY = (__nv_bfloat16 *)take(2 * r * 64);
         w.dYT = (__nv_bfloat16 *)take(2 * r * 64);
     }
+    if (train) w.part = (float *)take(part);
     w.count = (float *)take(4);
     w.loss = (float *)take(4);
     w.err = (int32_t *)take(4);
     return PAAM_OK;
+}
+
+// Column tile for a minibatch GEMM: the widest that still gives every SM a
+// tile (minibatches of a few thousand rows have few row tiles).
+int bn_for(int M, int N, int n_sm)
+{
+    const int mt = (M + 127) / 128;
+    for (int bn = 256; bn >= 64; bn /= 2)
+        if (N % bn == 0 && mt * (N / bn) >= n_sm) return bn;
+    return 64;
 }
 
 TcGemm gemm(const __nv_bfloat16 *A, int lda, int a_rows, const __nv_bfloat16 *B, int ldb, int b_rows, int K)
@@ -455,6 +560,7 @@ int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool t
         g.ep.ldh = OUT[l];
         g.ep.HT = train ? w.HT[l] : nullptr;
         g.ep.ldht = rows;
+        if (train) g.bn = bn_for(rows, OUT[l], m->ctx->n_sm);
         int rc = tc_gemm(g, w.err, s);
         if (rc != PAAM_OK) return rc;
     }
@@ -465,6 +571,7 @@ int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool t
     g.ep.bias = m->bias[3];
     g.ep.C = w.Y;
     g.ep.ldc = OUT[3];
+    if (train) g.bn = bn_for(rows, OUT[3], m->ctx->n_sm);
     if (so) {
         PAAM_CUDA_TRY(cudaMemsetAsync(so->score, 0, 4 * (size_t)rows, s));
         g.ep.mode = TC_EPI_ROWMAX;
@@ -476,39 +583,36 @@ int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool t
     return tc_gemm(g, w.err, s);
 }
 
-int splits_for(int tiles, int kb, int n_sm)
-{
-    int sp = (2 * n_sm + tiles - 1) / tiles;
-    if (sp > kb) sp = kb;
-    return sp < 1 ? 1 : sp;
-}
-
 // gradients of the masked MSE into m->gW, m->gb (accumulated)
 int backward(paam_model *m, Work &w, cudaStream_t s)
 {
-    const int rows = w.rows, kb = rows / 64, sm = m->ctx->n_sm;
-    loss_kernel<<<grid_for((int64_t)rows * 64, 256, sm), 256, 0, s>>>(w.Y, w.Lb, rows, w.count, w.dY, w.dYT,
-                                                                       w.loss);
+    const int rows = w.rows, sm = m->ctx->n_sm;
+    loss_kernel<<<grid_for((int64_t)rows * 64, 256, sm), 256, 0, s>>>(w.Y, w.Lb, rows, w.count, w.dY, w.loss);
+    transpose_kernel<<<dim3(NCH / 32, (rows + 31) / 32), dim3(32, 8), 0, s>>>(w.dY, rows, NCH, w.dYT);
     PAAM_CUDA_TRY(cudaGetLastError());
-    paam_count_launch();
+    paam_count_launch(2);
     // output layer: dW4 = dY^T H3, db4 = column sums of dY, dH3 = dY W4 (then the GELU derivative)
     const __nv_bfloat16 *dT = w.dYT; // [OUT[l]][rows]
     const __nv_bfloat16 *d = w.dY;   // [rows][OUT[l]]
     for (int l = 3; l >= 0; --l) {
         const __nv_bfloat16 *inT = l == 0 ? w.XbT : w.HT[l - 1];
         TcGemm g = gemm(dT, rows, OUT[l], inT, rows, IN[l], rows);
-        g.ep.mode = TC_EPI_ATOMIC_F32;
+        const DwPlan dp = dw_plan(OUT[l], IN[l], rows, sm);
+        g.ep.mode = TC_EPI_STORE_F32;
         g.ep.M = OUT[l];
         g.ep.N = IN[l];
-        g.ep.C = m->gW[l];
+        g.ep.C = w.part;
         g.ep.ldc = IN[l];
-        const int tiles = ((OUT[l] + 127) / 128) * (IN[l] % 256 == 0 ? IN[l] / 256 : IN[l] / 64);
-        g.splits = splits_for(tiles, kb, sm);
+        g.ep.split_stride = (int64_t)OUT[l] * IN[l];
+        g.splits = dp.splits;
+        g.bn = dp.bn;
         int rc = tc_gemm(g, w.err, s);
         if (rc != PAAM_OK) return rc;
+        const int64_t nw = (int64_t)OUT[l] * IN[l];
+        splitk_reduce_kernel<<<grid_for(nw, 256, sm), 256, 0, s>>>(w.part, nw, dp.z, m->gW[l]);
         rowsum_kernel<<<OUT[l], 256, 0, s>>>(dT, rows, m->gb[l]);
         PAAM_CUDA_TRY(cudaGetLastError());
-        paam_count_launch();
+        paam_count_launch(2);
         if (l == 0) break;
         TcGemm h = gemm(d, OUT[l], rows, m->WbT[l], OUT[l], IN[l], OUT[l]);
         h.ep.mode = TC_EPI_DGELU;
@@ -520,6 +624,7 @@ int backward(paam_model *m, Work &w, cudaStream_t s)
         h.ep.ldh = IN[l];
         h.ep.HT = w.dZT[l - 1];
         h.ep.ldht = rows;
+        h.bn = bn_for(rows, IN[l], sm);
         rc = tc_gemm(h, w.err, s);
         if (rc != PAAM_OK) return rc;
         dT = w.dZT[l - 1];
@@ -532,16 +637,25 @@ int adamw(paam_model *m, const paam_train_opts *o, cudaStream_t s)
 {
     m->step += 1;
     const float c1 = 1.0f - powf(o->beta1, (float)m->step), c2 = 1.0f - powf(o->beta2, (float)m->step);
+    AdamSegs a = {};
+    a.n = 2 * NL;
+    int64_t off = 0;
     for (int l = 0; l < NL; ++l) {
-        const int64_t nw = (int64_t)IN[l] * OUT[l];
-        adamw_kernel<<<grid_for(nw, 256, m->ctx->n_sm), 256, 0, s>>>(
-            m->W[l], m->mW[l], m->vW[l], m->gW[l], nw, OUT[l], IN[l], o->lr, o->beta1, o->beta2, o->adam_eps,
-            o->weight_decay, c1, c2, m->Wb[l], m->WbT[l]);
-        adamw_kernel<<<1, 256, 0, s>>>(m->bias[l], m->mb[l], m->vb[l], m->gb[l], OUT[l], 1, OUT[l], o->lr, o->beta1,
-                                       o->beta2, o->adam_eps, 0.0f, c1, c2, nullptr, nullptr);
-        PAAM_CUDA_TRY(cudaGetLastError());
+        const int w = 2 * l, b = 2 * l + 1; // the weights (decayed), then the biases (not decayed)
+        a.W[w] = m->W[l], a.m[w] = m->mW[l], a.v[w] = m->vW[l], a.g[w] = m->gW[l];
+        a.Wb[w] = m->Wb[l], a.WbT[w] = m->WbT[l], a.rows[w] = OUT[l], a.cols[w] = IN[l], a.wd[w] = o->weight_decay;
+        a.off[w] = off;
+        off += (int64_t)IN[l] * OUT[l];
+        a.W[b] = m->bias[l], a.m[b] = m->mb[l], a.v[b] = m->vb[l], a.g[b] = m->gb[l];
+        a.Wb[b] = nullptr, a.WbT[b] = nullptr, a.rows[b] = 1, a.cols[b] = OUT[l], a.wd[b] = 0.0f;
+        a.off[b] = off;
+        off += OUT[l];
     }
-    paam_count_launch(2 * NL);
+    a.off[2 * NL] = off;
+    adamw_all_kernel<<<grid_for(off, 256, m->ctx->n_sm), 256, 0, s>>>(a, o->lr, o->beta1, o->beta2, o->adam_eps, c1,
+                                                                      c2);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    paam_count_launch();
     return PAAM_OK;
 }
 
@@ -584,7 +698,7 @@ extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const in
         cudaGetLastError();
         rc = PAAM_E_NOMEM;
     }
-    if (rc == PAAM_OK) rc = work_alloc(w, rows, true, s);
+    if (rc == PAAM_OK) rc = work_alloc(w, rows, true, s, XW, ctx->n_sm);
     __nv_bfloat16 *X = (__nv_bfloat16 *)data;
     float *L = (float *)((char *)data + (size_t)n * 2 * XW);
     int64_t *idx_dev = (int64_t *)((char *)L + (size_t)n * 4 * NCH);
@@ -611,9 +725,10 @@ extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const in
             rc = PAAM_E_CUDA;
         for (int64_t st = 0; st < steps && rc == PAAM_OK; ++st) {
             if (cudaMemsetAsync(w.count, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
-            gather_kernel<<<rows, 128, 0, s>>>(X, L, idx_dev + st * rows, rows, w.Xb, w.XbT, w.Lb, w.count);
+            gather_kernel<<<rows, 128, 0, s>>>(X, L, idx_dev + st * rows, rows, w.Xb, w.Lb, w.count);
+            transpose_kernel<<<dim3(XW / 32, rows / 32), dim3(32, 8), 0, s>>>(w.Xb, rows, XW, w.XbT);
             if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-            paam_count_launch();
+            paam_count_launch(2);
             if (rc == PAAM_OK) rc = forward(m, w, w.Xb, XW, true, s);
             if (rc == PAAM_OK) rc = backward(m, w, s);
             if (rc == PAAM_OK) rc = adamw(m, o, s);
@@ -741,7 +856,7 @@ extern "C" int paam_surrogate_grad(paam_ctx *ctx, paam_model *m, const void *X, 
     PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->capture_stream;
     Work w;
-    int rc = work_alloc(w, rows, true, s);
+    int rc = work_alloc(w, rows, true, s, XW, ctx->n_sm);
     if (rc != PAAM_OK) return rc;
     int64_t *idx = nullptr;
     if (cudaMallocAsync((void **)&idx, 8 * (size_t)rows, s) != cudaSuccess) {
@@ -760,9 +875,10 @@ extern "C" int paam_surrogate_grad(paam_ctx *ctx, paam_model *m, const void *X, 
             cudaMemsetAsync(m->gb[l], 0, 4 * (size_t)OUT[l], s) != cudaSuccess)
             rc = PAAM_E_CUDA;
     if (rc == PAAM_OK) {
-        gather_kernel<<<rows, 128, 0, s>>>((const __nv_bfloat16 *)X, L, idx, rows, w.Xb, w.XbT, w.Lb, w.count);
+        gather_kernel<<<rows, 128, 0, s>>>((const __nv_bfloat16 *)X, L, idx, rows, w.Xb, w.Lb, w.count);
+        transpose_kernel<<<dim3(XW / 32, rows / 32), dim3(32, 8), 0, s>>>(w.Xb, rows, XW, w.XbT);
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-        paam_count_launch();
+        paam_count_launch(2);
     }
     if (rc == PAAM_OK) rc = forward(m, w, w.Xb, XW, true, s);
     if (rc == PAAM_OK) rc = backward(m, w, s);

@@ -278,6 +278,28 @@ def test_training_reduces_loss_and_predicts():
     b.free()
 
 
+def test_training_is_bit_reproducible():
+    """The weight gradients are split over the minibatch rows into slices
+    summed in a fixed order, so two trainings with the same seed and data give
+    the same parameters bit for bit."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    sy = g.generate("cfg2", n_sys=40_000)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    R, st, _ = pkg.analyze(ctx(), b)
+    torch.cuda.synchronize()
+    params = []
+    for _ in range(2):
+        m = pkg.paam_surrogate_train(ctx(), b, R, st, pkg.train_opts(epochs=2, batch_rows=4096, lr=2e-3, seed=9),
+                                     None)
+        params.append(m.get_params())
+        m.free()
+    b.free()
+    assert np.array_equal(params[0].view(np.uint32), params[1].view(np.uint32))
+
+
 def test_infer_ranks_by_score_and_guided_search_is_exact():
     import torch
 
