@@ -274,8 +274,11 @@ def search_bench(pkg, ctx, n_sys):
         sy = paam_gen.generate(cfg, n_sys=n_sys)
         b = pkg.paam_rta_load_systems(ctx, sy)
         r, t_seed = search_candidates(pkg, ctx, sy, b, cfg)
+        # each mode in the launch shape the search autotuner picks for it
+        cfg_x, _ = pkg.paam_rta_autotune_search(ctx, b, pkg.analysis_opts(), r)
         pkg.search(ctx, b, r)  # warm-up
         t_x, (first, cand) = _timed(lambda: pkg.search(ctx, b, r), 3)
+        cfg_e, _ = pkg.paam_rta_autotune_search(ctx, b, pkg.analysis_opts(), r, stop_at_first=True)
         t_e, (first_e, _) = _timed(lambda: pkg.search(ctx, b, r, stop_at_first=True, want_cand_ok=False), 3)
         cand_np = cand.cpu().numpy()
         assert np.array_equal(first.cpu().numpy(), first_e.cpu().numpy())
@@ -286,6 +289,7 @@ def search_bench(pkg, ctx, n_sys):
             "candidate_analyses_per_s": sy.n_sys * SEARCH_K / t_x,
             "systems_with_schedulable_order": float((first.cpu().numpy() >= 0).mean()),
             "schedulable_candidates": float(cand_np.mean()),
+            "launch_config": {"exhaustive": cfg_x, "early_exit": cfg_e},
             "audsley_seed_ms": t_seed * 1e3,
             "audsley_seed_admitted": float(cand_np[:, 0].mean()),
             "deadline_monotonic_admitted": float(cand_np[:, 1].mean()),
@@ -367,9 +371,13 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
     b = pkg.paam_rta_load_systems(ctx, sy)
     r, _ = search_candidates(pkg, ctx, sy, b, "cfg4s")
     opts = pkg.analysis_opts()
+    # the plain searches, each in the launch shape the search autotuner picks for it
+    pkg.paam_rta_autotune_search(ctx, b, opts, r, stop_at_first=True)
+    pkg.search(ctx, b, r, stop_at_first=True, want_cand_ok=False)
+    t_ee, _ = _timed(lambda: pkg.search(ctx, b, r, stop_at_first=True, want_cand_ok=False), 3)
+    pkg.paam_rta_autotune_search(ctx, b, opts, r)
     pkg.search(ctx, b, r)
     t_ex, (first_x, cand_x) = _timed(lambda: pkg.search(ctx, b, r), 3)
-    t_ee, _ = _timed(lambda: pkg.search(ctx, b, r, stop_at_first=True, want_cand_ok=False), 3)
     S = sy.n_sys
     order_k = torch.empty((S, top_k), dtype=torch.int32, device="cuda")
     order_all = torch.empty((S, K), dtype=torch.int32, device="cuda")

@@ -416,8 +416,10 @@ int paam_measure_preemption(int device, int kind, int iters, float *delay_us, fl
 /*
  * Launch configurations.  The analysis has several built-in launch
  * configurations (lanes per system, chain-table size of the first pass, lanes
- * per system for systems with more chains, CTA size); every one produces
- * bit-identical results.  A batch starts with configuration 0.
+ * per system for systems with more chains, CTA size, static shares or a
+ * device work queue, index or size order of the systems); every one produces
+ * bit-identical results.  A batch starts with configuration 12 (16 lanes per
+ * system, work queue).
  *
  * paam_rta_autotune times every configuration on the batch itself (the
  * analysis is run 6 times per configuration, the first run discarded, and
@@ -430,6 +432,18 @@ int paam_measure_preemption(int device, int kind, int iters, float *delay_us, fl
 int paam_rta_num_launch_configs(void);
 int paam_rta_autotune(paam_ctx *ctx, paam_batch *batch, const paam_analysis_opts *opts, void *stream,
                       float *times_ms, int max_out);
+
+/*
+ * paam_rta_autotune_search: the same for the priority search.  Every
+ * configuration runs paam_rta_search_priorities on `ranks` (layout as
+ * there; 6 runs, the first discarded, the median of 5 kept, timed on the host
+ * around each call), and the fastest is kept on the batch for later analyses
+ * and searches.  Returns its index or a negative error; times_ms as above.
+ * Synchronises `stream`.
+ */
+int paam_rta_autotune_search(paam_ctx *ctx, paam_batch *batch, const paam_analysis_opts *opts, const int16_t *ranks,
+                             int32_t K, int32_t nmax, int32_t stop_at_first, void *stream, float *times_ms,
+                             int max_out);
 int paam_rta_set_launch_config(paam_batch *batch, int index); /* PAAM_E_INVAL if out of range */
 int paam_rta_get_launch_config(const paam_batch *batch);
 

@@ -116,6 +116,9 @@ def lib():
                                                           _c_void_p, _c_void_p, _c_void_p]),
             "paam_rta_audsley_order": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), ctypes.c_int32,
                                                       _c_void_p, _c_void_p]),
+            "paam_rta_autotune_search": (ctypes.c_int, [_c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
+                                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _c_void_p,
+                                                        _c_void_p, ctypes.c_int]),
             "paam_rta_analyze_host": (ctypes.c_int, [_c_void_p, P(SystemsView), P(AnalysisOpts), ctypes.c_int32,
                                                      ctypes.c_int64, _c_void_p, _c_void_p, _c_void_p]),
         }
@@ -136,7 +139,8 @@ def exported_symbols() -> list:
             "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
             "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
             "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_rta_end_to_end",
-            "paam_measure_preemption", "paam_rta_audsley_order", "paam_rta_analyze_host"]
+            "paam_measure_preemption", "paam_rta_audsley_order", "paam_rta_analyze_host",
+            "paam_rta_autotune_search"]
 
 
 def launch_count() -> int:
@@ -315,6 +319,19 @@ def paam_rta_search_priorities(ctx: Context, batch: Batch, opts: AnalysisOpts, r
     _check(lib().paam_rta_search_priorities(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(ranks), int(K),
                                             int(nmax), 1 if stop_at_first else 0, _ptr(cand_ok), _ptr(first_ok),
                                             _stream_ptr(stream)), "paam_rta_search_priorities")
+
+
+def paam_rta_autotune_search(ctx: Context, batch: Batch, opts: AnalysisOpts, ranks, stop_at_first: bool = False,
+                             stream=None) -> tuple:
+    """Time every launch configuration on the search over ``ranks`` ([S, K,
+    nmax] int16 device tensor); keep the fastest.  Returns (index, ms list)."""
+    S, K, nmax = ranks.shape
+    n = paam_rta_num_launch_configs()
+    times = (ctypes.c_float * n)()
+    rc = lib().paam_rta_autotune_search(ctx.handle, batch.handle, ctypes.byref(opts), _ptr(ranks), int(K), int(nmax),
+                                        1 if stop_at_first else 0, _stream_ptr(stream), times, n)
+    _check(min(rc, 0), "paam_rta_autotune_search")
+    return rc, list(times)
 
 
 def paam_rta_analyze_host(ctx: Context, sy, opts: AnalysisOpts, R, status, verdict=None, launch_config: int = -1,

@@ -527,7 +527,8 @@ LaunchFn find_variant(int impl, int G, int maxn)
 
 } // namespace
 
-// Candidate launch configurations the autotuner times (first = default).
+// Candidate launch configurations the autotuner times (kDefaultLaunchCfg is
+// the one a batch starts with).
 const LaunchCfg kLaunchCfgs[] = {
     {1, 8, 16, 0, 16, 256, 0},  {0, 8, 16, 0, 16, 256, 0},  {0, 16, 32, 0, 16, 256, 0}, {1, 16, 16, 0, 16, 256, 0},
     {1, 4, 16, 0, 16, 256, 0},  {1, 16, 32, 1, 32, 256, 0}, {1, 32, 32, 1, 32, 256, 0}, {1, 8, 16, 1, 32, 256, 0},
@@ -539,6 +540,7 @@ const LaunchCfg kLaunchCfgs[] = {
     {1, 16, 16, 0, 16, 256, 4, 1}, {1, 32, 32, 1, 32, 256, 4, 1}, {1, 8, 16, 0, 16, 256, 4, 1},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
+static_assert(kDefaultLaunchCfg < (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0])), "default configuration");
 
 int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const LaunchCfg &cfg, int64_t *R,
                           uint8_t *status, uint8_t *verdict, cudaStream_t stream, int *n_kernels)

@@ -392,6 +392,7 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
     paam_batch *b = (paam_batch *)calloc(1, sizeof(paam_batch));
     if (!b) return PAAM_E_NOMEM;
     b->ctx = ctx;
+    b->cfg_index = kDefaultLaunchCfg;
     b->n_sys = v->n_sys;
     b->n_chain = v->n_chain;
     b->n_cb = v->n_cb;

@@ -278,7 +278,7 @@ extern "C" int paam_rta_analyze_host(paam_ctx *ctx, const paam_systems_view *v, 
     ap.eps = o->eps_ns;
     ap.kappa = o->kappa_ns;
     ap.blocking_mode = o->blocking_mode;
-    const LaunchCfg &cfg = kLaunchCfgs[launch_config < 0 ? 0 : launch_config];
+    const LaunchCfg &cfg = kLaunchCfgs[launch_config < 0 ? kDefaultLaunchCfg : launch_config];
     for (int64_t k = 0; k < n_chunks && rc == PAAM_OK; ++k) {
         const Chunk &c = ch[(size_t)k];
         if (cudaEventSynchronize(ev_val[k]) != cudaSuccess) {

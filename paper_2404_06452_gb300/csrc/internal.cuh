@@ -233,6 +233,9 @@ int launch_reg(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_
                const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
 extern const LaunchCfg kLaunchCfgs[];
 extern const int kNumLaunchCfgs;
+// Configuration of a batch before any autotuning: 16-lane register tables,
+// work queue (the fastest on the 1M-system and the 10k x 256 search workloads)
+constexpr int kDefaultLaunchCfg = 12;
 
 // Enqueue the whole analysis of a batch (analyze_fast.cu); *n_kernels receives
 // the number of kernels it launched.

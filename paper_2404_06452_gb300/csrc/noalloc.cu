@@ -134,7 +134,7 @@ extern "C" int paam_rta_analyze_noalloc(const paam_systems_view *v, const paam_a
     p.kappa = o->kappa_ns;
     p.blocking_mode = o->blocking_mode;
     int nk = 0;
-    rc = paam_enqueue_analysis(&b, p, kLaunchCfgs[0], R, status, verdict, stream, &nk);
+    rc = paam_enqueue_analysis(&b, p, kLaunchCfgs[kDefaultLaunchCfg], R, status, verdict, stream, &nk);
     if (rc == PAAM_OK) paam_count_launch((unsigned)nk);
     return rc;
 }

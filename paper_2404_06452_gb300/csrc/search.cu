@@ -7,6 +7,9 @@
 // mode (see AnalysisParams): candidates are visited in order and each stops
 // at its first unschedulable chain; with stop_at_first a candidate above the
 // best one already found for its system is skipped.
+#include <algorithm>
+#include <chrono>
+
 #include "internal.cuh"
 
 namespace {
@@ -126,4 +129,48 @@ extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const
     if (cudaStreamSynchronize(stream) != cudaSuccess) rc = PAAM_E_CUDA;
     if (rc == PAAM_OK && herr != 0) rc = herr;
     return rc;
+}
+
+// The search's own autotuner: every launch configuration timed on the search
+// itself (host clock around the whole call, one warm-up and the median of five),
+// the fastest kept on the batch.  The analysis autotuner times plain
+// analyses, whose best shape can differ from the candidate mode's.
+extern "C" int paam_rta_autotune_search(paam_ctx *ctx, paam_batch *b, const paam_analysis_opts *o,
+                                        const int16_t *ranks, int32_t K, int32_t nmax, int32_t stop_at_first,
+                                        void *stream_, float *times_ms, int max_out)
+{
+    if (!ctx || !b || !o) return PAAM_E_INVAL;
+    if (b->ctx != ctx) return PAAM_E_STATE;
+    if (b->n_sys == 0) return b->cfg_index;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int32_t *first = nullptr;
+    if (cudaMallocAsync((void **)&first, 4 * (size_t)b->n_sys, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return PAAM_E_NOMEM;
+    }
+    const int keep = b->cfg_index;
+    int best = keep, rc = PAAM_OK;
+    double best_ms = 1e300;
+    constexpr int kReps = 5;
+    for (int i = 0; i < kNumLaunchCfgs && rc == PAAM_OK; ++i) {
+        b->cfg_index = i;
+        double t[kReps + 1] = {};
+        for (int rep = 0; rep <= kReps && rc == PAAM_OK; ++rep) {
+            const auto t0 = std::chrono::steady_clock::now();
+            rc = paam_rta_search_priorities(ctx, b, o, ranks, K, nmax, stop_at_first, nullptr, first, stream_);
+            t[rep] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+        std::sort(t + 1, t + kReps + 1);
+        const double med = t[1 + kReps / 2];
+        if (times_ms && i < max_out) times_ms[i] = (float)med;
+        if (med < best_ms) {
+            best_ms = med;
+            best = i;
+        }
+    }
+    cudaFreeAsync(first, stream);
+    cudaStreamSynchronize(stream);
+    b->cfg_index = rc == PAAM_OK ? best : keep;
+    return rc == PAAM_OK ? best : rc;
 }

@@ -110,3 +110,25 @@ def test_autotune_picks_a_valid_config_and_stays_exact():
     assert_same(dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy()),
                 oracle.analyze(sy, threads=8))
     b.free()
+
+
+def test_search_autotune_picks_a_valid_config_and_stays_exact():
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    sy = g.generate("cfg4s", n_sys=2000)
+    ranks = g.candidate_ranks(sy, 32, 4)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    assert pkg.paam_rta_get_launch_config(b) == 12  # a new batch starts with the work-queue configuration
+    r = torch.from_numpy(ranks).cuda()
+    best, times = pkg.paam_rta_autotune_search(ctx(), b, pkg.analysis_opts(), r)
+    assert 0 <= best < pkg.paam_rta_num_launch_configs()
+    assert all(t > 0 for t in times) and times[best] == min(times)
+    assert pkg.paam_rta_get_launch_config(b) == best
+    first, cand = pkg.search(ctx(), b, r)
+    torch.cuda.synchronize()
+    ref = oracle.search(sy, ranks, threads=8)
+    assert np.array_equal(cand.cpu().numpy(), ref["cand_ok"])
+    assert np.array_equal(first.cpu().numpy(), ref["first_ok"])
+    b.free()
