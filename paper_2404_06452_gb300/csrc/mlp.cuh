@@ -1,6 +1,7 @@
 // mlp.cuh -- shared declarations of the surrogate network's GPU code.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
@@ -58,6 +59,10 @@ struct TcGemm {
 };
 
 int tc_gemm(const TcGemm &g, int32_t *err, cudaStream_t stream);
+
+
+
+
 
 // Surrogate input features (features.cu): rows item = (system - sys0) * K +
 // candidate for items [0, n_items) of systems starting at sys0; ranks NULL =
