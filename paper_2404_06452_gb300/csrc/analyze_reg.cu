@@ -13,17 +13,10 @@
 // every lane adding the terms of its own chains for the chain under analysis;
 // the group combines them with shuffles.  Shared memory only holds each
 // chain's own recurrence terms, read by the whole group as broadcasts.
-#include "internal.cuh"
+#include "reg_common.cuh"
 
 namespace {
-
-constexpr uint64_t kFitR = 1ull << 30;
-constexpr uint32_t kInfR = 0xFFFFFFFFu;
-
-template <int NMAX>
-struct RegMask {
-    using type = typename std::conditional<(NMAX <= 32), uint32_t, uint64_t>::type;
-};
+using namespace paam_reg;
 
 template <int NMAX>
 struct OwnSmem {
@@ -38,104 +31,6 @@ struct OwnSmem {
     uint32_t seg0[NMAX];
     uint8_t order[NMAX];
 };
-
-// Narrow systems (every deadline below 2^27 - 64) sum per-lane partials capped
-// at 2^27 - 1 in 32 bits (at most 32 lanes: no wrap-around).  A capped partial
-// already exceeds every deadline, so the capped sum decides each comparison
-// with D, and each minimum with a per-segment sum <= D, as the true sum would.
-constexpr uint32_t kNarrow = 1u << 27;
-
-template <int G>
-__device__ __forceinline__ unsigned rgroup_mask()
-{
-    if constexpr (G == 32) {
-        return 0xffffffffu;
-    } else {
-        const unsigned lane = threadIdx.x & 31u;
-        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
-    }
-}
-
-template <int G, typename V>
-__device__ __forceinline__ V rsum(V v, unsigned mask)
-{
-#pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off, G);
-    return v;
-}
-
-// Group reductions.  32-bit ones are one redux.sync over the group's member
-// mask (every lane of a group takes the same path; groups of one warp may
-// reduce at the same time, each over its own mask); 64-bit ones use shuffles.
-template <int G, typename V>
-__device__ __forceinline__ V ror(V v, unsigned mask)
-{
-    if constexpr (sizeof(V) == 4) {
-        return (V)__reduce_or_sync(mask, (unsigned)v);
-    } else {
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) v |= __shfl_xor_sync(mask, v, off, G);
-        return v;
-    }
-}
-
-template <int G>
-__device__ __forceinline__ unsigned rand_(unsigned v, unsigned mask)
-{
-    return __reduce_and_sync(mask, v);
-}
-
-template <int G>
-__device__ __forceinline__ uint64_t gsum(uint64_t v, bool narrow, unsigned mask)
-{
-    if (narrow) {
-        const uint32_t x = v < kNarrow - 1 ? (uint32_t)v : kNarrow - 1;
-        return __reduce_add_sync(mask, x);
-    }
-    return rsum<G>(v, mask);
-}
-
-template <int G>
-__device__ __forceinline__ uint32_t rmax(uint32_t v, unsigned mask)
-{
-    return __reduce_max_sync(mask, v);
-}
-
-// value of slot t / G held by lane t % G, broadcast to the group
-template <int G, int CPL, typename V>
-__device__ __forceinline__ V bcast(const V (&a)[CPL], int t, unsigned mask)
-{
-    const int k = t / G;
-    V v = a[0];
-#pragma unroll
-    for (int i = 1; i < CPL; ++i)
-        if (k == i) v = a[i];
-    return __shfl_sync(mask, v, t % G, G);
-}
-
-template <typename Mask>
-__device__ __forceinline__ int rpopc(Mask m)
-{
-    if constexpr (sizeof(Mask) == 8)
-        return __popcll(m);
-    else
-        return __popc(m);
-}
-
-template <typename Mask>
-__device__ __forceinline__ int rlowest(Mask m)
-{
-    if constexpr (sizeof(Mask) == 8)
-        return __ffsll((long long)m) - 1;
-    else
-        return __ffs((int)m) - 1;
-}
-
-// Lemma 1 (Eq. 2): ceil(t / T) + 1 for t, T < 2^30 (magic m, shift sh; see analyze_fast.cu)
-__device__ __forceinline__ uint32_t rarrivals(uint32_t t, uint32_t tm1, uint32_t m, uint32_t sh)
-{
-    return (uint32_t)(((uint64_t)(t + tm1) * m) >> sh) + 1u;
-}
 
 template <int G, int CPL>
 __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t item, OwnSmem<G * CPL> &s,
