@@ -56,8 +56,32 @@ def test_one_accelerator_under_another_index_and_bad_index():
 
     sy = g.generate("cfg2", n_sys=20_000, p_spin=0.3)
     base = gpu_analyze(sy, n_buckets=2, eps=1_000)
-    moved = g.Systems(**{**sy.__dict__, "acc": np.full_like(sy.acc, 2)})  # the int64 kernel, 4 tables
+    moved = g.Systems(**{**sy.__dict__, "acc": np.full_like(sy.acc, 2)})  # tables for three accelerators
     assert_same(gpu_analyze(moved, n_buckets=2, eps=1_000), {k: base[k] for k in ("R", "status", "verdict")})
     bad = g.Systems(**{**sy.__dict__, "acc": np.where(np.arange(len(sy.acc)) == 5, 4, 0).astype(np.int32)})
     with pytest.raises(pkg.PaamError):
         pkg.paam_rta_load_systems(ctx(), bad)
+
+
+def test_every_launch_config_with_several_accelerators():
+    """The register-table kernel with per-accelerator tables (systems of up to
+    16 chains inside the 32-bit bound) and the int64 kernel for the rest give
+    the oracle's results in every launch configuration (static shares, work
+    queue, size order), with several buckets."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    mixed = g.assign_accelerators(g.generate("cfg3", n_sys=20_000, seed=5), 3)  # 2-64 chains: both kernels
+    sy2 = g.assign_accelerators(g.generate("cfg2", n_sys=20_000, p_spin=0.4), 2)
+    for sy in (mixed, sy2):
+        p = dict(n_buckets=3, eps=2_000, kappa=700)
+        ref = oracle.analyze(sy, threads=8, **p)
+        b = pkg.paam_rta_load_systems(ctx(), sy)
+        for i in range(pkg.paam_rta_num_launch_configs()):
+            pkg.paam_rta_set_launch_config(b, i)
+            R, st, v = pkg.analyze(ctx(), b, **p)
+            torch.cuda.synchronize()
+            assert_same(dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy()), ref)
+        b.free()
+
