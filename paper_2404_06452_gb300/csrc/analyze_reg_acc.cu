@@ -383,8 +383,10 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     __syncwarp(gm);
 }
 
+// three resident blocks of 256 per SM for up to three accelerators (80
+// registers, no spills); four accelerators need more registers: two blocks
 template <int G, int NACC>
-__global__ void __launch_bounds__(256, 2) analyze_reg_acc_kernel(BatchDev b, AnalysisParams p, int64_t *R,
+__global__ void __launch_bounds__(256, NACC <= 3 ? 3 : 2) analyze_reg_acc_kernel(BatchDev b, AnalysisParams p, int64_t *R,
                                                                  uint8_t *st, uint8_t *verdict, int32_t *wide_list,
                                                                  int32_t *wide_count)
 {
