@@ -32,7 +32,10 @@ struct OwnSmem {
     uint8_t order[NMAX];
 };
 
-template <int G, int CPL>
+// TARGET (a separate instantiation, used by the Audsley-style seed): the
+// candidate's verdict is the status of chain p.target[..] alone, the chains
+// are analysed until that one is done, and no candidate stops early.
+template <int G, int CPL, bool TARGET = false>
 __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t item, OwnSmem<G * CPL> &s,
                            int lane, unsigned gm, int64_t *__restrict__ R_out, uint8_t *__restrict__ st_out,
                            uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
@@ -49,6 +52,11 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     }
     const int64_t c0 = b.sys_chain_off[sys];
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
+    int tgt = -1;
+    if constexpr (TARGET) {
+        tgt = p.target[sys * p.Kc + cand_of(p, sys, cand)];
+        if (tgt < 0 || tgt >= n) return; // no trial in this slot
+    }
     if (n > NMAX) {
         if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
         return;
@@ -311,7 +319,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         const Mask cbit = (Mask)1 << c;
         if ((hp | (hpp & spins)) & ~sched) { // a needed H*_h is not available
             dep |= cbit;
-            if (rank_row) break; // a candidate fails at its first unschedulable chain
+            if (TARGET ? c == tgt : rank_row != nullptr) break; // a candidate fails at its first unschedulable chain
             continue;
         }
         uint32_t ccoef[CPL], acoef[CPL];
@@ -359,12 +367,18 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                     Ehp[k] = Ev[k] + (uint32_t)hs;
                     if (sp[k]) Ehpp[k] = Ev[k] + (uint32_t)hs;
                 }
-        } else if (rank_row) {
+        } else if (!TARGET && rank_row) {
             break;
         }
+        if (TARGET && c == tgt) break; // chains after the target cannot change its result
     }
 
     // ---- outputs --------------------------------------------------------------
+    if constexpr (TARGET) {
+        if (lane == 0) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = (uint8_t)((sched >> tgt) & 1);
+        __syncwarp(gm);
+        return;
+    }
     if (rank_row) {
         if (lane == 0) {
             const bool ok = sched == all;
@@ -386,7 +400,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     __syncwarp(gm);
 }
 
-template <int G, int CPL>
+template <int G, int CPL, bool TARGET = false>
 __device__ __forceinline__ void reg_items(const BatchDev &b, const AnalysisParams &p, int64_t *R, uint8_t *st,
                                           uint8_t *verdict, const int32_t *list, const int32_t *count,
                                           int32_t *big_list, int32_t *big_count, int32_t *wide_list,
@@ -401,7 +415,8 @@ __device__ __forceinline__ void reg_items(const BatchDev &b, const AnalysisParam
     const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for_each_item<G>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
         const int64_t item = list ? (int64_t)list[i] : i;
-        reg_system<G, CPL>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
+        reg_system<G, CPL, TARGET>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list,
+                                   wide_count);
     });
 }
 
@@ -425,6 +440,16 @@ __global__ void __launch_bounds__(256, 4) analyze_reg1_kernel(BatchDev b, Analys
                                                               int32_t *wide_count)
 {
     reg_items<G, 1>(b, p, R, st, verdict, list, count, big_list, big_count, wide_list, wide_count);
+}
+
+// Target mode for the Audsley-style seed: systems of up to G chains; larger
+// ones and those outside the 32-bit bound go to the wide list
+template <int G>
+__global__ void __launch_bounds__(256, 4) analyze_reg1_target_kernel(BatchDev b, AnalysisParams p,
+                                                                     int32_t *wide_list, int32_t *wide_count)
+{
+    reg_items<G, 1, true>(b, p, nullptr, nullptr, nullptr, nullptr, nullptr, wide_list, wide_count, wide_list,
+                          wide_count);
 }
 
 } // namespace
@@ -469,3 +494,23 @@ template int launch_reg<32, 1>(const paam_batch *, const AnalysisParams &, int64
                                const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
 template int launch_reg<32, 2>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
                                const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+
+int paam_launch_reg_target(const paam_batch *bt, const AnalysisParams &p, int32_t *list, int32_t *count,
+                           int64_t max_items, cudaStream_t stream)
+{
+    constexpr int G = 16, threads = 256;
+    const int groups = threads / G;
+    const size_t smem = sizeof(OwnSmem<G>) * groups;
+    auto kern = analyze_reg1_target_kernel<G>;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (max_items + groups - 1) / groups;
+    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, list, count);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    return PAAM_OK;
+}

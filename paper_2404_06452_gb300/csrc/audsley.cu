@@ -6,9 +6,11 @@
 // every unassigned chain c is a trial: the chains already placed keep their
 // ranks (all below l), c takes rank l and the other unassigned chains take
 // ranks 0 .. l-1 in deadline-monotonic order (D ascending, ties by index).
-// All trials of all systems are analysed in one launch of the exact int64
-// kernel in target mode, where a trial's verdict is whether c itself is
-// schedulable and the analysis stops once c is done.  The first passing c
+// All trials of all systems are analysed at once in target mode, where a
+// trial's verdict is whether c itself is schedulable and the analysis stops
+// once c is done: the register-table kernel for systems of up to 16 chains
+// inside its 32-bit bound (one accelerator, Lemma 4 as printed), the exact
+// int64 kernel for the rest.  The first passing c
 // in index order takes level l; if none passes, the unassigned chain with the
 // largest D (ties: highest index) does.  The admission test is not
 // OPA-compatible (bucket ranks, blocking and the DEP rule depend on the whole
@@ -106,7 +108,7 @@ extern "C" int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *b, const 
     PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t stream = (cudaStream_t)stream_;
     const int32_t Kc = b->max_chains > 0 ? b->max_chains : 1; // trials per system at step 0
-    const size_t per_sys = (size_t)Kc * ((size_t)nmax * sizeof(int16_t) + sizeof(int16_t) + 1);
+    const size_t per_sys = (size_t)Kc * ((size_t)nmax * sizeof(int16_t) + sizeof(int16_t) + 1 + sizeof(int32_t));
     int64_t chunk = (int64_t)(kTrialBytes / per_sys);
     if (chunk < 1) chunk = 1;
     if (chunk > b->n_sys) chunk = b->n_sys;
@@ -116,14 +118,19 @@ extern "C" int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *b, const 
     const size_t trial_bytes = (size_t)chunk * Kc * nmax * sizeof(int16_t);
     const size_t target_bytes = (size_t)chunk * Kc * sizeof(int16_t);
     const size_t ok_bytes = (size_t)chunk * Kc;
-    if (cudaMallocAsync(&tmp, trial_bytes + target_bytes + ok_bytes + 256, stream) != cudaSuccess) {
+    const size_t list_bytes = 4 * (size_t)chunk * Kc; // trials deferred to the int64 kernel
+    if (cudaMallocAsync(&tmp, trial_bytes + target_bytes + ok_bytes + list_bytes + 512, stream) != cudaSuccess) {
         cudaGetLastError();
         return PAAM_E_NOMEM;
     }
     int16_t *trial = (int16_t *)tmp;
     int16_t *target = (int16_t *)((char *)tmp + trial_bytes);
     uint8_t *ok = (uint8_t *)((char *)tmp + trial_bytes + target_bytes);
-    int32_t *err = (int32_t *)(((uintptr_t)ok + ok_bytes + 15) & ~(uintptr_t)15);
+    int32_t *list = (int32_t *)(((uintptr_t)ok + ok_bytes + 15) & ~(uintptr_t)15);
+    int32_t *err = (int32_t *)(((uintptr_t)(list + (size_t)chunk * Kc) + 15) & ~(uintptr_t)15);
+    int32_t *count = err + 4;
+    // the register-table kernel serves one accelerator and Lemma 4 as printed
+    const bool reg = !b->acc && o->blocking_mode == 0;
 
     int rc = PAAM_OK;
     unsigned launches = 0;
@@ -166,7 +173,15 @@ extern "C" int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *b, const 
         for (int32_t j = 0; j < b->max_chains && rc == PAAM_OK; ++j) {
             audsley_trials<<<tb, threads, 0, stream>>>(bd, j, Kc, nmax, rank, trial, target);
             if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-            if (rc == PAAM_OK) rc = paam_launch_wide(&sub, p, nullptr, nullptr, nullptr, nullptr, nullptr, items, stream);
+            if (rc == PAAM_OK && reg) {
+                if (cudaMemsetAsync(count, 0, sizeof(int32_t), stream) != cudaSuccess) rc = PAAM_E_CUDA;
+                if (rc == PAAM_OK) rc = paam_launch_reg_target(&sub, p, list, count, items, stream);
+                if (rc == PAAM_OK)
+                    rc = paam_launch_wide(&sub, p, nullptr, nullptr, nullptr, list, count, items, stream);
+                launches += 1;
+            } else if (rc == PAAM_OK) {
+                rc = paam_launch_wide(&sub, p, nullptr, nullptr, nullptr, nullptr, nullptr, items, stream);
+            }
             if (rc == PAAM_OK) {
                 audsley_pick<<<sb, threads, 0, stream>>>(bd, j, Kc, nmax, rank, target, ok);
                 if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;

@@ -264,6 +264,13 @@ int paam_launch_validate_range(const paam_batch *b, const int32_t *acc, const Va
 int paam_launch_reg_acc(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                         int64_t max_items, cudaStream_t stream);
 
+// Target mode of the register-table kernel (analyze_reg.cu; see
+// AnalysisParams.target): candidates of systems with up to 16 chains inside
+// the 32-bit bound; the others are appended to list (count *count) for the
+// int64 kernel.
+int paam_launch_reg_target(const paam_batch *bt, const AnalysisParams &p, int32_t *list, int32_t *count,
+                           int64_t max_items, cudaStream_t stream);
+
 // Exact int64 kernel (analyze_wide.cu) over list[0 .. *count) or, with
 // list == nullptr, over every system.
 int paam_launch_wide(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st,
