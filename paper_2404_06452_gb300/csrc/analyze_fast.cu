@@ -550,8 +550,8 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     if (!small || !bigfn) return PAAM_E_INVAL;
     int k = 0;
     const int64_t items = p.K > 0 ? b->n_sys * (int64_t)p.K : b->n_sys;
-    // the safe blocking term needs every segment bound: the int64 kernel for every system
-    if (p.blocking_mode == 1) {
+    // the safe blocking term with several accelerators: the int64 kernel for every system
+    if (p.blocking_mode == 1 && b->acc) {
         AnalysisParams pw = p; // the configuration's work distribution and order apply here too
         pw.queue_batch = 0;
         pw.sys_order = cfg.binned ? b->sys_order : nullptr;
@@ -575,6 +575,12 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
         pb.queue = b->queue + 1;
         pw.queue = b->queue + 2;
         pm.queue_batch = pb.queue_batch = pw.queue_batch = cfg.queue;
+    }
+    if (p.blocking_mode == 1) { // the safe blocking term in register tables, the int64 kernel for the rest
+        int rc = paam_launch_reg_safe(b, pm, R, status, verdict, items, stream);
+        if (rc == PAAM_OK) rc = paam_launch_wide(b, pw, R, status, verdict, b->list_wide, b->counts + 1, items, stream);
+        if (n_kernels) *n_kernels = 2;
+        return rc;
     }
     if (b->acc) { // several accelerators: per-accelerator register tables, the int64 kernel for the rest
         int rc = paam_launch_reg_acc(b, pm, R, status, verdict, items, stream);

@@ -264,6 +264,12 @@ int paam_launch_validate_range(const paam_batch *b, const int32_t *acc, const Va
 int paam_launch_reg_acc(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                         int64_t max_items, cudaStream_t stream);
 
+// The safe blocking reading (blocking_mode 1) in the register-table kernel
+// (analyze_reg.cu): systems of up to 16 chains inside the 32-bit bound; the
+// others go to b->list_wide (count b->counts[1]) for the int64 kernel.
+int paam_launch_reg_safe(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                         int64_t max_items, cudaStream_t stream);
+
 // Target mode of the register-table kernel (analyze_reg.cu; see
 // AnalysisParams.target): candidates of systems with up to 16 chains inside
 // the 32-bit bound; the others are appended to list (count *count) for the

@@ -132,3 +132,23 @@ def test_search_autotune_picks_a_valid_config_and_stays_exact():
     assert np.array_equal(cand.cpu().numpy(), ref["cand_ok"])
     assert np.array_equal(first.cpu().numpy(), ref["first_ok"])
     b.free()
+
+
+def test_safe_blocking_every_launch_config():
+    """The safe reading of Lemma 4 (blocking_mode 1) in the register-table
+    kernel, with the int64 kernel for systems over 16 chains or outside the
+    32-bit bound, in every launch configuration, against the oracle."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    p = dict(n_buckets=2, eps=1_500, kappa=300)
+    for sy in (g.generate("cfg2", n_sys=20_000, p_spin=0.5), g.generate("cfg3", n_sys=6_000, seed=8)):
+        ref = oracle.analyze(sy, blocking_mode=1, threads=8, **p)
+        b = pkg.paam_rta_load_systems(ctx(), sy)
+        for i in range(pkg.paam_rta_num_launch_configs()):
+            pkg.paam_rta_set_launch_config(b, i)
+            R, st, v = pkg.analyze(ctx(), b, blocking_mode=1, **p)
+            torch.cuda.synchronize()
+            assert_same(dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy()), ref)
+        b.free()
