@@ -155,16 +155,15 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
                  19: "analyze_reg_kernel<8, 2> (work queue, size-binned)"}
 
 
-# DRAM read + write per system of the analysis kernel, from an ncu capture
+# DRAM read + write per system of the analysis kernel, from ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum) of 500,000 systems of this
-# workload in launch configuration 12 (analyze_reg1_kernel<16> pulling from
-# the work queue): 956.51 MB.  Valid only while that kernel is unchanged and
-# the autotuner picks it.
-TRAFFIC_PER_SYSTEM = {12: 956.513792e6 / 500_000}
-# Executed warp-instructions per system of the same kernel and capture
+# workload, per launch configuration.  Valid only while the kernel is
+# unchanged since its capture; the kernel changed after the last one.
+TRAFFIC_PER_SYSTEM = {}
+# Executed warp-instructions per system of the same kernels and captures
 # (smsp__inst_executed.sum / 500,000 systems): the instruction-issue side of
 # the kernel, against the issue peak of 152 SMs x 4 schedulers x 1 per clock.
-WARP_INST_PER_SYSTEM = {12: 880.560887e6 / 500_000}
+WARP_INST_PER_SYSTEM = {}
 ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions / s at the 2070 MHz maximum SM clock
 
 
@@ -533,8 +532,8 @@ def kappa_bench(pkg, ctx, iters, sy=None):
 
 def accelerators_bench(pkg, ctx, n_sys, units=3):
     """The workload with its accelerator segments spread over `units` units by
-    worst-fit decreasing (one server per unit, rule R1): analysed by the
-    exact int64 kernel with per-accelerator tables."""
+    worst-fit decreasing (one server per unit, rule R1): analysed with
+    per-accelerator tables (the register-table kernel up to four units)."""
     import torch
 
     import paam_gen
@@ -550,6 +549,27 @@ def accelerators_bench(pkg, ctx, n_sys, units=3):
         out[k] = {"ms": t * 1e3, "chains_per_s": sy.n_chain / t,
                   "sched_chains": float((st == 0).float().mean().item())}
         b.free()
+    return out
+
+
+def safe_blocking_bench(pkg, ctx, sy):
+    """The same batch under the safe reading of Lemma 4's blocking term
+    (blocking_mode 1: a lower-priority callback holds its executor for its
+    WCET plus each of its segments' bounds), in the launch configuration the
+    autotuner picks for that mode, beside the literal reading."""
+    import torch
+
+    b = pkg.paam_rta_load_systems(ctx, sy)
+    out = {"systems": sy.n_sys}
+    for mode, key in ((0, "literal"), (1, "safe")):
+        opts = pkg.analysis_opts(blocking_mode=mode)
+        pkg.paam_rta_autotune(ctx, b, opts)
+        R, st, v = pkg.analyze(ctx, b, blocking_mode=mode)
+        t, _ = _timed(lambda: pkg.analyze(ctx, b, blocking_mode=mode), 5)
+        torch.cuda.synchronize()
+        out[key] = {"ms": t * 1e3, "chains_per_s": sy.n_chain / t, "launch_config": pkg.paam_rta_get_launch_config(b),
+                    "sched_chains": float((st == 0).float().mean().item())}
+    b.free()
     return out
 
 
@@ -776,10 +796,11 @@ def run_ours(args):
             search["cpu_baseline"] = search_cpu_baseline(min(args.search_sys, 2000))
     if rank == 0 and world == 1 and not args.no_surrogate:
         surrogate = surrogate_bench(pkg, ctx, args.train_sys, args.search_sys, args.top_k)
-    e2e_chains = kappa = accel = None
+    e2e_chains = kappa = accel = safe = None
     if rank == 0 and world == 1 and not args.no_search:
         e2e_chains = end_to_end_bench(pkg, ctx, min(n_sys, 1_000_000))
         accel = accelerators_bench(pkg, ctx, min(n_sys, 1_000_000))
+        safe = safe_blocking_bench(pkg, ctx, sy if sy.n_sys <= 1_000_000 else sy.subset(np.arange(1_000_000)))
         if args.kappa_iters > 0:
             kappa = kappa_bench(pkg, ctx, args.kappa_iters, sy.subset(np.arange(min(sy.n_sys, 200_000))))
 
@@ -796,6 +817,7 @@ def run_ours(args):
             "systems_per_s": total_sys * args.steps / (elapsed_ms / 1e3),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "search": search, "surrogate": surrogate, "end_to_end": e2e_chains, "kappa": kappa, "accelerators": accel,
+            "safe_blocking": safe,
         }
         print(json.dumps(line), flush=True)
     batch.free()

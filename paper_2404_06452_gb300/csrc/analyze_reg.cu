@@ -23,7 +23,7 @@ struct OwnSmem {
     using Mask = typename RegMask<NMAX>::type;
     // each chain's keys, read by the whole group as broadcasts in the relations pass
     int4 key[NMAX];   // {chain priority, executor, core, executor priority}
-    uint4 dv[NMAX];   // {Emax, T - 1, magic, shift}
+    uint4 dv[NMAX];   // {Emax, 2 (T - 1), magic, l}: the divisor T (rdivisor)
     uint2 sm[NMAX];   // {S*, M*}
     Mask hp[NMAX], hpp[NMAX], hps[NMAX];
     uint4 rec[NMAX];  // {D, base = B + E, own = S* + delta blk (capped at D + 1), deps = delta eps}
@@ -85,7 +85,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     const int64_t seg_base = n > 0 ? b.cb_seg_off[b.chain_cb_off[c0]] : 0;
 
     // ---- per-chain aggregates (Sec. II-C), one chain per slot ---------------
-    uint32_t tm1[CPL], mg[CPL], sh[CPL], Dv[CPL], Ev[CPL], Sv[CPL], Emx[CPL], Mv[CPL], Amn[CPL], dlv[CPL];
+    uint32_t tm2[CPL], mg[CPL], lg[CPL], Dv[CPL], Ev[CPL], Sv[CPL], Emx[CPL], Mv[CPL], Amn[CPL], dlv[CPL];
     uint32_t seg0[CPL];
     int32_t pr[CPL], ep[CPL], ex[CPL], co[CPL];
     bool sp[CPL], val[CPL];
@@ -95,7 +95,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     for (int k = 0; k < CPL; ++k) {
         const int j = lane + G * k;
         val[k] = j < n;
-        tm1[k] = mg[k] = sh[k] = Dv[k] = Ev[k] = Sv[k] = Emx[k] = Mv[k] = Amn[k] = dlv[k] = seg0[k] = 0;
+        tm2[k] = mg[k] = lg[k] = Dv[k] = Ev[k] = Sv[k] = Emx[k] = Mv[k] = Amn[k] = dlv[k] = seg0[k] = 0;
         pr[k] = ep[k] = INT32_MIN;
         ex[k] = co[k] = -1 - j;
         sp[k] = false;
@@ -135,13 +135,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         const bool fit = (uint64_t)T < kFitR && (uint64_t)D < kFitR && E < kFitR && S < kFitR && dl < kFitR &&
                          (eps == 0 || dl <= (kFitR - 1) / eps);
         fits &= fit ? 1u : 0u;
-        if (fit) {
-            const uint32_t Tu = (uint32_t)T;
-            const uint32_t l = Tu > 1 ? 32u - (uint32_t)__clz(Tu - 1u) : 0u;
-            mg[k] = (uint32_t)(((1ull << (31 + l)) + Tu - 1u) / Tu);
-            sh[k] = 31 + l;
-            tm1[k] = Tu - 1u;
-        }
+        if (fit) rdivisor((uint32_t)T, tm2[k], mg[k], lg[k]);
         Dv[k] = (uint32_t)D;
         Ev[k] = (uint32_t)E;
         Sv[k] = (uint32_t)S;
@@ -210,7 +204,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         if (!val[k]) continue;
         const int j = lane + G * k;
         s.key[j] = make_int4(pr[k], ex[k], co[k], ep[k]);
-        s.dv[j] = make_uint4(Emx[k], tm1[k], mg[k], sh[k]);
+        s.dv[j] = make_uint4(Emx[k], tm2[k], mg[k], lg[k]);
         s.sm[j] = make_uint2(Sv[k], Mv[k]);
     }
     __syncwarp(gm);
@@ -219,7 +213,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         const uint4 dv4 = s.dv[t];
         const uint2 sm2 = s.sm[t];
         const int32_t pt = kt4.x, xt = kt4.y, kt = kt4.z, et = kt4.w;
-        const uint32_t emt = dv4.x, tmt = dv4.y, mgt = dv4.z, sht = dv4.w;
+        const uint32_t emt = dv4.x, tmt = dv4.y, mgt = dv4.z, lgt = dv4.w;
         const uint32_t st = sm2.x, mt = sm2.y;
         const bool ut = (users >> t) & 1;
         const Mask bit = (Mask)1 << t;
@@ -231,16 +225,17 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             samex[k] |= sx ? bit : 0;
             hppm[k] |= (!sx && kt == co[k] && et > ep[k]) ? bit : 0; // hpp, Lemma 4
             pos[k] += (et > ep[k]) || (et == ep[k] && hi);           // executor, then chain priority
-            rank[k] += (ut && hi) ? 1 : 0;
             if (sx && pt < pr[k] && emt > Bv[k]) Bv[k] = emt; // one LP callback on the executor
             const bool act = dlv[k] != 0 && ut;               // c and t both use the accelerator
             const uint32_t sv = (act && hi) ? st : 0u;
-            hchd[k] += (uint64_t)rarrivals(Dv[k], tmt, mgt, sht) * sv;
+            hchd[k] += (uint64_t)rarrivals(Dv[k], tmt, mgt, lgt) * sv;
             sums[k] += sv;
             if (one_bucket && act && pt < pr[k] && mt > blk[k]) blk[k] = mt;
         }
     }
     const int n_users = rpopc(users);
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) rank[k] = rpopc(higher[k] & users); // users of higher priority
     int32_t bucket[CPL];
 #pragma unroll
     for (int k = 0; k < CPL; ++k) // bucket = floor(rank * n_buckets / |U|) (R2)
@@ -314,7 +309,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                             inf = true;
                             break;
                         }
-                        const uint64_t part = (uint64_t)rarrivals((uint32_t)h, tm1[0], mg[0], sh[0]) * acoef;
+                        const uint64_t part = (uint64_t)rarrivals((uint32_t)h, tm2[0], mg[0], lg[0]) * acoef;
                         const uint64_t nh = base + gsum<G>(part, narrow, gm);
                         if (nh == h) break;
                         h = nh;
@@ -359,23 +354,49 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         for (int k = 0; k < CPL; ++k) acoef[k] = ((hps >> (lane + G * k)) & 1) ? Sv[k] : 0u;
         uint64_t Hsum = 0;
         bool inf = false;
-        for (uint32_t q = 0; q < dl && !inf; ++q) {
-            const uint64_t base = (uint64_t)b.A[seg_base + s.seg0[c] + q] + kappa2 + blkc;
-            uint64_t h = base; // the recurrence starts with the first two terms
-            for (;;) {
-                if (h > Dc || Hsum + h >= lim) {
-                    inf = true;
-                    break;
-                }
-                uint64_t part = 0;
+        if (narrow) {
+            // 32 bits hold every value: base below 2^31, h <= D below 2^27, the
+            // group sum capped at 2^27 (a capped sum exceeds D as the true one would)
+            uint32_t H32 = 0;
+            const uint32_t k2 = (uint32_t)kappa2;
+            for (uint32_t q = 0; q < dl && !inf; ++q) {
+                const uint32_t base = (uint32_t)b.A[seg_base + s.seg0[c] + q] + k2 + blkc;
+                uint32_t h = base;
+                for (;;) {
+                    if (h > Dc || H32 + h >= lim) {
+                        inf = true;
+                        break;
+                    }
+                    uint64_t part = 0;
 #pragma unroll
-                for (int k = 0; k < CPL; ++k)
-                    part += (uint64_t)rarrivals((uint32_t)h, tm1[k], mg[k], sh[k]) * acoef[k];
-                const uint64_t nh = base + gsum<G>(part, narrow, gm);
-                if (nh == h) break; // strictly increasing until here, bounded by D
-                h = nh;
+                    for (int k = 0; k < CPL; ++k) part += (uint64_t)rarrivals(h, tm2[k], mg[k], lg[k]) * acoef[k];
+                    const uint32_t nh =
+                        base + umin(__reduce_add_sync(gm, part < kNarrow - 1 ? (uint32_t)part : kNarrow - 1), kNarrow);
+                    if (nh == h) break;
+                    h = nh;
+                }
+                H32 += h;
             }
-            Hsum += h;
+            Hsum = H32;
+        } else {
+            for (uint32_t q = 0; q < dl && !inf; ++q) {
+                const uint64_t base = (uint64_t)b.A[seg_base + s.seg0[c] + q] + kappa2 + blkc;
+                uint64_t h = base; // the recurrence starts with the first two terms
+                for (;;) {
+                    if (h > Dc || Hsum + h >= lim) {
+                        inf = true;
+                        break;
+                    }
+                    uint64_t part = 0;
+#pragma unroll
+                    for (int k = 0; k < CPL; ++k)
+                        part += (uint64_t)rarrivals((uint32_t)h, tm2[k], mg[k], lg[k]) * acoef[k];
+                    const uint64_t nh = base + gsum<G>(part, narrow, gm);
+                    if (nh == h) break; // strictly increasing until here, bounded by D
+                    h = nh;
+                }
+                Hsum += h;
+            }
         }
         if (lane == 0 && !inf) s.seg[c].x = (uint32_t)Hsum;
         __syncwarp(gm);
@@ -413,27 +434,62 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         uint64_t R = base + (dl ? (Hseg < own ? Hseg : own) + deps : 0);
         uint64_t hs = 0;
         bool ok = false;
-        while (R <= Dc) {
-            uint64_t cpu = 0, acc = 0;
+        if (narrow) {
+            // the same iteration in 32 bits: every deadline is below 2^27 - 64, in
+            // the loop base <= R <= D, the group sums are below 2^32, and each sum
+            // is capped at 2^27 where it is added (a capped term already exceeds D)
+            const uint32_t D32 = rc.x, base32 = rc.y, own32 = rc.z, deps32 = rc.w, Hs32 = sg.x;
+            uint32_t R32 = (uint32_t)R, hs32 = 0;
+            if (R <= Dc) {
+                for (;;) {
+                    uint64_t cpu = 0, acc = 0;
 #pragma unroll
-            for (int k = 0; k < CPL; ++k) {
-                const uint64_t mu = rarrivals((uint32_t)R, tm1[k], mg[k], sh[k]);
-                cpu += mu * ccoef[k];
-                acc += mu * acoef[k];
+                    for (int k = 0; k < CPL; ++k) {
+                        const uint64_t mu = rarrivals(R32, tm2[k], mg[k], lg[k]);
+                        cpu += mu * ccoef[k];
+                        acc += mu * acoef[k];
+                    }
+                    const uint32_t cs = __reduce_add_sync(gm, cpu < kNarrow - 1 ? (uint32_t)cpu : kNarrow - 1);
+                    const uint32_t as = __reduce_add_sync(gm, acc < kNarrow - 1 ? (uint32_t)acc : kNarrow - 1);
+                    hs32 = 0;
+                    if (dl) {
+                        const uint32_t hch = own32 + umin(as, kNarrow); // Eq. 4
+                        hs32 = (Hs32 < hch ? Hs32 : hch) + deps32;      // Eq. 1 with min(Eq. 3, Eq. 4)
+                    }
+                    const uint32_t Rn = base32 + umin(hs32, kNarrow) + umin(cs, kNarrow);
+                    if (Rn == R32) {
+                        ok = true;
+                        break;
+                    }
+                    R32 = Rn;
+                    if (R32 > D32) break;
+                }
             }
-            cpu = gsum<G>(cpu, narrow, gm);
-            acc = gsum<G>(acc, narrow, gm);
-            hs = 0;
-            if (dl) {
-                const uint64_t hch = own + acc; // Eq. 4
-                hs = (Hseg < hch ? Hseg : hch) + deps; // Eq. 1 with min(Eq. 3, Eq. 4)
+            R = R32;
+            hs = hs32;
+        } else {
+            while (R <= Dc) {
+                uint64_t cpu = 0, acc = 0;
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) {
+                    const uint64_t mu = rarrivals((uint32_t)R, tm2[k], mg[k], lg[k]);
+                    cpu += mu * ccoef[k];
+                    acc += mu * acoef[k];
+                }
+                cpu = gsum<G>(cpu, narrow, gm);
+                acc = gsum<G>(acc, narrow, gm);
+                hs = 0;
+                if (dl) {
+                    const uint64_t hch = own + acc; // Eq. 4
+                    hs = (Hseg < hch ? Hseg : hch) + deps; // Eq. 1 with min(Eq. 3, Eq. 4)
+                }
+                const uint64_t Rn = base + hs + cpu;
+                if (Rn == R) {
+                    ok = true;
+                    break;
+                }
+                R = Rn;
             }
-            const uint64_t Rn = base + hs + cpu;
-            if (Rn == R) {
-                ok = true;
-                break;
-            }
-            R = Rn;
         }
         if (ok) {
             sched |= cbit;

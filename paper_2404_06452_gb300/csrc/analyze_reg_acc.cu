@@ -24,7 +24,7 @@ template <int NMAX, int NACC>
 struct AccSmem {
     using Mask = typename RegMask<NMAX>::type;
     int4 key[NMAX];           // {chain priority, executor, core, executor priority}
-    uint4 dv[NMAX];           // {Emax, T - 1, magic, shift}
+    uint4 dv[NMAX];           // {Emax, 2 (T - 1), magic, l}: the divisor T (rdivisor)
     uint2 sm[NMAX][NACC];     // {S*_a, M*_a}
     Mask hp[NMAX], hpp[NMAX];
     Mask hps[NMAX][NACC];
@@ -72,7 +72,7 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     // ---- per-chain aggregates (Sec. II-C), per accelerator ------------------
     const int j = lane;
     const bool val = j < n;
-    uint32_t tm1 = 0, mg = 0, sh = 0, Dv = 0, Ev = 0, Emx = 0, seg0 = 0, dlt = 0;
+    uint32_t tm2 = 0, mg = 0, lg = 0, Dv = 0, Ev = 0, Emx = 0, seg0 = 0, dlt = 0;
     uint32_t Sa[NACC], Ma[NACC], Amn[NACC], dla[NACC];
     Mask users[NACC];
 #pragma unroll
@@ -127,13 +127,7 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         const bool fit = (uint64_t)T < kFitR && (uint64_t)D < kFitR && E < kFitR && Stot < kFitR && dtot < kFitR &&
                          (eps == 0 || dtot <= (kFitR - 1) / eps);
         fits = fit ? 1u : 0u;
-        if (fit) {
-            const uint32_t Tu = (uint32_t)T;
-            const uint32_t l = Tu > 1 ? 32u - (uint32_t)__clz(Tu - 1u) : 0u;
-            mg = (uint32_t)(((1ull << (31 + l)) + Tu - 1u) / Tu);
-            sh = 31 + l;
-            tm1 = Tu - 1u;
-        }
+        if (fit) rdivisor((uint32_t)T, tm2, mg, lg);
         Dv = (uint32_t)D;
         Ev = (uint32_t)E;
         Emx = (uint32_t)Emax;
@@ -192,7 +186,7 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     const bool one_bucket = p.n_buckets == 1;
     if (val) {
         s.key[j] = make_int4(pr, ex, co, ep);
-        s.dv[j] = make_uint4(Emx, tm1, mg, sh);
+        s.dv[j] = make_uint4(Emx, tm2, mg, lg);
 #pragma unroll
         for (int u = 0; u < NACC; ++u) s.sm[j][u] = make_uint2(Sa[u], Ma[u]);
     }
@@ -290,7 +284,7 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                         inf = true;
                         break;
                     }
-                    const uint64_t part = (uint64_t)rarrivals((uint32_t)h, tm1, mg, sh) * acoef;
+                    const uint64_t part = (uint64_t)rarrivals((uint32_t)h, tm2, mg, lg) * acoef;
                     const uint64_t nh = base + gsum<G>(part, narrow, gm);
                     if (nh == h) break; // strictly increasing until here, bounded by D
                     h = nh;
@@ -335,7 +329,7 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         uint64_t hs = 0;
         bool ok = false;
         while (R <= Dc) {
-            const uint64_t mu = rarrivals((uint32_t)R, tm1, mg, sh);
+            const uint64_t mu = rarrivals((uint32_t)R, tm2, mg, lg);
             const uint64_t cpu = gsum<G>(mu * ccoef, narrow, gm);
             hs = 0;
 #pragma unroll

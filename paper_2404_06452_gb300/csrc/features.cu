@@ -428,9 +428,24 @@ int paam_launch_features(const paam_batch *b, const int16_t *ranks, int32_t K, i
     K = K < 1 ? 1 : K;
     if (ranks && b->max_chains <= 32 && b->max_exec <= 32 && n_items % K == 0) {
         const int64_t n_systems = n_items / K;
+        // one wave of resident CTAs, each taking every so-many-th system: a grid
+        // above residency leaves a partial second wave behind the first
+        const bool l16 = b->max_chains <= 16;
+        static int resident[2] = {0, 0};
+        int &per_sm = resident[l16 ? 0 : 1];
+        if (per_sm == 0) {
+            int r = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &r, l16 ? cand_features_kernel<16> : cand_features_kernel<32>, CF_THREADS, 0) != cudaSuccess ||
+                r < 1) {
+                cudaGetLastError();
+                r = 8;
+            }
+            per_sm = r;
+        }
         int64_t blocks = n_systems;
-        if (blocks > 16 * (int64_t)b->ctx->n_sm) blocks = 16 * (int64_t)b->ctx->n_sm;
-        if (b->max_chains <= 16)
+        if (blocks > (int64_t)per_sm * b->ctx->n_sm) blocks = (int64_t)per_sm * b->ctx->n_sm;
+        if (l16)
             cand_features_kernel<16><<<(unsigned)blocks, CF_THREADS, 0, stream>>>(
                 batch_dev(b), ranks, K, nmax, sys0, n_systems, n_buckets, kappa, slots, X);
         else

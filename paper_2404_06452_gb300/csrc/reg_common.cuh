@@ -112,10 +112,22 @@ __device__ __forceinline__ int rlowest(Mask m)
         return __ffs((int)m) - 1;
 }
 
-// Lemma 1 (Eq. 2): ceil(t / T) + 1 for t, T < 2^30 (magic m, shift sh; see analyze_fast.cu)
-__device__ __forceinline__ uint32_t rarrivals(uint32_t t, uint32_t tm1, uint32_t m, uint32_t sh)
+// Lemma 1 (Eq. 2): ceil(t / T) + 1 for t, T < 2^30.  With x = t + T - 1 < 2^31,
+// l = ceil(log2 T) and m = ceil(2^(31 + l) / T), floor(x / T) = floor(x m /
+// 2^(31 + l)) for every x < 2^31 (Granlund and Montgomery 1994, Theorem 4.2
+// with N = 31).  Since 2x < 2^32 that is the high word of (2x) m shifted right
+// by l: one multiply-high and one 32-bit shift.  The divisor is kept as
+// {tm2 = 2 (T - 1), m, l}.
+__device__ __forceinline__ void rdivisor(uint32_t T, uint32_t &tm2, uint32_t &m, uint32_t &l)
 {
-    return (uint32_t)(((uint64_t)(t + tm1) * m) >> sh) + 1u;
+    l = T > 1 ? 32u - (uint32_t)__clz(T - 1u) : 0u;
+    m = (uint32_t)(((1ull << (31 + l)) + T - 1u) / T);
+    tm2 = 2u * (T - 1u);
+}
+
+__device__ __forceinline__ uint32_t rarrivals(uint32_t t, uint32_t tm2, uint32_t m, uint32_t l)
+{
+    return (__umulhi(2u * t + tm2, m) >> l) + 1u;
 }
 
 } // namespace paam_reg
