@@ -157,13 +157,14 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
 
 # DRAM read + write per system of the analysis kernel, from ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum) of 500,000 systems of this
-# workload, per launch configuration.  Valid only while the kernel is
-# unchanged since its capture; the kernel changed after the last one.
-TRAFFIC_PER_SYSTEM = {}
+# workload, per launch configuration: 12 is analyze_reg1_kernel<16> with the
+# work queue in index order (946.58 MB).  Valid only while the kernel and the
+# order it visits are unchanged since the capture.
+TRAFFIC_PER_SYSTEM = {12: 946.577408e6 / 500_000}
 # Executed warp-instructions per system of the same kernels and captures
 # (smsp__inst_executed.sum / 500,000 systems): the instruction-issue side of
 # the kernel, against the issue peak of 152 SMs x 4 schedulers x 1 per clock.
-WARP_INST_PER_SYSTEM = {}
+WARP_INST_PER_SYSTEM = {12: 780.865443e6 / 500_000}
 ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions / s at the 2070 MHz maximum SM clock
 
 

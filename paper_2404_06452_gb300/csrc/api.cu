@@ -284,13 +284,18 @@ int paam_launch_validate_range(const paam_batch *b, const int32_t *acc, const Va
 static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // ---------------------------------------------------------------------------
-// size binning: systems by increasing chain count (a counting sort over the
-// 65 possible counts; counts are clamped, so a batch that fails validation
-// cannot index outside the table)
+// size binning: within each window of kBinWindow consecutive systems, the
+// systems by increasing chain count (a counting sort over the 65 possible
+// counts; counts are clamped, so a batch that fails validation cannot index
+// outside the table).  Neighbouring queue items then have about the same
+// chain count, while the systems in flight at any time stay within a few
+// windows, whose tables L2 holds: a sort over the whole batch scatters the
+// reads and fetches each boundary sector twice.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int kBins = PAAM_MAX_CHAINS + 1;
+constexpr int kBinWindow = 8192;
 
 __device__ __forceinline__ int size_bin(const int64_t *off, int64_t s)
 {
@@ -298,66 +303,38 @@ __device__ __forceinline__ int size_bin(const int64_t *off, int64_t s)
     return c < 0 ? 0 : (c > PAAM_MAX_CHAINS ? PAAM_MAX_CHAINS : (int)c);
 }
 
-__global__ void bin_count(const int64_t *off, int64_t n_sys, int32_t *hist)
+// one CTA per window: histogram, exclusive scan, scatter to order[w0 + position]
+__global__ void bin_window(const int64_t *off, int64_t n_sys, int32_t *order)
 {
     __shared__ int32_t h[kBins];
+    const int64_t w0 = (int64_t)blockIdx.x * kBinWindow;
+    const int64_t w1 = w0 + kBinWindow < n_sys ? w0 + kBinWindow : n_sys;
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_sys; s += stride)
-        atomicAdd(&h[size_bin(off, s)], 1);
+    for (int64_t s = w0 + threadIdx.x; s < w1; s += blockDim.x) atomicAdd(&h[size_bin(off, s)], 1);
     __syncthreads();
-    for (int i = threadIdx.x; i < kBins; i += blockDim.x)
-        if (h[i]) atomicAdd(&hist[i], h[i]);
-}
-
-// counts -> first position of each bin
-__global__ void bin_scan(int32_t *hist)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (threadIdx.x == 0) {
         int32_t run = 0;
         for (int i = 0; i < kBins; ++i) {
-            const int32_t c = hist[i];
-            hist[i] = run;
+            const int32_t c = h[i];
+            h[i] = run;
             run += c;
         }
     }
-}
-
-// one atomic per distinct bin per warp; within a bin, systems keep roughly
-// their index order
-__global__ void bin_scatter(const int64_t *off, int64_t n_sys, int32_t *cursor, int32_t *order)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); s0 < n_sys; s0 += stride) {
-        const int64_t s = s0 + lane;
-        const bool v = s < n_sys;
-        const int k = v ? size_bin(off, s) : kBins + lane; // idle lanes: keys of their own
-        const unsigned peers = __match_any_sync(0xffffffffu, k);
-        const int leader = __ffs((int)peers) - 1;
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        int32_t base = 0;
-        if (v && lane == leader) base = atomicAdd(&cursor[k], __popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (v) order[base + rank] = (int32_t)s;
-    }
+    __syncthreads();
+    for (int64_t s = w0 + threadIdx.x; s < w1; s += blockDim.x)
+        order[w0 + atomicAdd(&h[size_bin(off, s)], 1)] = (int32_t)s;
 }
 
 } // namespace
 
-int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, int32_t *scratch, cudaStream_t stream)
+int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, cudaStream_t stream)
 {
     if (b->n_sys <= 0) return PAAM_OK;
-    const int threads = 256;
-    int64_t blocks = (b->n_sys + threads - 1) / threads;
-    if (blocks > 8 * (int64_t)b->ctx->n_sm) blocks = 8 * (int64_t)b->ctx->n_sm;
-    PAAM_CUDA_TRY(cudaMemsetAsync(scratch, 0, kBins * sizeof(int32_t), stream));
-    bin_count<<<(unsigned)blocks, threads, 0, stream>>>(b->sys_chain_off, b->n_sys, scratch);
-    bin_scan<<<1, 32, 0, stream>>>(scratch);
-    bin_scatter<<<(unsigned)blocks, threads, 0, stream>>>(b->sys_chain_off, b->n_sys, scratch, order);
+    const int64_t blocks = (b->n_sys + kBinWindow - 1) / kBinWindow;
+    bin_window<<<(unsigned)blocks, 256, 0, stream>>>(b->sys_chain_off, b->n_sys, order);
     PAAM_CUDA_TRY(cudaGetLastError());
-    paam_count_launch(3);
+    paam_count_launch(1);
     return PAAM_OK;
 }
 
@@ -426,7 +403,7 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
     total += align_up(acc_bytes) + 256;
     const size_t list_bytes = 4 * (size_t)(v->n_sys > 0 ? v->n_sys : 1);
     total += 2 * align_up(list_bytes) + 256;
-    total += align_up(list_bytes) + align_up(kBins * sizeof(int32_t)); // size-binned order and its counts
+    total += align_up(list_bytes); // size-binned order
     if (cudaMallocAsync(&b->block, total, stream) != cudaSuccess) {
         cudaGetLastError();
         free(b);
@@ -461,15 +438,13 @@ extern "C" int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *v, 
     b->queue = (unsigned long long *)(b->counts + 8); // inside the 256-byte counts area
     p += 256;
     b->sys_order = (int32_t *)p;
-    p += align_up(list_bytes);
-    int32_t *bin_scratch = (int32_t *)p;
     int32_t h_err[4] = {0, 0x7fffffff, 0, 0};
     if (rc == PAAM_OK && b->n_sys > 0) {
         if (cudaMemcpyAsync(ctx->d_err, h_err, sizeof(h_err), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
             cudaMemsetAsync(ctx->d_stats, 0, ST_COUNT * sizeof(unsigned long long), stream) != cudaSuccess)
             rc = PAAM_E_CUDA;
         if (paam_launch_validate(b, acc_dev, ctx->d_err, ctx->d_stats, stream) != PAAM_OK) rc = PAAM_E_CUDA;
-        if (rc == PAAM_OK && paam_launch_bin_by_size(b, b->sys_order, bin_scratch, stream) != PAAM_OK)
+        if (rc == PAAM_OK && paam_launch_bin_by_size(b, b->sys_order, stream) != PAAM_OK)
             rc = PAAM_E_CUDA;
         if (rc == PAAM_OK &&
             (cudaMemcpyAsync(h_err, ctx->d_err, sizeof(h_err), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||

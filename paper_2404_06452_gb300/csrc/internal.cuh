@@ -159,7 +159,7 @@ struct paam_batch {
     int32_t *list_big, *list_wide;
     int32_t *counts; // [0] big, [1] wide
     unsigned long long *queue; // [3] work-queue counters of the three passes (NULL: none)
-    int32_t *sys_order;        // [n_sys] systems by increasing chain count (NULL: not built)
+    int32_t *sys_order;        // [n_sys] systems by increasing chain count within windows of consecutive systems (NULL: not built)
     void *block;
     size_t block_bytes;
     int cfg_index; // launch configuration (index into kLaunchCfgs)
@@ -221,11 +221,12 @@ inline BatchDev batch_dev(const paam_batch *b)
 struct LaunchCfg {
     int impl_small, g_small, maxn_small, impl_big, g_big, threads;
     int queue;  // 0: static grid-stride shares; > 0: work queue, items per fetch
-    int binned; // 1: hand systems out in order of chain count (batch->sys_order)
+    int binned; // 1: hand systems out by chain count within windows (batch->sys_order)
 };
 
-// Builds b->sys_order (api.cu): a counting sort of the systems by chain count.
-int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, int32_t *scratch, cudaStream_t stream);
+// Builds b->sys_order (api.cu): a counting sort of the systems by chain count
+// within each window of consecutive systems.
+int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, cudaStream_t stream);
 
 // Register-table kernels (analyze_reg.cu): G lanes per system, CPL chains per lane.
 template <int G, int CPL>
