@@ -533,11 +533,11 @@ const LaunchCfg kLaunchCfgs[] = {
     {1, 8, 16, 0, 16, 256, 0},  {0, 8, 16, 0, 16, 256, 0},  {0, 16, 32, 0, 16, 256, 0}, {1, 16, 16, 0, 16, 256, 0},
     {1, 4, 16, 0, 16, 256, 0},  {1, 16, 32, 1, 32, 256, 0}, {1, 32, 32, 1, 32, 256, 0}, {1, 8, 16, 1, 32, 256, 0},
     {0, 4, 16, 0, 16, 256, 0},  {0, 8, 32, 0, 32, 256, 0},  {1, 16, 32, 0, 16, 256, 0}, {1, 4, 16, 1, 32, 128, 0},
-    // the same shapes pulling from the work queue, 4 items per fetch
-    {1, 16, 16, 0, 16, 256, 4}, {1, 8, 16, 0, 16, 256, 4},  {0, 8, 16, 0, 16, 256, 4},  {1, 16, 32, 1, 32, 256, 4},
-    {1, 32, 32, 1, 32, 256, 4},
+    // the same shapes pulling from the work queue, 2 items per fetch
+    {1, 16, 16, 0, 16, 256, 2}, {1, 8, 16, 0, 16, 256, 2},  {0, 8, 16, 0, 16, 256, 2},  {1, 16, 32, 1, 32, 256, 2},
+    {1, 32, 32, 1, 32, 256, 2},
     // the queue shapes again, handing systems out by increasing chain count
-    {1, 16, 16, 0, 16, 256, 4, 1}, {1, 32, 32, 1, 32, 256, 4, 1}, {1, 8, 16, 0, 16, 256, 4, 1},
+    {1, 16, 16, 0, 16, 256, 2, 1}, {1, 32, 32, 1, 32, 256, 2, 1}, {1, 8, 16, 0, 16, 256, 2, 1},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
 static_assert(kDefaultLaunchCfg < (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0])), "default configuration");

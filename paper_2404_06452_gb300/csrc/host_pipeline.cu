@@ -24,7 +24,7 @@
 
 namespace {
 
-constexpr size_t kChunkInputBytes = (size_t)128 << 20; // input bytes per chunk when not given
+constexpr size_t kMinChunkBytes = (size_t)32 << 20; // input bytes of the smallest automatic chunk
 constexpr int kMaxChunks = 4096;
 constexpr size_t kWords = 4 * sizeof(int32_t) + ST_COUNT * sizeof(unsigned long long); // per chunk
 
@@ -124,27 +124,40 @@ extern "C" int paam_rta_analyze_host(paam_ctx *ctx, const paam_systems_view *v, 
     const size_t in_bytes = 8 * (size_t)(2 * v->n_sys + 2) + (8 + 8 + 8 + 4 + 4 + 1) * (size_t)v->n_chain +
                             (8 + 8) * (size_t)v->n_cb + (8 + (v->acc ? 4 : 0)) * (size_t)v->n_seg +
                             (4 + (v->exec_prio ? 4 : 0)) * (size_t)v->n_exec;
-    int64_t per = chunk_systems;
-    if (per <= 0) {
+    // chunk k covers systems [starts[k], starts[k + 1])
+    std::vector<int64_t> starts{0};
+    if (chunk_systems > 0) {
+        int64_t per = chunk_systems < v->n_sys ? chunk_systems : v->n_sys;
+        if ((v->n_sys + per - 1) / per > kMaxChunks) per = (v->n_sys + kMaxChunks - 1) / kMaxChunks;
+        for (int64_t s = per; s < v->n_sys; s += per) starts.push_back(s);
+    } else {
+        // halving sizes: half the batch, a quarter, ... down to about
+        // kMinChunkBytes of input, the rest in the last chunk.  Each copy has a
+        // fixed cost on the link, so few chunks; the last one, whose analysis
+        // and copies back follow the last byte in, is small; and each chunk's
+        // analysis is shorter than the next chunk's copy.
         const double bytes_per_sys = (double)in_bytes / (double)v->n_sys;
-        per = (int64_t)((double)kChunkInputBytes / (bytes_per_sys > 1.0 ? bytes_per_sys : 1.0));
-        if (per < 1024) per = 1024;
+        int64_t min_sys = (int64_t)((double)kMinChunkBytes / (bytes_per_sys > 1.0 ? bytes_per_sys : 1.0));
+        if (min_sys < 1024) min_sys = 1024;
+        int64_t s = 0;
+        for (int64_t left = v->n_sys; left / 2 >= min_sys && left - left / 2 >= min_sys; left -= left / 2) {
+            s += left / 2;
+            starts.push_back(s);
+        }
     }
-    if (per > v->n_sys) per = v->n_sys;
-    int64_t n_chunks = (v->n_sys + per - 1) / per;
-    if (n_chunks > kMaxChunks) {
-        n_chunks = kMaxChunks;
-        per = (v->n_sys + n_chunks - 1) / n_chunks;
-        n_chunks = (v->n_sys + per - 1) / per;
-    }
+    starts.push_back(v->n_sys);
+    const int64_t n_chunks = (int64_t)starts.size() - 1;
+    int64_t per = 0; // the largest chunk, which sizes the deferral lists
+    for (int64_t k = 0; k < n_chunks; ++k)
+        per = starts[(size_t)k + 1] - starts[(size_t)k] > per ? starts[(size_t)k + 1] - starts[(size_t)k] : per;
     struct Chunk {
         int64_t s0, s1, c0, c1, b0, b1, q0, q1, x0, x1;
     };
     std::vector<Chunk> ch((size_t)n_chunks);
     for (int64_t k = 0; k < n_chunks; ++k) {
         Chunk &c = ch[(size_t)k];
-        c.s0 = k * per;
-        c.s1 = c.s0 + per < v->n_sys ? c.s0 + per : v->n_sys;
+        c.s0 = starts[(size_t)k];
+        c.s1 = starts[(size_t)k + 1];
         c.c0 = v->sys_chain_off[c.s0];
         c.c1 = v->sys_chain_off[c.s1];
         c.x0 = v->sys_exec_off[c.s0];

@@ -78,3 +78,16 @@ def test_invalid_system_in_a_later_chunk_is_rejected():
     bad2.sys_chain_off[-1] += 1
     with pytest.raises(pkg.PaamError):
         _host(bad2)
+
+
+def test_automatic_chunks_reject_an_invalid_system_in_the_last_chunk():
+    import paper_2404_06452_gb300 as pkg
+
+    # 200,000 systems: automatic chunks of halving size, the last one small
+    sy = g.generate("cfg2", n_sys=200_000)
+    assert_same(_host(sy), gpu_analyze(sy))
+    bad = sy.subset(np.arange(sy.n_sys))
+    c = int(bad.sys_chain_off[199_990])
+    bad.D[c] = bad.T[c] + 1  # D > T near the end of the batch
+    with pytest.raises(pkg.PaamError):
+        _host(bad)
