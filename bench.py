@@ -158,14 +158,15 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
 # DRAM read + write per system of the analysis kernel, from ncu captures
 # (dram__bytes_read.sum + dram__bytes_write.sum) of 500,000 systems of this
 # workload, per launch configuration: 12 is analyze_reg1_kernel<16> with the
-# work queue in index order (946.58 MB), 17 the same kernel visiting the
-# systems by chain count within windows of 8,192 systems (956.30 MB).  Valid
-# only while the kernel and the order it visits are unchanged since the capture.
-TRAFFIC_PER_SYSTEM = {12: 946.577408e6 / 500_000, 17: 956.297216e6 / 500_000}
+# work queue (2 systems per fetch) in index order (934.00 MB), 17 the same
+# kernel visiting the systems by chain count within windows of 8,192 systems
+# (937.25 MB).  Valid only while the kernel and the order it visits are
+# unchanged since the capture.
+TRAFFIC_PER_SYSTEM = {12: 934.004992e6 / 500_000, 17: 937.245184e6 / 500_000}
 # Executed warp-instructions per system of the same kernels and captures
 # (smsp__inst_executed.sum / 500,000 systems): the instruction-issue side of
 # the kernel, against the issue peak of 152 SMs x 4 schedulers x 1 per clock.
-WARP_INST_PER_SYSTEM = {12: 780.865443e6 / 500_000, 17: 746.750091e6 / 500_000}
+WARP_INST_PER_SYSTEM = {12: 783.638901e6 / 500_000, 17: 749.578079e6 / 500_000}
 ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions / s at the 2070 MHz maximum SM clock
 
 
