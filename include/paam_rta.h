@@ -243,7 +243,7 @@ int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *batch, const paam_a
  *                   (paam_rta_num_launch_configs), or -1 for the default.
  *   chunk_systems   systems per chunk, or <= 0 for automatic chunks of
  *                   halving size (half the batch, a quarter, ... down to
- *                   about 32 MB of input, the rest in the last chunk).
+ *                   about 64 MB of input, the rest in the last chunk).
  *   R, status       host [n_chain]; verdict host [n_sys], optional.
  *
  * Device memory for the whole batch is taken from the device's memory pool

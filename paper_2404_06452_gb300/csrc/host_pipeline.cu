@@ -24,7 +24,7 @@
 
 namespace {
 
-constexpr size_t kMinChunkBytes = (size_t)32 << 20; // input bytes of the smallest automatic chunk
+constexpr size_t kMinChunkBytes = (size_t)64 << 20; // input bytes of the smallest automatic chunk
 constexpr int kMaxChunks = 4096;
 constexpr size_t kWords = 4 * sizeof(int32_t) + ST_COUNT * sizeof(unsigned long long); // per chunk
 
