@@ -5,7 +5,8 @@ One step = one exact analysis of every chain of the 1,000,000-system workload
 (8-16 chains of 3-8 callbacks, 4 executors on 2 cores, utilisation swept
 0.3..0.9, accelerator-segment probability 0.5), inputs resident in HBM.
 Prints one JSON line.  ``--impl reference`` times the plain CPU oracle on the
-host cores instead (the reference arm of this build).
+host cores instead (the reference arm: there is no reference implementation
+to run, so the oracle stands in for it).
 """
 from __future__ import annotations
 

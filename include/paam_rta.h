@@ -39,7 +39,7 @@ extern "C" {
 #define PAAM_E_NOMEM (-3)       /* device or host allocation failed */
 #define PAAM_E_CUDA (-4)        /* a CUDA runtime call failed */
 #define PAAM_E_TIMEOUT (-5)     /* a bounded device wait gave up */
-#define PAAM_E_UNSUPPORTED (-6) /* input outside what this build implements */
+#define PAAM_E_UNSUPPORTED (-6) /* input outside what the library implements */
 #define PAAM_E_STATE (-7)       /* object used with the wrong context / after free */
 
 /* ---- per-chain status --------------------------------------------------- */

@@ -508,7 +508,7 @@ struct Variant {
     LaunchFn fn;
 };
 
-// Every (family, group width, table size) this build instantiates.
+// Every (family, group width, table size) the library instantiates.
 const Variant kVariants[] = {
     {0, 1, 16, launch_fast<1, 16>},   {0, 2, 16, launch_fast<2, 16>},   {0, 4, 16, launch_fast<4, 16>},
     {0, 8, 16, launch_fast<8, 16>},   {0, 2, 32, launch_fast<2, 32>},   {0, 4, 32, launch_fast<4, 32>},
