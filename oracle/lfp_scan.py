@@ -32,8 +32,18 @@ def _least_t(F, limit: int):
     return None
 
 
-def scan_system(sysd: dict, n_buckets: int = 1, eps: int = 0, kappa: int = 0):
-    """Returns (R list, status list) for one tiny system dict."""
+def scan_system(sysd: dict, n_buckets: int = 1, eps: int = 0, kappa: int = 0, blocking_mode: int = 0):
+    """Returns (R list, status list) for one tiny system dict.
+
+    ``blocking_mode`` 0 takes Lemma 4 as printed (the longest CPU WCET of a
+    lower-priority callback on the executor); 1 takes the safe reading, in
+    which such a callback keeps the single-threaded executor for its CPU work
+    and for each of its accelerator requests, each request bounded by its own
+    least fixed point of Eq. 3 plus the overhead eps, and an unbounded request
+    makes the blocking, and so the chain, unbounded (OVERRUN after the DEP
+    rule)."""
+    if blocking_mode not in (0, 1):
+        raise ValueError("blocking_mode: 0 or 1")
     ch = sysd["chains"]
     ex = sysd["execs"]
     n = len(ch)
@@ -65,22 +75,34 @@ def scan_system(sysd: dict, n_buckets: int = 1, eps: int = 0, kappa: int = 0):
     hpp = [[h for h in range(n) if xe[h] != xe[c] and core[h] == core[c] and eprio[h] > eprio[c]]
            for c in range(n)]
 
-    # Lemma 2 / Eq. 3 for every segment, summed per accelerator; None if some
-    # segment on that accelerator exceeds D_c
+    # Lemma 2 / Eq. 3: the least fixed point of every segment on its own
+    # (None when it lies above D_c), kept per callback for the safe blocking
+    # reading, and summed per accelerator (None if one of them is None)
+    def seg_lfp(c, a, u):
+        return _least_t(lambda t: a + blk[u][c] + sum(_mu(t, T[k]) * S[u][k] for k in hps[u][c]), D[c])
+
+    cb_h = [[[(seg_lfp(c, a + 2 * kappa, u), u) for a, u in map(_seg, ss)] for _, ss in ch[c]["cbs"]]
+            for c in range(n)]
     Hseg = {u: [] for u in accs}
     for u in accs:
         for c in range(n):
-            tot = 0
-            for a, v in segs[c]:
-                if v != u:
-                    continue
-                h = _least_t(lambda t, a=a, c=c, u=u: a + blk[u][c] + sum(_mu(t, T[k]) * S[u][k] for k in hps[u][c]),
-                             D[c])
-                if h is None:
-                    tot = None
-                    break
-                tot += h
-            Hseg[u].append(tot)
+            hs = [h for cb in cb_h[c] for h, v in cb if v == u]
+            Hseg[u].append(None if any(h is None for h in hs) else sum(hs))
+
+    if blocking_mode == 1:
+        # a lower-priority callback holds the executor for E plus, per request,
+        # its Lemma 2 bound and eps; B_c is the longest hold on c's executor
+        def cb_hold(l, i):
+            hs = [h for h, _ in cb_h[l][i]]
+            return None if any(h is None for h in hs) else ch[l]["cbs"][i][0] + sum(h + eps for h in hs)
+
+        hold = []
+        for l in range(n):
+            hl = [cb_hold(l, i) for i in range(len(ch[l]["cbs"]))]
+            hold.append(None if any(h is None for h in hl) else max(hl, default=0))
+        for c in range(n):
+            lp = [hold[l] for l in range(n) if xe[l] == xe[c] and prio[l] < prio[c]]
+            B[c] = None if any(h is None for h in lp) else max(lp, default=0)
 
     def Hstar(c, t):
         if delta[c] == 0:
@@ -101,6 +123,9 @@ def scan_system(sysd: dict, n_buckets: int = 1, eps: int = 0, kappa: int = 0):
         need = hp[c] + [h for h in hpp[c] if ch[h]["spin"]]
         if any(st[h] != SCHED for h in need):
             st[c], R[c] = DEP, -1
+            continue
+        if B[c] is None:  # unbounded blocking (safe reading only)
+            st[c], R[c] = OVERRUN, -1
             continue
 
         def F(t, c=c):

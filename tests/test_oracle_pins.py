@@ -90,6 +90,32 @@ def test_bruteforce_scan_agrees():
     assert n_checked > 5000
 
 
+def test_bruteforce_scan_agrees_safe_blocking():
+    """The safe blocking reading (blocking_mode=1) evaluated twice: the C
+    oracle against the brute-force scan, which takes each lower-priority
+    callback's hold from its own per-segment least fixed points.  Systems have
+    several callbacks per chain and several segments per callback, so the
+    longest-callback maximum, eps per segment and unbounded segments all
+    occur."""
+    rng = random.Random(20240407)
+    n_checked = n_differs = n_unbounded = 0
+    for trial in range(3000):
+        d = tiny.tiny_system(rng, n_max=5, n_min=2, cb_max=3, x_max=2, exec_per_core=rng.choice([1, 2]),
+                             periods=tuple(range(6, 41)), e_max=6, a_max=6, p_seg=0.6, p_spin=0.4,
+                             seg_max=rng.choice([2, 3]), n_acc=rng.choice([1, 1, 2]))
+        p = dict(n_buckets=rng.choice([1, 2, 3]), eps=rng.choice([0, 1, 2]), kappa=rng.choice([0, 1]))
+        R, st = lfp_scan.scan_system(d, blocking_mode=1, **p)
+        out = oracle.analyze(tiny.to_systems([d]), blocking_mode=1, aux=True, **p)
+        assert out["R"].tolist() == R, (d, p)
+        assert out["status"].tolist() == st, (d, p)
+        lit = oracle.analyze(tiny.to_systems([d]), aux=True, **p)
+        col = oracle.AUX_FIELDS.index("B")
+        n_differs += int(np.any(out["aux"][:, col] != lit["aux"][:, col]))
+        n_unbounded += int(np.any(out["aux"][:, col] == np.iinfo(np.int64).max))
+        n_checked += len(R)
+    assert n_checked > 8000 and n_differs > 800 and n_unbounded > 50, (n_checked, n_differs, n_unbounded)
+
+
 def test_monotone_in_wcets_and_overheads():
     sy = g.generate("cfg2", n_sys=3000, p_spin=0.5)
     base = oracle.analyze(sy, eps=10_000, kappa=5_000, n_buckets=2)
