@@ -53,6 +53,8 @@ def parse():
                     help="only measure the device preemption cost, ITERS iterations per kernel kind")
     ap.add_argument("--kappa-iters", type=int, default=300, help="preemption-cost iterations in the full run")
     ap.add_argument("--launch-config", type=int, default=None, help="fixed launch configuration (no autotune)")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the other analysis workloads (cfg1, cfg3)")
+    ap.add_argument("--workload-steps", type=int, default=20, help="timed steps of each other workload")
     return ap.parse_args()
 
 
@@ -164,6 +166,8 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
 # (937.25 MB).  Valid only while the kernel and the order it visits are
 # unchanged since the capture.
 TRAFFIC_PER_SYSTEM = {12: 934.004992e6 / 500_000, 17: 937.245184e6 / 500_000}
+# the same for the other workloads, keyed by (workload, launch configuration)
+TRAFFIC_OTHER = {}
 # Executed warp-instructions per system of the same kernels and captures
 # (smsp__inst_executed.sum / 500,000 systems): the instruction-issue side of
 # the kernel, against the issue peak of 152 SMs x 4 schedulers x 1 per clock.
@@ -179,6 +183,109 @@ def algorithmic_bytes(sy) -> int:
            + sy.exec_core.nbytes + (sy.exec_prio.nbytes if sy.exec_prio is not None else 0))
     out = sy.n_chain * 9 + sy.n_sys
     return int(inp + out)
+
+
+# The other analysis workloads, each timed as the headline one is (one step =
+# one graph replay of the autotuned analysis of the whole batch, inputs
+# resident), with its own roofline, end-to-end call and oracle baseline.
+EXTRA_WORKLOADS = {
+    "cfg1": dict(desc="1,000 systems: 4 chains of 2-4 callbacks, 2 executors on 1 core, one accelerator, "
+                      "utilisation 0.5, segment probability 0.3; n_buckets = 1, eps = kappa = 0; int64 ns",
+                 cpu_sample=None, flush_l2=True, params=dict(n_buckets=1, eps=0, kappa=0)),
+    "cfg3": dict(desc="4,000,000 systems of uneven size: 2 + Geom(1/9) chains (<= 64), 1-12 callbacks, "
+                      "2-8 executors, utilisation U[0.2, 0.95], segment probability 0.5; n_buckets = 1, "
+                      "eps = kappa = 0; int64 ns; one CUDA-graph replay of the autotuned persistent launch "
+                      "(size-binned work queue, deferral of larger systems) per step",
+                 cpu_sample=200_000, flush_l2=False, params=dict(n_buckets=1, eps=0, kappa=0)),
+}
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workload_bench(pkg, ctx, cfg, steps, warmup, e2e_steps, with_cpu):
+    """Throughput, roofline, end-to-end call and oracle baseline of one more
+    analysis workload (see EXTRA_WORKLOADS)."""
+    import torch
+
+    import paam_gen
+
+    w = EXTRA_WORKLOADS[cfg]
+    sy = paam_gen.generate(cfg)
+    stream = torch.cuda.Stream()
+    batch = pkg.paam_rta_load_systems(ctx, sy, stream=stream)
+    opts = pkg.analysis_opts(**w["params"])
+    cfg_index, _ = pkg.paam_rta_autotune(ctx, batch, opts, stream=stream)
+    R = torch.empty(batch.n_chain, dtype=torch.int64, device="cuda")
+    st = torch.empty(batch.n_chain, dtype=torch.uint8, device="cuda")
+    v = torch.empty(batch.n_sys, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda") if w["flush_l2"] else None
+    step = lambda: pkg.paam_rta_analyze_batch(ctx, batch, opts, R, st, v, stream=stream)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = pkg.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        if flush is not None:  # inputs smaller than L2: evict them between steps (untimed)
+            with torch.cuda.stream(stream):
+                flush.random_(0, 255)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    launches = pkg.launch_count() - launches0
+    ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+    alg = algorithmic_bytes(sy)
+    pk = peaks()
+    traffic = TRAFFIC_OTHER.get((cfg, cfg_index))
+    out = {"workload": w["desc"], "systems": sy.n_sys, "chains": sy.n_chain, "steps": steps, "warmup": warmup,
+           "ms_per_step": ms, "chains_per_s": sy.n_chain / (ms / 1e3), "systems_per_s": sy.n_sys / (ms / 1e3),
+           "launch_config": cfg_index, "kernel": CONFIG_KERNEL.get(cfg_index, "analysis kernel"),
+           "gpu_launches": int(launches),
+           "l2": "L2 flushed before every step (inputs %.1f MB)" % (sy.nbytes() / 1e6) if flush is not None
+           else "inputs larger than L2 (%.2f GB)" % (sy.nbytes() / 1e9),
+           "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "peak_src": pk["src"],
+                        "traffic": None if traffic is None else traffic * sy.n_sys,
+                        "algorithmic_bytes_per_launch": alg,
+                        "scope": "every kernel of the step (the analysis graph), algorithmic bytes of the batch"}}
+    # end to end through the C ABI with page-locked host buffers
+    pinned = pkg.to_device(sy, pin=True)
+    hR = torch.empty(batch.n_chain, dtype=torch.int64).pin_memory()
+    hst = torch.empty(batch.n_chain, dtype=torch.uint8).pin_memory()
+    hv = torch.empty(batch.n_sys, dtype=torch.uint8).pin_memory()
+    h2d = sum(getattr(pinned, f).numel() * getattr(pinned, f).element_size()
+              for f in ["sys_chain_off", "chain_cb_off", "cb_seg_off", "T", "D", "prio", "exec", "spin", "E",
+                        "A", "acc", "sys_exec_off", "exec_core", "exec_prio"] if getattr(pinned, f) is not None)
+    e2e_step = lambda: pkg.paam_rta_analyze_host(ctx, pinned, opts, hR, hst, hv, launch_config=cfg_index)
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    dt = (time.perf_counter() - t0) / e2e_steps
+    out["e2e"] = {"value": sy.n_chain / dt, "unit": "chains/s", "ms_per_step": dt * 1e3, "steps": e2e_steps,
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hR.numel() * 9 + hv.numel())}
+    same_host = bool(torch.equal(hR, R.cpu()) and torch.equal(hst, st.cpu()) and torch.equal(hv, v.cpu()))
+    out["e2e"]["same_results_as_device_path"] = same_host
+    if with_cpu:
+        import oracle
+
+        cores = os.cpu_count() or 1
+        idx = np.arange(sy.n_sys if w["cpu_sample"] is None else min(w["cpu_sample"], sy.n_sys))
+        sub = sy.subset(idx)
+        t0 = time.perf_counter()
+        ref = oracle.analyze(sub, threads=cores, **w["params"])
+        dt = time.perf_counter() - t0
+        ci = sy.chain_index(idx)
+        same = bool(np.array_equal(ref["R"], R.cpu().numpy()[ci]) and
+                    np.array_equal(ref["status"], st.cpu().numpy()[ci]) and
+                    np.array_equal(ref["verdict"], v.cpu().numpy()[idx]))
+        out["cpu_baseline"] = {"value": sub.n_chain / dt, "unit": "chains/s", "cores": cores, "kind": "oracle",
+                               "sample": ("the whole workload" if w["cpu_sample"] is None else
+                                          f"the first {len(idx)} systems of the workload ({sub.n_chain} chains)"),
+                               "systems_per_s": len(idx) / dt, "bit_exact_vs_gpu": same}
+    out["status_fractions"] = [float((st == k).float().mean()) for k in range(3)]
+    batch.free()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -606,7 +713,12 @@ def infer_bench(pkg, n_sys, steps, warmup):
             "candidates_per_s": n_sys * SEARCH_K / t}
 
 
-def search_cpu_baseline(n_sys):
+def search_cpu_baseline(pkg, ctx, n_sys):
+    """The oracle's exhaustive search on the first n_sys systems of the
+    sparse-executor search workload, and the GPU's exhaustive search on the
+    same candidates compared with it (cand_ok and first_ok)."""
+    import torch
+
     import oracle
     import paam_gen
 
@@ -615,10 +727,15 @@ def search_cpu_baseline(n_sys):
     cores = os.cpu_count() or 1
     ranks[:, 0, :] = oracle.audsley(sy, nmax=ranks.shape[2], threads=cores)  # slot 0 as on the GPU, untimed
     t0 = time.perf_counter()
-    oracle.search(sy, ranks, threads=cores)
+    ref = oracle.search(sy, ranks, threads=cores)
     dt = time.perf_counter() - t0
+    b = pkg.paam_rta_load_systems(ctx, sy)
+    first, cand = pkg.search(ctx, b, torch.from_numpy(ranks).cuda())
+    same = bool(np.array_equal(first.cpu().numpy(), ref["first_ok"]) and
+                np.array_equal(cand.cpu().numpy(), ref["cand_ok"]))
+    b.free()
     return {"value": n_sys / dt, "unit": "systems/s (exhaustive, 256 candidates)", "cores": cores, "kind": "oracle",
-            "sample": f"{n_sys} systems of the sparse-executor search workload"}
+            "sample": f"{n_sys} systems of the sparse-executor search workload", "bit_exact_vs_oracle": same}
 
 
 # ---------------------------------------------------------------------------
@@ -792,12 +909,18 @@ def run_ours(args):
         same = bool(np.array_equal(ref["R"], R.cpu().numpy()) and np.array_equal(ref["status"], st.cpu().numpy()))
         cpu["bit_exact_vs_gpu"] = same
 
+    # ---- the other analysis workloads (single GPU, rank 0) ---------------------
+    workloads = None
+    if rank == 0 and world == 1 and not args.no_workloads:
+        workloads = {cfg: workload_bench(pkg, ctx, cfg, args.workload_steps, max(3, args.warmup), 3,
+                                         not args.no_cpu_baseline) for cfg in EXTRA_WORKLOADS}
+
     # ---- priority search and surrogate (single GPU, rank 0) -------------------
     search = surrogate = None
     if rank == 0 and world == 1 and not args.no_search:
         search = search_bench(pkg, ctx, args.search_sys)
         if not args.no_cpu_baseline:
-            search["cpu_baseline"] = search_cpu_baseline(min(args.search_sys, 2000))
+            search["cpu_baseline"] = search_cpu_baseline(pkg, ctx, min(args.search_sys, 2000))
     if rank == 0 and world == 1 and not args.no_surrogate:
         surrogate = surrogate_bench(pkg, ctx, args.train_sys, args.search_sys, args.top_k)
     e2e_chains = kappa = accel = safe = None
@@ -821,7 +944,7 @@ def run_ours(args):
             "systems_per_s": total_sys * args.steps / (elapsed_ms / 1e3),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clocks, "search": search, "surrogate": surrogate, "end_to_end": e2e_chains, "kappa": kappa, "accelerators": accel,
-            "safe_blocking": safe,
+            "safe_blocking": safe, "workloads": workloads,
         }
         print(json.dumps(line), flush=True)
     batch.free()

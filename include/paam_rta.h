@@ -46,13 +46,16 @@ extern "C" {
 #define PAAM_ST_SCHED 0   /* R <= D: the chain meets its deadline                    */
 #define PAAM_ST_OVERRUN 1 /* the recurrence exceeded D (Theorem 1 gives no bound <= D) */
 #define PAAM_ST_DEP 2     /* a chain whose H* this chain needs is not schedulable     */
-#define PAAM_ST_ITERCAP 3 /* iteration safety cap hit; unreachable (each step raises a
-                             ceil(t/T)), kept as a guard                              */
+#define PAAM_ST_ITERCAP 3 /* a fixed-point recurrence reached PAAM_MAX_ITER evaluations;
+                             unreachable for a loaded batch (paam_rta_load_systems
+                             refuses systems whose bound exceeds it), kept as a guard */
 
 #define PAAM_MAX_CHAINS 64        /* chains per system                           */
 #define PAAM_MAX_TIME (1LL << 40) /* largest T, D, E, A accepted (about 18 min)  */
 #define PAAM_MAX_ACC 4            /* accelerators per batch (indices 0..3)        */
 #define PAAM_MAX_OVERHEAD (1LL << 32) /* largest eps, kappa accepted             */
+#define PAAM_MAX_ITER (1 << 20)   /* evaluations any one fixed-point recurrence of a
+                                     system may need (paam_rta_load_systems)      */
 
 typedef struct paam_ctx paam_ctx;
 typedef struct paam_batch paam_batch;
@@ -150,8 +153,16 @@ const char *paam_strerror(int code);
  * PAAM_E_RANGE when N * (ceil(Dmax / Tmin) + 1) * Cmax + Base could exceed
  * 2^62 for some system (the largest value any fixed-point iterate of Eqs. 3-6
  * can take with eps, kappa <= PAAM_MAX_OVERHEAD), so that no int64 sum
- * overflows; PAAM_E_INVAL for an accelerator index outside 0..PAAM_MAX_ACC-1;
- * PAAM_E_NOMEM / PAAM_E_CUDA.
+ * overflows; PAAM_E_RANGE also when a system's iteration bound
+ * L = sum over its chains h of ceil(Dmax / T_h), plus 2, exceeds
+ * PAAM_MAX_ITER (Dmax: the system's largest deadline).  Each recurrence of
+ * Eqs. 3 and 6 rises strictly until it converges or passes its deadline, and
+ * after its first step it can rise again only when some arrival count
+ * ceil(t / T_h) + 1 of Lemma 1 has grown, which happens at most
+ * ceil(Dmax / T_h) times per chain h below the deadline; so no recurrence of
+ * an accepted system takes more than L evaluations, and the analysis kernels
+ * stop any that would at PAAM_MAX_ITER (PAAM_ST_ITERCAP).  PAAM_E_INVAL for
+ * an accelerator index outside 0..PAAM_MAX_ACC-1; PAAM_E_NOMEM / PAAM_E_CUDA.
  * On error *out is NULL and nothing is leaked.
  */
 int paam_rta_load_systems(paam_ctx *ctx, const paam_systems_view *view, void *stream,
@@ -460,7 +471,7 @@ int paam_rta_get_launch_config(const paam_batch *batch);
  * call needs no context and allocates nothing: `view` must hold DEVICE
  * pointers (is_device = 1) to the caller's tables, R / status / verdict are
  * the caller's device outputs, and the bookkeeping the analysis needs lives in
- * one fixed device array of the library (PAAM_NOALLOC_MAX_SYS * 8 + 96 bytes,
+ * one fixed device array of the library (PAAM_NOALLOC_MAX_SYS * 8 + 128 bytes,
  * about 512 KiB), present on every GPU that loads the library until the
  * process exits.
  *
@@ -469,8 +480,10 @@ int paam_rta_get_launch_config(const paam_batch *batch);
  *   - the input is validated exactly as paam_rta_load_systems does, so the
  *     call synchronises `stream` once (after validation) and returns the
  *     same error codes; the analysis itself is then enqueued on `stream`;
- *   - the first call on a device (the current device) looks up the array's
- *     device address; make that first call before any stream capture;
+ *   - every call looks up the array's device address on the current device
+ *     (a lookup, no allocation), so the address stays right across a
+ *     cudaDeviceReset; the first call on a device also reads two device
+ *     attributes once; make that first call before any stream capture;
  *   - every call shares the array and it keeps the last call's contents
  *     (each call resets the parts that must start at zero): calls whose work
  *     overlaps on the GPU -- other streams, other host threads -- race and

@@ -139,6 +139,37 @@ def analyze(sy, n_buckets: int = 1, eps: int = 0, kappa: int = 0, blocking_mode:
     return out
 
 
+def iterations(sy, n_buckets: int = 1, eps: int = 0, kappa: int = 0, blocking_mode: int = 0, threads: int = 1):
+    """Evaluation counts of the fixed-point recurrences, per system: of the
+    segment recurrences (Eq. 3), of the chain recurrences (Eq. 6), and the
+    most evaluations any single recurrence took (``max_loop``)."""
+    lib = _lib("paam_oracle")
+    a = _arrays(sy)
+    nc, ns = len(a["T"]), len(a["sys_chain_off"]) - 1
+    out = {k: np.zeros(ns, np.int64) for k in ("seg", "chain", "max_loop")}
+    f = lib.oracle_analyze_iters
+    f.restype = None
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 14 + [
+        ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32] + [ctypes.c_void_p] * 5
+
+    def run(r):
+        R = np.zeros(nc, np.int64)
+        st = np.zeros(nc, np.uint8)
+        f(r[0], r[1], _p(a["sys_chain_off"]), _p(a["chain_cb_off"]), _p(a["cb_seg_off"]), _p(a["T"]),
+          _p(a["D"]), _p(a["prio"]), _p(a["exec"]), _p(a["spin"]), _p(a["E"]), _p(a["A"]), _p(a["acc"]),
+          _p(a["sys_exec_off"]), _p(a["exec_core"]), _p(a["exec_prio"]), int(n_buckets), int(eps),
+          int(kappa), int(blocking_mode), _p(R), _p(st), _p(out["seg"]), _p(out["chain"]), _p(out["max_loop"]))
+
+    rs = _ranges(ns, threads)
+    if len(rs) <= 1:
+        for r in rs:
+            run(r)
+    else:
+        with ThreadPoolExecutor(len(rs)) as ex:
+            list(ex.map(run, rs))
+    return out
+
+
 AUX_FIELDS = ("E", "Emax", "delta", "S", "M", "bucket", "blk", "B", "Hseg", "Hstar", "eprio", "prio")
 
 

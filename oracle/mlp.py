@@ -73,3 +73,56 @@ def loss_and_grad(params, X, L):
         flat.append(gW.ravel())
         flat.append(gb)
     return loss, np.concatenate(flat)
+
+
+def bf16(x):
+    """Round to bfloat16 (round to nearest, ties to even) through float32, as
+    a float32 value stored in bfloat16 is; returned as float64."""
+    f = np.ascontiguousarray(np.asarray(x, np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def loss_and_grad_bf16(params, X, L):
+    """The same masked MSE and gradient with the network's storage in
+    bfloat16, as the benchmark spec specifies it (BF16 weights, FP32
+    accumulation): weights, each layer's pre-activation kept for the backward
+    pass and its activation, the output gradient and each back-propagated
+    gradient are rounded to bfloat16 where they are stored; every sum is
+    exact (float64).  Also returns, per parameter, the sum of the magnitudes
+    of the products the gradient adds up (sum_r |g_r| |h_r|, and sum_r |g_r|
+    for a bias), the scale of the rounding error any summation order of
+    those products can make."""
+    layers = [(bf16(W), b) for W, b in unpack(params)]
+    h = np.asarray(X, np.float64)
+    cache = []
+    for i, (W, b) in enumerate(layers):
+        z = h @ W.T + b
+        if i < len(layers) - 1:
+            cache.append((h, bf16(z)))
+            h = bf16(gelu(z))
+        else:
+            cache.append((h, None))
+            h = z
+    Y = h
+    L = np.asarray(L, np.float64)
+    mask = L >= 0
+    cnt = max(int(mask.sum()), 1)
+    d = np.where(mask, Y - L, 0.0)
+    loss = float((d * d).sum() / cnt)
+    g = bf16(2.0 * d / cnt)  # dLoss / dY as stored
+    grads, scales = [], []
+    for i in range(len(layers) - 1, -1, -1):
+        W, b = layers[i]
+        h_in, _ = cache[i]
+        grads.append((g.T @ h_in, g.sum(axis=0)))
+        scales.append((np.abs(g).T @ np.abs(h_in), np.abs(g).sum(axis=0)))
+        if i == 0:
+            break
+        g = bf16((g @ W) * gelu_grad(cache[i - 1][1]))  # through the GELU of layer i - 1, stored
+    flat, sflat = [], []
+    for (gW, gb), (sW, sb) in zip(reversed(grads), reversed(scales)):
+        flat += [gW.ravel(), gb]
+        sflat += [sW.ravel(), sb]
+    return loss, np.concatenate(flat), np.concatenate(sflat)

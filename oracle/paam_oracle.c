@@ -48,7 +48,7 @@ enum { ST_SCHED = 0, ST_OVERRUN = 1, ST_DEP = 2, ST_ITERCAP = 3 };
 #define O_MAXACC 8 /* accelerators per system handled here */
 
 /* diagnostic counters (test infrastructure): fixed-point iterations per system */
-static __thread int64_t g_seg_iters, g_chain_iters;
+static __thread int64_t g_seg_iters, g_chain_iters, g_max_loop;
 #define O_ITER_LIMIT 100000000LL /* never reached: every iteration raises some mu */
 
 typedef struct {
@@ -210,7 +210,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
             const int64_t a_star = A[q] + 2 * kappa;
             const int64_t u = acc ? acc[q] : 0;
             int64_t h = a_star + ch[c].blkA[u]; /* the first two terms */
-            int64_t it = 0;
+            int64_t it = 0, evals = 0;
             for (;;) {
                 if (h > ch[c].D) {
                     h = O_INF;
@@ -224,6 +224,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                     }
                 }
                 g_seg_iters += 1;
+                evals += 1;
                 if (nh == h) break;
                 h = nh;
                 if (++it > O_ITER_LIMIT) {
@@ -231,6 +232,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                     break;
                 }
             }
+            if (evals > g_max_loop) g_max_loop = evals;
             hq[q - q_sys] = h;
             if (h == O_INF || ch[c].HsegA[u] == O_INF)
                 ch[c].HsegA[u] = O_INF;
@@ -321,7 +323,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                 h0 += ch[c].delta * eps;
             }
             int64_t R = ch[c].B + ch[c].E + h0;
-            int64_t it = 0;
+            int64_t it = 0, evals = 0;
             ch[c].status = ST_OVERRUN;
             for (;;) {
                 if (R > ch[c].D) break;
@@ -342,6 +344,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                     }
                 }
                 g_chain_iters += 1;
+                evals += 1;
                 if (Rn == R) {
                     ch[c].status = ST_SCHED;
                     ch[c].Hstar = hs;
@@ -353,6 +356,7 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
                     break;
                 }
             }
+            if (evals > g_max_loop) g_max_loop = evals;
             ch[c].R = ch[c].status == ST_SCHED ? R : -1;
         }
         if (!progressed) break; /* unreachable: the dependency relation is acyclic */
@@ -384,7 +388,9 @@ static void analyze_system(int64_t s, const int64_t *sys_chain_off, const int64_
     free(ch);
 }
 
-/* per-system iteration counts of the last oracle_analyze_iters call */
+/* per system: evaluations of the segment recurrences (Eq. 3), of the chain
+ * recurrences (Eq. 6), and the most evaluations any one of them took
+ * (max_loop may be NULL) */
 void oracle_analyze_iters(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
                           const int64_t *chain_cb_off, const int64_t *cb_seg_off, const int64_t *T,
                           const int64_t *D, const int32_t *prio, const int32_t *exec,
@@ -392,16 +398,18 @@ void oracle_analyze_iters(int64_t lo, int64_t hi, const int64_t *sys_chain_off,
                           const int64_t *sys_exec_off, const int32_t *exec_core,
                           const int32_t *exec_prio, int32_t n_buckets, int64_t eps, int64_t kappa,
                           int32_t blocking_mode, int64_t *R, uint8_t *status, int64_t *seg_iters,
-                          int64_t *chain_iters)
+                          int64_t *chain_iters, int64_t *max_loop)
 {
     for (int64_t s = lo; s < hi; ++s) {
         g_seg_iters = 0;
         g_chain_iters = 0;
+        g_max_loop = 0;
         analyze_system(s, sys_chain_off, chain_cb_off, cb_seg_off, T, D, prio, exec, spin, E, A, acc,
                        sys_exec_off, exec_core, exec_prio, NULL, n_buckets, eps, kappa, blocking_mode, R,
                        status, NULL, NULL, NULL);
         seg_iters[s] = g_seg_iters;
         chain_iters[s] = g_chain_iters;
+        if (max_loop) max_loop[s] = g_max_loop;
     }
 }
 

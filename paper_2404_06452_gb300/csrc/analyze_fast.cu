@@ -49,6 +49,7 @@ struct FastSmem {
     uint8_t sh[MAXN];    // shift of the magic division
     uint8_t order[MAXN]; // analysis order
     uint8_t spin[MAXN];
+    uint8_t cap[MAXN];   // 1: a segment recurrence reached kIterCap evaluations
     // per chain: interferer sets and the terms of its own recurrence
     Mask hp[MAXN], hpp[MAXN], hps[MAXN];
     uint32_t D[MAXN], B[MAXN], E[MAXN], blk[MAXN], Hseg[MAXN], R[MAXN], dlt[MAXN];
@@ -307,6 +308,7 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         const uint32_t Dc = s.D[c];
         const uint32_t dl = s.dlt[c];
         uint32_t Hseg = kInf32;
+        bool capped = false;
         if (dl > 0) {
             // Eq. 4 can take at most own + sum_h mu_h(D) S_h for any window R <= D.  Every
             // segment's Lemma 2 fixed point is at least x + sum_h mu_h(x) S_h >= x + f sum_h S_h
@@ -329,9 +331,14 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
                 for (uint32_t j = 0; j < dl && !inf; ++j) {
                     const uint64_t base = (uint64_t)b.A[seg_base + s.seg0[c] + j] + kappa2 + blk;
                     uint64_t h = base; // the recurrence starts with the first two terms
+                    uint32_t ev = 0;
                     for (;;) {
                         if (h > Dc || Hsum + h >= limit) {
                             inf = true;
+                            break;
+                        }
+                        if (ev++ == kIterCap) {
+                            inf = capped = true;
                             break;
                         }
                         uint64_t nh = base;
@@ -348,6 +355,7 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             }
         }
         s.Hseg[c] = Hseg;
+        s.cap[c] = capped ? 1 : 0;
         s.Ehp[c] = s.E[c];
         s.Ehpp[c] = s.E[c] + (s.spin[c] ? 0u : (uint32_t)((uint64_t)dl * eps));
     }
@@ -356,6 +364,7 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     // ---- Theorem 1 (Eq. 6), chain by chain ----------------------------------
     const Mask mine = lane_bits<G, Mask>(lane);
     Mask sched = 0, dep = 0;
+    Mask capm = 0; // chains whose chain recurrence reached kIterCap evaluations
     for (int k = 0; k < n; ++k) {
         const int c = s.order[k];
         const Mask hp = s.hp[c], hpp = s.hpp[c], hps = s.hps[c];
@@ -363,6 +372,10 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         if ((hp | (hpp & spins)) & ~sched) { // a needed H*_h is not available
             dep |= cbit;
             if (rank_row) break; // a candidate fails at its first unschedulable chain
+            continue;
+        }
+        if (s.cap[c]) { // a segment recurrence was cut short: no bound (PAAM_ST_ITERCAP)
+            if (rank_row) break;
             continue;
         }
         const uint64_t Dc = s.D[c];
@@ -376,7 +389,12 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         uint64_t R = base + (dl ? (Hseg < own ? Hseg : own) + deps : 0);
         uint64_t hs = 0;
         bool ok = false;
+        uint32_t ev = 0;
         while (R <= Dc) {
+            if (ev++ == kIterCap) {
+                capm |= cbit;
+                break;
+            }
             uint64_t cpu = 0, acc = 0;
             const uint32_t t = (uint32_t)R;
             for (Mask mm = todo; mm; mm &= mm - 1) {
@@ -428,7 +446,8 @@ __device__ void fast_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         const Mask bit = (Mask)1 << c;
         const bool ok = sched & bit;
         R_out[c0 + c] = ok ? (int64_t)s.R[c] : -1;
-        st_out[c0 + c] = ok ? PAAM_ST_SCHED : ((dep & bit) ? PAAM_ST_DEP : PAAM_ST_OVERRUN);
+        st_out[c0 + c] = ok ? PAAM_ST_SCHED
+                            : (((capm & bit) || s.cap[c]) ? PAAM_ST_ITERCAP : ((dep & bit) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
     }
     if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
     __syncwarp(gmask);

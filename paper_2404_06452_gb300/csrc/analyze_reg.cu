@@ -260,6 +260,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
 
     // ---- own recurrence terms to shared memory ------------------------------
     Mask need_exact = 0;
+    Mask capm = 0; // chains whose recurrence reached kIterCap evaluations
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         if (!val[k]) continue;
@@ -304,9 +305,15 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                     const uint64_t base = (uint64_t)b.A[q] + kappa2 + blkc;
                     uint64_t h = base; // the recurrence starts with the first two terms
                     bool inf = false;
+                    uint32_t ev = 0;
                     for (;;) {
                         if (h > Dc) {
                             inf = true;
+                            break;
+                        }
+                        if (ev++ == kIterCap) {
+                            inf = true;
+                            capm |= (Mask)1 << c;
                             break;
                         }
                         const uint64_t part = (uint64_t)rarrivals((uint32_t)h, tm2[0], mg[0], lg[0]) * acoef;
@@ -362,9 +369,15 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             for (uint32_t q = 0; q < dl && !inf; ++q) {
                 const uint32_t base = (uint32_t)b.A[seg_base + s.seg0[c] + q] + k2 + blkc;
                 uint32_t h = base;
+                uint32_t ev = 0;
                 for (;;) {
                     if (h > Dc || H32 + h >= lim) {
                         inf = true;
+                        break;
+                    }
+                    if (ev++ == kIterCap) {
+                        inf = true;
+                        capm |= (Mask)1 << c;
                         break;
                     }
                     uint64_t part = 0;
@@ -382,9 +395,15 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             for (uint32_t q = 0; q < dl && !inf; ++q) {
                 const uint64_t base = (uint64_t)b.A[seg_base + s.seg0[c] + q] + kappa2 + blkc;
                 uint64_t h = base; // the recurrence starts with the first two terms
+                uint32_t ev = 0;
                 for (;;) {
                     if (h > Dc || Hsum + h >= lim) {
                         inf = true;
+                        break;
+                    }
+                    if (ev++ == kIterCap) {
+                        inf = true;
+                        capm |= (Mask)1 << c;
                         break;
                     }
                     uint64_t part = 0;
@@ -420,6 +439,10 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             if (TARGET ? c == tgt : rank_row != nullptr) break; // a candidate fails at its first unschedulable chain
             continue;
         }
+        if (capm & cbit) { // a segment recurrence was cut short: no bound (PAAM_ST_ITERCAP)
+            if (TARGET ? c == tgt : rank_row != nullptr) break;
+            continue;
+        }
         uint32_t ccoef[CPL], acoef[CPL];
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
@@ -440,8 +463,13 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             // is capped at 2^27 where it is added (a capped term already exceeds D)
             const uint32_t D32 = rc.x, base32 = rc.y, own32 = rc.z, deps32 = rc.w, Hs32 = sg.x;
             uint32_t R32 = (uint32_t)R, hs32 = 0;
+            uint32_t ev = 0;
             if (R <= Dc) {
                 for (;;) {
+                    if (ev++ == kIterCap) {
+                        capm |= cbit;
+                        break;
+                    }
                     uint64_t cpu = 0, acc = 0;
 #pragma unroll
                     for (int k = 0; k < CPL; ++k) {
@@ -468,7 +496,12 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             R = R32;
             hs = hs32;
         } else {
+            uint32_t ev = 0;
             while (R <= Dc) {
+                if (ev++ == kIterCap) {
+                    capm |= cbit;
+                    break;
+                }
                 uint64_t cpu = 0, acc = 0;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
@@ -527,7 +560,9 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         const int j = lane + G * k;
         const bool ok = (sched >> j) & 1;
         R_out[c0 + j] = ok ? (int64_t)Rv[k] : -1;
-        st_out[c0 + j] = ok ? PAAM_ST_SCHED : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN);
+        st_out[c0 + j] = ok ? PAAM_ST_SCHED
+                            : (((capm >> j) & 1) ? PAAM_ST_ITERCAP
+                                                 : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
     }
     if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
     __syncwarp(gm);

@@ -264,6 +264,7 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     __syncwarp(gm);
 
     // ---- exact per-segment fixed points (Lemma 2), per accelerator ----------
+    Mask capm = 0; // chains whose recurrence reached kIterCap evaluations
 #pragma unroll 1
     for (int u = 0; u < NACC; ++u) {
         for (Mask nm = need_exact[u]; nm; nm &= nm - 1) {
@@ -279,9 +280,15 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                 if (acc_at<NACC>(b, qb + q) != u) continue; // the chain's segments on accelerator u
                 const uint64_t base = (uint64_t)b.A[qb + q] + kappa2 + blkc;
                 uint64_t h = base; // the recurrence starts with the first two terms
+                uint32_t ev = 0;
                 for (;;) {
                     if (h > Dc || Hsum + h >= lim) {
                         inf = true;
+                        break;
+                    }
+                    if (ev++ == kIterCap) {
+                        inf = true;
+                        capm |= (Mask)1 << c;
                         break;
                     }
                     const uint64_t part = (uint64_t)rarrivals((uint32_t)h, tm2, mg, lg) * acoef;
@@ -308,6 +315,10 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             if (rank_row) break; // a candidate fails at its first unschedulable chain
             continue;
         }
+        if (capm & cbit) { // a segment recurrence was cut short: no bound (PAAM_ST_ITERCAP)
+            if (rank_row) break;
+            continue;
+        }
         const uint32_t ccoef = ((hp >> j) & 1) ? Ehp : (((hpp >> j) & 1) ? Ehpp : 0u);
         uint32_t acoef[NACC];
         bool uses[NACC]; // the same in every lane of the group
@@ -328,7 +339,12 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         uint64_t R = base + (dl ? h0 + deps : 0);
         uint64_t hs = 0;
         bool ok = false;
+        uint32_t ev = 0;
         while (R <= Dc) {
+            if (ev++ == kIterCap) {
+                capm |= cbit;
+                break;
+            }
             const uint64_t mu = rarrivals((uint32_t)R, tm2, mg, lg);
             const uint64_t cpu = gsum<G>(mu * ccoef, narrow, gm);
             hs = 0;
@@ -371,7 +387,9 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     if (val) {
         const bool ok = (sched >> j) & 1;
         R_out[c0 + j] = ok ? (int64_t)Rv : -1;
-        st_out[c0 + j] = ok ? PAAM_ST_SCHED : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN);
+        st_out[c0 + j] = ok ? PAAM_ST_SCHED
+                            : (((capm >> j) & 1) ? PAAM_ST_ITERCAP
+                                                 : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
     }
     if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
     __syncwarp(gm);

@@ -22,6 +22,7 @@ template <int MAXN, int NACC>
 struct SysSmem {
     int64_t T[MAXN], D[MAXN], E[MAXN], Hs[MAXN], B[MAXN];
     int64_t Emax[MAXN], seglo[MAXN], hold[MAXN];
+    uint8_t cap[MAXN]; // 1: a segment recurrence of the chain reached kIterCap evaluations
     int64_t S[MAXN][NACC], M[MAXN][NACC], blk[MAXN][NACC], Hseg[MAXN][NACC];
     int32_t prio[MAXN], eprio[MAXN], delta[MAXN], core[MAXN], exec[MAXN];
     int32_t dA[MAXN][NACC], bucket[MAXN][NACC];
@@ -251,6 +252,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
     for (int c = lane; c < n; c += G) {
         int64_t Hseg[NACC], hold = 0;
         bool any_inf = false; // some segment of the chain has no bound
+        bool capped = false;
 #pragma unroll
         for (int a = 0; a < NACC; ++a) Hseg[a] = 0;
         const int64_t Dc = s.D[c];
@@ -270,9 +272,14 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
                 const int64_t a = b.A[q] + kappa2, blk = s.blk[c][u];
                 int64_t h = a + blk;
                 bool inf = false;
+                uint32_t ev = 0;
                 for (;;) {
                     if (h > Dc) {
                         inf = true;
+                        break;
+                    }
+                    if (ev++ == kIterCap) {
+                        inf = capped = true;
                         break;
                     }
                     int64_t nh = a + blk;
@@ -294,6 +301,7 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
 #pragma unroll
         for (int a = 0; a < NACC; ++a) s.Hseg[c][a] = Hseg[a];
         s.hold[c] = any_inf ? kInf : hold;
+        s.cap[c] = capped ? 1 : 0;
     }
     __syncwarp(gmask);
     if (safe) { // B_c: the longest hold of a lower-priority chain on the same executor
@@ -339,8 +347,13 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
             // start: B + E + H* with the interference parts of Eq. 4 empty
             int64_t Rc = Bc + Ec + (dc > 0 ? h0 + deps : 0);
             st = PAAM_ST_OVERRUN;
+            uint32_t ev = 0;
             for (;;) {
                 if (Rc > Dc) break;
+                if (ev++ == kIterCap) {
+                    st = PAAM_ST_ITERCAP;
+                    break;
+                }
                 int64_t cpu = 0, acc[NACC];
 #pragma unroll
                 for (int a = 0; a < NACC; ++a) acc[a] = 0;
@@ -377,6 +390,10 @@ __device__ void analyze_system(const BatchDev &b, const AnalysisParams &p, int64
                 Rc = Rn;
             }
             R = st == PAAM_ST_SCHED ? Rc : -1;
+        }
+        if (s.cap[c] && st != PAAM_ST_DEP) { // a segment bound was cut short
+            st = PAAM_ST_ITERCAP;
+            R = -1;
         }
         if (lane == 0) {
             s.status[c] = st;

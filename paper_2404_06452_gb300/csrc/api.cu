@@ -233,6 +233,16 @@ __global__ void validate_kernel(ValidateArgs a)
             const double bound = (double)n * m * Cmax + Base + Emax_sys + dseg_max * Mmax_sys + Dmax;
             if (!(bound < 2.305843009213694e18)) /* 2^61: margin under 2^62 */
                 fail(a.err, PAAM_E_RANGE, s);
+            // iteration bound: after its first step a recurrence rises only when an
+            // arrival count ceil(t / T_h) + 1 (Lemma 1) has grown, at most
+            // ceil(Dmax / T_h) times per chain h while t <= Dmax
+            const uint64_t Dm = (uint64_t)Dmax; // exact: below 2^40
+            uint64_t iters = 2;
+            for (int64_t c = c0; c < c1 && iters <= (uint64_t)PAAM_MAX_ITER; ++c) {
+                const uint64_t T = (uint64_t)b.T[c];
+                iters += (Dm + T - 1) / T;
+            }
+            if (iters > (uint64_t)PAAM_MAX_ITER) fail(a.err, PAAM_E_RANGE, s);
         }
     }
     // one atomic per warp and statistic

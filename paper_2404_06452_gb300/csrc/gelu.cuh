@@ -1,5 +1,5 @@
-// gelu.cuh -- the surrogate network's activation on the GPU, shared by the
-// GEMM epilogues (mlp_gemm.cu) and the fused inference kernel (mlp_fused.cu).
+// gelu.cuh -- the surrogate network's activation on the GPU, used by the
+// GEMM epilogues (mlp_gemm.cu).
 #pragma once
 
 #include <cuda_runtime.h>

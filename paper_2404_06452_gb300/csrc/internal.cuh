@@ -238,6 +238,13 @@ extern const int kNumLaunchCfgs;
 // work queue (the fastest on the 1M-system and the 10k x 256 search workloads)
 constexpr int kDefaultLaunchCfg = 12;
 
+// Evaluations any one fixed-point recurrence may take before the analysis
+// kernels stop it with PAAM_ST_ITERCAP.  Validation refuses systems whose
+// bound (sum over chains of ceil(Dmax / T) plus 2) exceeds it, so for a loaded
+// batch the cap is never reached; it bounds the kernels' running time all the
+// same.
+constexpr uint32_t kIterCap = (uint32_t)PAAM_MAX_ITER;
+
 // Enqueue the whole analysis of a batch (analyze_fast.cu); *n_kernels receives
 // the number of kernels it launched.
 int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const LaunchCfg &cfg, int64_t *R,

@@ -24,33 +24,38 @@ constexpr int kM = PAAM_NOALLOC_MAX_SYS;
 constexpr int kWords = 2 * kM + 8 + 2 * ST_COUNT + 6 + 6; // ... + three 64-bit work-queue counters
 
 static __device__ __align__(256) int32_t g_noalloc_scratch[kWords];
+static_assert(sizeof(g_noalloc_scratch) == (size_t)PAAM_NOALLOC_MAX_SYS * 8 + 128,
+              "the header documents the array as PAAM_NOALLOC_MAX_SYS * 8 + 128 bytes");
 
 struct DeviceSetup {
     bool ready;
     int n_sm, max_smem_optin;
-    int32_t *scratch; // device address of g_noalloc_scratch on this device
 };
 
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
-// First call on a device: with that device current, look up the scratch
-// array's device address (host code must never pass the array's own name to
-// a kernel: on the host it is only a stand-in for the device symbol).
-int setup_device(int dev, DeviceSetup **out)
+// With the device current: its attributes (read on the first call only) and
+// the scratch array's device address, looked up on every call so that it is
+// right even after the device was reset.  Host code must never pass the
+// array's own name to a kernel: on the host it is only a stand-in for the
+// device symbol.
+int setup_device(int dev, DeviceSetup *out, int32_t **scratch)
 {
     if (dev < 0 || dev >= kMaxDevices) return PAAM_E_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    DeviceSetup &d = g_setup[dev];
-    if (!d.ready) {
-        void *ptr = nullptr;
-        PAAM_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-        PAAM_CUDA_TRY(cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev));
-        PAAM_CUDA_TRY(cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        d.scratch = (int32_t *)ptr;
-        d.ready = true;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        DeviceSetup &d = g_setup[dev];
+        if (!d.ready) {
+            PAAM_CUDA_TRY(cudaDeviceGetAttribute(&d.n_sm, cudaDevAttrMultiProcessorCount, dev));
+            PAAM_CUDA_TRY(cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+            d.ready = true;
+        }
+        *out = d;
     }
-    *out = &d;
+    void *ptr = nullptr;
+    PAAM_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    *scratch = (int32_t *)ptr;
     return PAAM_OK;
 }
 
@@ -73,9 +78,11 @@ extern "C" int paam_rta_analyze_noalloc(const paam_systems_view *v, const paam_a
     if (v->n_sys == 0) return PAAM_OK;
     int dev = 0;
     PAAM_CUDA_TRY(cudaGetDevice(&dev));
-    DeviceSetup *d = nullptr;
-    int rc = setup_device(dev, &d);
+    DeviceSetup dset = {};
+    int32_t *scratch = nullptr;
+    int rc = setup_device(dev, &dset, &scratch);
     if (rc != PAAM_OK) return rc;
+    const DeviceSetup *d = &dset;
     cudaStream_t stream = (cudaStream_t)stream_;
 
     // a context and a batch that live on this stack frame and point at the
@@ -104,12 +111,12 @@ extern "C" int paam_rta_analyze_noalloc(const paam_systems_view *v, const paam_a
     b.exec_core = (int32_t *)v->exec_core;
     b.exec_prio = (int32_t *)v->exec_prio;
     b.spin = (uint8_t *)v->spin;
-    b.list_big = d->scratch;
-    b.list_wide = d->scratch + kM;
-    b.counts = d->scratch + 2 * kM;
-    b.queue = (unsigned long long *)(d->scratch + 2 * kM + 8 + 2 * ST_COUNT + 6);
-    int32_t *err = d->scratch + 2 * kM + 4;
-    unsigned long long *stats = (unsigned long long *)(d->scratch + 2 * kM + 8);
+    b.list_big = scratch;
+    b.list_wide = scratch + kM;
+    b.counts = scratch + 2 * kM;
+    b.queue = (unsigned long long *)(scratch + 2 * kM + 8 + 2 * ST_COUNT + 6);
+    int32_t *err = scratch + 2 * kM + 4;
+    unsigned long long *stats = (unsigned long long *)(scratch + 2 * kM + 8);
 
     // the array keeps the previous call's contents: reset what must start at zero
     const int32_t err0[4] = {0, 0x7fffffff, 0, 0};

@@ -100,13 +100,20 @@ struct KernelSet {
         else if (k == 1) na = kRedN, nc = 1;
         else if (k == 2) na = nb = nc = kVecN;
         else na = kHistN / 4, nc = 0;
-        if (na && cudaMalloc(&a, 4 * na) != cudaSuccess) return PAAM_E_NOMEM;
-        if (nb && cudaMalloc(&b, 4 * nb) != cudaSuccess) return PAAM_E_NOMEM;
-        if (nc && cudaMalloc(&c, 4 * nc) != cudaSuccess) return PAAM_E_NOMEM;
-        if (k == 3 && cudaMalloc(&bins, 256 * sizeof(unsigned)) != cudaSuccess) return PAAM_E_NOMEM;
+        // on any failure the buffers taken so far are freed before returning
+        if ((na && cudaMalloc(&a, 4 * na) != cudaSuccess) || (nb && cudaMalloc(&b, 4 * nb) != cudaSuccess) ||
+            (nc && cudaMalloc(&c, 4 * nc) != cudaSuccess) ||
+            (k == 3 && cudaMalloc(&bins, 256 * sizeof(unsigned)) != cudaSuccess)) {
+            cudaGetLastError();
+            release();
+            return PAAM_E_NOMEM;
+        }
         fill_kernel<<<1024, 256>>>(a, (int64_t)na, 0.5f);
         if (nb) fill_kernel<<<1024, 256>>>(b, (int64_t)nb, 0.25f);
-        PAAM_CUDA_TRY(cudaGetLastError());
+        if (cudaGetLastError() != cudaSuccess) {
+            release();
+            return PAAM_E_CUDA;
+        }
         return PAAM_OK;
     }
 

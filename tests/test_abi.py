@@ -62,3 +62,17 @@ def test_host_only_entry_points(lib):
     assert lib.paam_rta_load_systems(None, None, None, None) < 0
     lib.paam_rta_set_launch_config.argtypes = [ctypes.c_void_p, ctypes.c_int]
     assert lib.paam_rta_set_launch_config(None, 0) < 0
+
+
+def _define(name):
+    m = re.search(r"#define\s+" + name + r"\s+\(?(\d+)(?:\s*<<\s*(\d+))?\)?", open(HEADER).read())
+    assert m, name
+    return int(m.group(1)) << int(m.group(2) or 0)
+
+
+def test_binding_constants_match_the_header():
+    import paper_2404_06452_gb300 as pkg
+
+    assert pkg.PAAM_NOALLOC_MAX_SYS == _define("PAAM_NOALLOC_MAX_SYS")
+    assert pkg.PAAM_MAX_CHAINS == _define("PAAM_MAX_CHAINS")
+    assert _define("PAAM_MAX_ITER") == 1 << 20

@@ -110,3 +110,38 @@ def test_ordered_search_subset():
         pkg.paam_rta_search_ordered(ctx(), b, pkg.analysis_opts(), r, bad, False, None,
                                     torch.empty(sy.n_sys, dtype=torch.int32, device="cuda"))
     b.free()
+
+
+@pytest.mark.parametrize("cfg", ["cfg4", "cfg4s"])
+def test_search_full_shape_matches_oracle(cfg):
+    """The search workload at its specified shape, 10,000 systems of 16 chains
+    x 256 candidate orders (slot 0 the Audsley-style seed, slot 1
+    deadline-monotonic, the rest random permutations), in the launch
+    configuration the search autotuner picks for each mode, against the
+    oracle's exhaustive search on every system and candidate."""
+    import os
+
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    sy = g.generate(cfg)
+    assert sy.n_sys == 10000
+    ranks = g.candidate_ranks(sy, 256, g.CONFIGS[cfg]["seed"] + 7)
+    threads = os.cpu_count() or 8
+    ranks[:, 0, :] = oracle.audsley(sy, nmax=ranks.shape[2], threads=threads)  # the seed, from the oracle
+    ref = oracle.search(sy, ranks, threads=threads)
+    b = pkg.paam_rta_load_systems(ctx(), sy)
+    r = torch.from_numpy(ranks).cuda()
+    for stop in (False, True):
+        pkg.paam_rta_autotune_search(ctx(), b, pkg.analysis_opts(), r, stop_at_first=stop)
+        first, cand = pkg.search(ctx(), b, r, stop_at_first=stop)
+        torch.cuda.synchronize()
+        assert np.array_equal(first.cpu().numpy(), ref["first_ok"]), stop
+        if not stop:
+            assert np.array_equal(cand.cpu().numpy(), ref["cand_ok"])
+        else:
+            assert np.all(cand.cpu().numpy() <= ref["cand_ok"])
+    b.free()
+    if cfg == "cfg4s":
+        assert 0.3 < (ref["first_ok"] >= 0).mean() < 0.95
