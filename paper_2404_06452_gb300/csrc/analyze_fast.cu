@@ -535,6 +535,7 @@ const Variant kVariants[] = {
     {0, 8, 64, launch_fast<8, 64>},   {0, 16, 64, launch_fast<16, 64>}, {0, 32, 64, launch_fast<32, 64>},
     {1, 4, 16, launch_reg<4, 4>},     {1, 8, 16, launch_reg<8, 2>},     {1, 16, 16, launch_reg<16, 1>},
     {1, 16, 32, launch_reg<16, 2>},   {1, 32, 32, launch_reg<32, 1>},   {1, 32, 64, launch_reg<32, 2>},
+    {2, 16, 16, launch_lazy},
 };
 
 LaunchFn find_variant(int impl, int G, int maxn)
@@ -557,6 +558,8 @@ const LaunchCfg kLaunchCfgs[] = {
     {1, 32, 32, 1, 32, 256, 2},
     // the queue shapes again, handing systems out by increasing chain count
     {1, 16, 16, 0, 16, 256, 2, 1}, {1, 32, 32, 1, 32, 256, 2, 1}, {1, 8, 16, 0, 16, 256, 2, 1},
+    // register tables with lazy per-chain work (analyze_lazy.cu): static shares, queue, queue by size
+    {2, 16, 16, 1, 32, 256, 0, 0}, {2, 16, 16, 1, 32, 256, 2, 0}, {2, 16, 16, 1, 32, 256, 2, 1},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
 static_assert(kDefaultLaunchCfg < (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0])), "default configuration");
@@ -610,7 +613,9 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     int rc = small(b, pm, R, status, verdict, nullptr, nullptr, items, cfg.threads, stream);
     if (rc != PAAM_OK) return rc;
     ++k;
-    if (b->max_chains > cfg.maxn_small) {
+    // the lazy kernel also defers systems inside the 32-bit bound that are not narrow
+    const bool lazy_defers = cfg.impl_small == 2 && b->stats[ST_DMAX] >= kLazyNarrowD;
+    if (b->max_chains > cfg.maxn_small || lazy_defers) {
         rc = bigfn(b, pb, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
         if (rc != PAAM_OK) return rc;
         ++k;

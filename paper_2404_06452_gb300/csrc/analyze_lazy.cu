@@ -1,0 +1,368 @@
+// analyze_lazy.cu -- the register-table analysis with lazy per-chain work.
+//
+// Same mathematics as analyze_reg.cu (Theorem 1, Eq. 6, with Eqs. 1-5): one
+// system per group of 16 lanes, one chain per lane, Lemma 1's arrival counts
+// by exact multiply-shift division, and the 32-bit narrow sums (every
+// deadline below 2^27 - 16; a capped partial sum already exceeds every
+// deadline, so it decides each comparison with D as the true sum would).  It
+// differs in where the work goes:
+//
+//  - Relations cost one pass of a few instructions per chain pair: the
+//    same-executor and same-core sets come from __match_any_sync, lower- and
+//    higher-priority sets from one comparison each, and CPU blocking (Lemma 4)
+//    from the few lower-priority chains of the executor.
+//  - The test that decides whether Lemma 2's per-segment sum can beat Eq. 4
+//    below the deadline, and the exact per-segment fixed points it calls for,
+//    run when the chain's own recurrence is reached, with the lanes over the
+//    chain's higher-priority accelerator users.  A chain that turns out
+//    dependent on an unschedulable chain (the DEP rule) never pays for them;
+//    only its own recurrence reads a per-segment sum, so results are those of
+//    the eager order.
+//
+// Systems with more than 16 chains, or that fit the 32-bit bound but not the
+// narrow one, go to b.list_big (the 64-chain register-table kernel); systems
+// outside the 32-bit bound to b.list_wide (the int64 kernel).  One
+// accelerator, Lemma 4 as printed (blocking_mode 0), analysis and candidate
+// mode; the other modes keep their kernels.
+#include "reg_common.cuh"
+
+namespace {
+using namespace paam_reg;
+
+constexpr int LG = 16; // lanes per system = largest chain count
+
+struct LazySmem {
+    uint4 rel[LG];    // {hp, hpp, hps, first segment relative to the system's first}
+    uint4 rec[LG];    // {D, base = B + E, own = S* + delta blk (capped at D + 1), deps = delta eps}
+    uint4 seg[LG];    // {-, Amin*, blk, delta}
+    uint32_t emax[LG]; // longest callback, for Lemma 4's blocking
+    uint32_t m[LG];    // M*, for the same-bucket blocking with several buckets
+    int32_t bucket[LG];
+    uint8_t order[LG];
+};
+
+// ceil(t / T) + 1 (Lemma 1) times c, capped at 2^27 - 1 so that 16 lanes' sum fits 32 bits
+__device__ __forceinline__ uint32_t capped_term(uint32_t t, uint32_t tm2, uint32_t mg, uint32_t lg, uint32_t c)
+{
+    const uint64_t v = (uint64_t)rarrivals(t, tm2, mg, lg) * c;
+    return v < kNarrow - 1 ? (uint32_t)v : kNarrow - 1;
+}
+
+__device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t item, LazySmem &s, int lane,
+                            unsigned gm, int64_t *__restrict__ R_out, uint8_t *__restrict__ st_out,
+                            uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
+                            int32_t *wide_list, int32_t *wide_count)
+{
+    using Mask = uint32_t;
+    int64_t sys;
+    int32_t cand;
+    item_of(p, item, sys, cand);
+    if (p.K > 0 && p.early) { // candidate above the best schedulable one found so far
+        const int pruned = __shfl_sync(gm, cand_pruned(p, sys, cand) ? 1 : 0, 0, LG);
+        if (pruned) return;
+    }
+    const int64_t c0 = b.sys_chain_off[sys];
+    const int n = (int)(b.sys_chain_off[sys + 1] - c0);
+    if (n > LG) {
+        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
+        return;
+    }
+    const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.Kc + cand_of(p, sys, cand)) * p.nmax : nullptr;
+    const int32_t *xprio = p.K > 0 ? nullptr : b.exec_prio; // candidates: criticality-as-priority
+    const int64_t x0 = b.sys_exec_off[sys];
+    const uint64_t kappa2 = 2 * (uint64_t)p.kappa, eps = (uint64_t)p.eps;
+    const int64_t seg_base = n > 0 ? b.cb_seg_off[b.chain_cb_off[c0]] : 0;
+    const int j = lane;
+    const Mask jbit = 1u << j;
+
+    // ---- per-chain aggregates (Sec. II-C) -----------------------------------
+    uint32_t tm2 = 0, mg = 0, lg = 0, Dv = 0, Ev = 0, Sv = 0, Emx = 0, Mv = 0, Amn = 0, dlv = 0, seg0 = 0;
+    int32_t pr = INT32_MIN, ep = INT32_MIN, ex = -1 - j, co = -1 - j;
+    bool sp = false;
+    unsigned fit = 1, rank_ok = 1;
+    Mask rbit = 0;
+    const bool val = j < n;
+    if (val) {
+        const int64_t g = c0 + j;
+        const int64_t T = b.T[g], D = b.D[g];
+        ex = b.exec[g];
+        if (rank_row) { // candidate priority order: rank 0 is the highest priority
+            const int r = rank_row[j];
+            rank_ok = (r >= 0 && r < n) ? 1u : 0u;
+            rbit = rank_ok ? 1u << r : 0u;
+            pr = n - 1 - r;
+        } else {
+            pr = b.prio[g];
+        }
+        co = b.exec_core[x0 + ex];
+        if (xprio) ep = xprio[x0 + ex];
+        sp = b.spin[g] != 0;
+        const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
+        uint64_t E = 0, Emax = 0, S = 0, M = 0, Amin = ~0ull;
+#pragma unroll 4
+        for (int64_t cb = cb0; cb < cb1; ++cb) {
+            const uint64_t e = (uint64_t)b.E[cb];
+            E += e;
+            Emax = e > Emax ? e : Emax;
+        }
+        const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
+#pragma unroll 4
+        for (int64_t q = q0; q < q1; ++q) {
+            const uint64_t a = (uint64_t)b.A[q] + kappa2; // A* = A + 2 kappa
+            S += a;
+            M = a > M ? a : M;
+            Amin = a < Amin ? a : Amin;
+        }
+        const uint64_t dl = (uint64_t)(q1 - q0);
+        fit = ((uint64_t)T < kFitR && (uint64_t)D < kFitR && E < kFitR && S < kFitR && dl < kFitR &&
+               (eps == 0 || dl <= (kFitR - 1) / eps))
+                  ? 1u
+                  : 0u;
+        if (fit) rdivisor((uint32_t)T, tm2, mg, lg);
+        Dv = (uint32_t)D;
+        Ev = (uint32_t)E;
+        Sv = (uint32_t)S;
+        Emx = (uint32_t)Emax;
+        Mv = (uint32_t)M;
+        Amn = dl ? (uint32_t)(Amin < kFitR ? Amin : 0) : 0;
+        dlv = (uint32_t)dl;
+        seg0 = (uint32_t)(q0 - seg_base);
+    }
+    const unsigned sh = threadIdx.x & 16u; // the group's first lane in the warp
+    const Mask users = __ballot_sync(gm, val && dlv != 0) >> sh;
+    const Mask spins = __ballot_sync(gm, sp) >> sh;
+    const Mask all = (n >= 32) ? ~0u : ((1u << n) - 1u);
+    if (rank_row) { // a candidate must be a permutation of 0..n-1
+        rank_ok = __reduce_and_sync(gm, rank_ok);
+        rbit = __reduce_or_sync(gm, rbit);
+        if (!rank_ok || rbit != all) {
+            if (lane == 0) {
+                atomicExch(p.err, PAAM_E_INVAL);
+                if (p.cand_ok) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = 0;
+            }
+            return;
+        }
+    }
+    if (!__reduce_and_sync(gm, fit)) { // outside the 32-bit bound
+        if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)item;
+        return;
+    }
+    if (__reduce_max_sync(gm, Dv) >= kNarrow - LG) { // inside it but not narrow
+        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
+        return;
+    }
+
+    // ---- relations (Lemma 4, Theorem 1, Eq. 3), analysis order ---------------
+    const unsigned xm = __match_any_sync(gm, ex); // lanes of the same executor (unique keys past n)
+    const Mask samex = xm >> sh;
+    const Mask corem = __match_any_sync(gm, co) >> sh;
+    if (!xprio) ep = __reduce_max_sync(xm, pr); // criticality-as-priority: highest chain priority on the executor
+    const bool one_bucket = p.n_buckets == 1;
+    Mask higher = 0, ehigher = 0;
+    int pos = 0;
+    uint32_t blk = 0;
+    for (int t = 0; t < n; ++t) {
+        const int32_t pt = __shfl_sync(gm, pr, t, LG), et = __shfl_sync(gm, ep, t, LG);
+        const uint32_t mt = __shfl_sync(gm, Mv, t, LG);
+        const bool hi = pt > pr;
+        const Mask bit = 1u << t;
+        higher |= hi ? bit : 0u;
+        ehigher |= et > ep ? bit : 0u;
+        pos += (et > ep) || (et == ep && hi); // executor priority, then chain priority
+        // with one bucket every user shares it: the longest lower-priority request (R2-R3)
+        if (one_bucket && pt < pr && ((users >> t) & 1) && mt > blk) blk = mt;
+    }
+    const Mask hp = samex & higher;                 // hp(c), Lemma 4
+    const Mask hpp = corem & ~samex & ehigher;      // hpp(c), Theorem 1
+    const Mask hps = users & higher;                // hps(c), Eq. 3
+    const bool user = (users >> j) & 1;
+    if (!user) blk = 0;
+    s.emax[j] = Emx;
+    uint32_t Bv = 0;
+    __syncwarp(gm);
+    for (Mask lo = samex & ~higher & ~jbit & all; lo; lo &= lo - 1) // Lemma 4: one LP callback on the executor
+        Bv = umax(Bv, s.emax[__ffs(lo) - 1]);
+    if (!one_bucket) { // bucket = floor(rank * n_buckets / |U|), rank among the users (R2)
+        const int32_t bk = user ? (int32_t)((uint32_t)__popc(hps) * (uint32_t)p.n_buckets / (uint32_t)__popc(users))
+                                : -1;
+        s.bucket[j] = bk;
+        s.m[j] = Mv;
+        __syncwarp(gm);
+        if (user)
+            for (Mask lo = users & ~higher & ~jbit; lo; lo &= lo - 1) {
+                const int l = __ffs(lo) - 1;
+                if (s.bucket[l] == bk) blk = umax(blk, s.m[l]);
+            }
+    }
+
+    // ---- own recurrence terms ------------------------------------------------
+    if (val) {
+        const uint64_t own = (uint64_t)Sv + (uint64_t)dlv * blk;
+        const uint64_t cap = (uint64_t)Dv + 1; // values above D act the same as D + 1
+        s.rel[j] = make_uint4(hp, hpp, hps, seg0);
+        s.rec[j] = make_uint4(Dv, Bv + Ev, (uint32_t)(own < cap ? own : cap), (uint32_t)((uint64_t)dlv * eps));
+        s.seg[j] = make_uint4(0u, Amn, blk, dlv);
+        s.order[pos] = (uint8_t)j;
+    }
+    __syncwarp(gm);
+
+    // ---- Theorem 1 (Eq. 6), chain by chain -----------------------------------
+    uint32_t Ehp = Ev, Ehpp = Ev + (sp ? 0u : (uint32_t)((uint64_t)dlv * eps)), Rv = 0;
+    Mask sched = 0, dep = 0;
+    const uint32_t k2 = (uint32_t)kappa2;
+    for (int step = 0; step < n; ++step) {
+        const int c = s.order[step];
+        const uint4 rl = s.rel[c];
+        const Mask cbit = 1u << c;
+        if ((rl.x | (rl.y & spins)) & ~sched) { // a needed H*_h is not available
+            dep |= cbit;
+            if (rank_row) break; // a candidate fails at its first unschedulable chain
+            continue;
+        }
+        const uint4 rc = s.rec[c];
+        const uint32_t D32 = rc.x, base = rc.y, own = rc.z, deps = rc.w;
+        const uint32_t ccoef = ((rl.x >> j) & 1) ? Ehp : (((rl.y >> j) & 1) ? Ehpp : 0u);
+        const uint32_t acoef = ((rl.z >> j) & 1) ? Sv : 0u;
+        uint32_t Hs = kInfR; // Lemma 2's per-segment sum; unbounded unless computed below
+        const uint4 sg = s.seg[c];
+        const uint32_t dl = sg.w;
+        bool capped = false;
+        if (dl) {
+            // Lemma 2 matters only if its sum can fall below Eq. 4 at some R <= D: Eq. 4 is
+            // at most own + sum_h mu_h(D) S_h there, and every segment's fixed point is at
+            // least x + f sum_h S_h with x = A* + blk, f = 2 if x >= 1 (mu >= 2 for t >= 1)
+            const uint32_t hchd = umin(__reduce_add_sync(gm, capped_term(D32, tm2, mg, lg, acoef)), kNarrow);
+            const uint32_t sums = umin(__reduce_add_sync(gm, umin(acoef, kNarrow - 1)), kNarrow);
+            const uint64_t f = ((uint64_t)sg.y + sg.z) >= 1 ? 2 : 1;
+            if (f * dl * sums < hchd) {
+                const uint32_t lim = umin(own + hchd, D32 + 1); // the sum matters only below this
+                const uint32_t blkc = sg.z;
+                const int64_t qb = seg_base + rl.w;
+                uint32_t H32 = 0;
+                bool inf = false;
+                for (uint32_t q = 0; q < dl && !inf; ++q) {
+                    const uint32_t hb = (uint32_t)b.A[qb + q] + k2 + blkc;
+                    uint32_t h = hb; // the recurrence starts with the first two terms
+                    uint32_t ev = 0;
+                    for (;;) {
+                        if (h > D32 || H32 + h >= lim) {
+                            inf = true;
+                            break;
+                        }
+                        if (ev++ == kIterCap) {
+                            inf = capped = true;
+                            break;
+                        }
+                        const uint32_t nh =
+                            hb + umin(__reduce_add_sync(gm, capped_term(h, tm2, mg, lg, acoef)), kNarrow);
+                        if (nh == h) break; // strictly increasing until here, bounded by D
+                        h = nh;
+                    }
+                    H32 += h;
+                }
+                if (!inf) Hs = H32;
+            }
+        }
+        if (capped) { // a segment recurrence was cut short: no bound (PAAM_ST_ITERCAP)
+            if (j == c) Rv = kCapR;
+            if (rank_row) break;
+            continue;
+        }
+        // start: B + E + H* with the interference part of Eq. 4 empty
+        uint32_t R = base + (dl ? umin(Hs, own) + deps : 0u);
+        uint32_t hs = 0, ev = 0;
+        bool ok = false;
+        if (R <= D32) {
+            // every deadline is below 2^27 - 16: in the loop base <= R <= D, each group
+            // sum is capped at 2^27 where it is added (a capped term already exceeds D)
+            for (;;) {
+                if (ev++ == kIterCap) break;
+                const uint32_t cs = __reduce_add_sync(gm, capped_term(R, tm2, mg, lg, ccoef));
+                const uint32_t as = __reduce_add_sync(gm, capped_term(R, tm2, mg, lg, acoef));
+                hs = 0;
+                if (dl) {
+                    const uint32_t hch = own + umin(as, kNarrow); // Eq. 4
+                    hs = umin(Hs, hch) + deps;                    // Eq. 1 with min(Eq. 3, Eq. 4)
+                }
+                const uint32_t Rn = base + umin(hs, kNarrow) + umin(cs, kNarrow);
+                if (Rn == R) {
+                    ok = true;
+                    break;
+                }
+                R = Rn;
+                if (R > D32) break;
+            }
+        }
+        if (ok) {
+            sched |= cbit;
+            if (j == c) {
+                Rv = R;
+                Ehp = Ev + hs;
+                if (sp) Ehpp = Ev + hs;
+            }
+        } else {
+            if (ev > kIterCap && j == c) Rv = kCapR; // the recurrence was cut short (PAAM_ST_ITERCAP)
+            if (rank_row) break;
+        }
+    }
+
+    // ---- outputs -------------------------------------------------------------
+    if (rank_row) {
+        if (lane == 0) {
+            const bool ok = sched == all;
+            if (p.cand_ok) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = ok ? 1 : 0;
+            if (ok) atomicMin(p.first_ok + sys, cand);
+        }
+        __syncwarp(gm);
+        return;
+    }
+    if (val) {
+        const bool ok = (sched >> j) & 1;
+        R_out[c0 + j] = ok ? (int64_t)Rv : -1;
+        st_out[c0 + j] = ok ? PAAM_ST_SCHED
+                            : (Rv == kCapR ? PAAM_ST_ITERCAP : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
+    }
+    if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
+    __syncwarp(gm);
+}
+
+__global__ void __launch_bounds__(256, 4) analyze_lazy_kernel(BatchDev b, AnalysisParams p, int64_t *R, uint8_t *st,
+                                                              uint8_t *verdict, int32_t *big_list,
+                                                              int32_t *big_count, int32_t *wide_list,
+                                                              int32_t *wide_count)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int groups = blockDim.x / LG;
+    const int grp = threadIdx.x / LG;
+    const int lane = threadIdx.x % LG;
+    LazySmem &s = reinterpret_cast<LazySmem *>(smem_raw)[grp];
+    const unsigned gm = rgroup_mask<LG>();
+    const int64_t n_items = p.K > 0 ? b.n_sys * p.K : b.n_sys;
+    for_each_item<LG>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
+        lazy_system(b, p, i, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
+    });
+}
+
+} // namespace
+
+int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream)
+{
+    if (list || count) return PAAM_E_INVAL; // first pass only: every item of the launch
+    if (threads % 32 != 0 || threads > 256) return PAAM_E_INVAL;
+    const int groups = threads / LG;
+    const size_t smem = sizeof(LazySmem) * groups;
+    auto kern = analyze_lazy_kernel;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (max_items + groups - 1) / groups;
+    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, bt->list_big, bt->counts,
+                                                      bt->list_wide, bt->counts + 1);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    return PAAM_OK;
+}

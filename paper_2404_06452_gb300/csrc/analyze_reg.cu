@@ -260,7 +260,6 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
 
     // ---- own recurrence terms to shared memory ------------------------------
     Mask need_exact = 0;
-    Mask capm = 0; // chains whose recurrence reached kIterCap evaluations
 #pragma unroll
     for (int k = 0; k < CPL; ++k) {
         if (!val[k]) continue;
@@ -296,7 +295,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             const int64_t g = c0 + c;
             const int64_t cb1 = b.chain_cb_off[g + 1];
             uint64_t Hsum = 0, hold = 0;
-            bool seg_inf = false, hold_inf = false;
+            bool seg_inf = false, hold_inf = false, capped = false;
             for (int64_t cb = b.chain_cb_off[g]; cb < cb1; ++cb) {
                 uint64_t t = (uint64_t)b.E[cb];
                 bool t_inf = false;
@@ -312,8 +311,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                             break;
                         }
                         if (ev++ == kIterCap) {
-                            inf = true;
-                            capm |= (Mask)1 << c;
+                            inf = capped = true;
                             break;
                         }
                         const uint64_t part = (uint64_t)rarrivals((uint32_t)h, tm2[0], mg[0], lg[0]) * acoef;
@@ -333,7 +331,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             }
             if (lane == 0) {
                 const uint64_t cap = (uint64_t)Dc + 1;
-                s.seg[c].x = seg_inf ? kInfR : (uint32_t)(Hsum < cap ? Hsum : cap);
+                s.seg[c].x = capped ? kCapR : seg_inf ? kInfR : (uint32_t)(Hsum < cap ? Hsum : cap);
                 hold_s[c] = hold_inf || hold >= kHoldInf ? kHoldInf : (uint32_t)hold;
             }
             __syncwarp(gm);
@@ -361,6 +359,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         for (int k = 0; k < CPL; ++k) acoef[k] = ((hps >> (lane + G * k)) & 1) ? Sv[k] : 0u;
         uint64_t Hsum = 0;
         bool inf = false;
+        uint32_t ev = 0; // evaluations of the current segment's recurrence
         if (narrow) {
             // 32 bits hold every value: base below 2^31, h <= D below 2^27, the
             // group sum capped at 2^27 (a capped sum exceeds D as the true one would)
@@ -369,7 +368,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             for (uint32_t q = 0; q < dl && !inf; ++q) {
                 const uint32_t base = (uint32_t)b.A[seg_base + s.seg0[c] + q] + k2 + blkc;
                 uint32_t h = base;
-                uint32_t ev = 0;
+                ev = 0;
                 for (;;) {
                     if (h > Dc || H32 + h >= lim) {
                         inf = true;
@@ -377,7 +376,6 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                     }
                     if (ev++ == kIterCap) {
                         inf = true;
-                        capm |= (Mask)1 << c;
                         break;
                     }
                     uint64_t part = 0;
@@ -395,7 +393,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             for (uint32_t q = 0; q < dl && !inf; ++q) {
                 const uint64_t base = (uint64_t)b.A[seg_base + s.seg0[c] + q] + kappa2 + blkc;
                 uint64_t h = base; // the recurrence starts with the first two terms
-                uint32_t ev = 0;
+                ev = 0;
                 for (;;) {
                     if (h > Dc || Hsum + h >= lim) {
                         inf = true;
@@ -403,7 +401,6 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                     }
                     if (ev++ == kIterCap) {
                         inf = true;
-                        capm |= (Mask)1 << c;
                         break;
                     }
                     uint64_t part = 0;
@@ -417,7 +414,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                 Hsum += h;
             }
         }
-        if (lane == 0 && !inf) s.seg[c].x = (uint32_t)Hsum;
+        if (lane == 0 && (!inf || ev > kIterCap)) s.seg[c].x = ev > kIterCap ? kCapR : (uint32_t)Hsum;
         __syncwarp(gm);
     }
 
@@ -439,10 +436,6 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             if (TARGET ? c == tgt : rank_row != nullptr) break; // a candidate fails at its first unschedulable chain
             continue;
         }
-        if (capm & cbit) { // a segment recurrence was cut short: no bound (PAAM_ST_ITERCAP)
-            if (TARGET ? c == tgt : rank_row != nullptr) break;
-            continue;
-        }
         uint32_t ccoef[CPL], acoef[CPL];
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
@@ -451,25 +444,29 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             acoef[k] = ((hps >> j) & 1) ? Sv[k] : 0u;
         }
         const uint4 rc = s.rec[c], sg = s.seg[c];
+        if (sg.x == kCapR) { // a segment recurrence was cut short: no bound (PAAM_ST_ITERCAP)
+#pragma unroll
+            for (int k = 0; k < CPL; ++k)
+                if (lane + G * k == c) Rv[k] = kCapR;
+            if (TARGET ? c == tgt : rank_row != nullptr) break;
+            continue;
+        }
         const uint64_t Dc = rc.x, base = rc.y, own = rc.z, deps = rc.w, dl = sg.w;
         const uint64_t Hseg = sg.x == kInfR ? ~0ull : (uint64_t)sg.x;
         // start: B + E + H* with the interference part of Eq. 4 empty
         uint64_t R = base + (dl ? (Hseg < own ? Hseg : own) + deps : 0);
         uint64_t hs = 0;
         bool ok = false;
+        uint32_t ev = 0; // evaluations of the recurrence
         if (narrow) {
             // the same iteration in 32 bits: every deadline is below 2^27 - 64, in
             // the loop base <= R <= D, the group sums are below 2^32, and each sum
             // is capped at 2^27 where it is added (a capped term already exceeds D)
             const uint32_t D32 = rc.x, base32 = rc.y, own32 = rc.z, deps32 = rc.w, Hs32 = sg.x;
             uint32_t R32 = (uint32_t)R, hs32 = 0;
-            uint32_t ev = 0;
             if (R <= Dc) {
                 for (;;) {
-                    if (ev++ == kIterCap) {
-                        capm |= cbit;
-                        break;
-                    }
+                    if (ev++ == kIterCap) break;
                     uint64_t cpu = 0, acc = 0;
 #pragma unroll
                     for (int k = 0; k < CPL; ++k) {
@@ -496,12 +493,8 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             R = R32;
             hs = hs32;
         } else {
-            uint32_t ev = 0;
             while (R <= Dc) {
-                if (ev++ == kIterCap) {
-                    capm |= cbit;
-                    break;
-                }
+                if (ev++ == kIterCap) break;
                 uint64_t cpu = 0, acc = 0;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
@@ -533,8 +526,12 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                     Ehp[k] = Ev[k] + (uint32_t)hs;
                     if (sp[k]) Ehpp[k] = Ev[k] + (uint32_t)hs;
                 }
-        } else if (!TARGET && rank_row) {
-            break;
+        } else {
+            if (ev > kIterCap) // the recurrence was cut short (PAAM_ST_ITERCAP)
+#pragma unroll
+                for (int k = 0; k < CPL; ++k)
+                    if (lane + G * k == c) Rv[k] = kCapR;
+            if (!TARGET && rank_row) break;
         }
         if (TARGET && c == tgt) break; // chains after the target cannot change its result
     }
@@ -561,8 +558,8 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         const bool ok = (sched >> j) & 1;
         R_out[c0 + j] = ok ? (int64_t)Rv[k] : -1;
         st_out[c0 + j] = ok ? PAAM_ST_SCHED
-                            : (((capm >> j) & 1) ? PAAM_ST_ITERCAP
-                                                 : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
+                            : (Rv[k] == kCapR ? PAAM_ST_ITERCAP
+                                              : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
     }
     if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
     __syncwarp(gm);

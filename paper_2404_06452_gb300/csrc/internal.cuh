@@ -228,6 +228,14 @@ struct LaunchCfg {
 // within each window of consecutive systems.
 int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, cudaStream_t stream);
 
+// Register-table kernel with lazy per-chain work (analyze_lazy.cu): 16 lanes
+// per system, first pass only (list == count == nullptr).  Systems over 16
+// chains, or with a deadline at or above kLazyNarrowD inside the 32-bit
+// bound, go to b->list_big; systems outside the 32-bit bound to b->list_wide.
+int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
+constexpr unsigned long long kLazyNarrowD = (1ull << 27) - 16;
+
 // Register-table kernels (analyze_reg.cu): G lanes per system, CPL chains per lane.
 template <int G, int CPL>
 int launch_reg(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,

@@ -12,6 +12,9 @@ namespace paam_reg {
 
 constexpr uint64_t kFitR = 1ull << 30;
 constexpr uint32_t kInfR = 0xFFFFFFFFu;
+// a per-segment sum, or a chain's R, whose recurrence was stopped at kIterCap
+// evaluations (PAAM_ST_ITERCAP); above every 32-bit-bound value
+constexpr uint32_t kCapR = 0xFFFFFFFEu;
 
 template <int NMAX>
 struct RegMask {
