@@ -156,8 +156,10 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
                  16: "analyze_reg1_kernel<32> (work queue)", 17: "analyze_reg1_kernel<16> (work queue, size-binned)",
                  18: "analyze_reg1_kernel<32> (work queue, size-binned)",
                  19: "analyze_reg_kernel<8, 2> (work queue, size-binned)",
-                 20: "analyze_lazy_kernel", 21: "analyze_lazy_kernel (work queue)",
-                 22: "analyze_lazy_kernel (work queue, size-binned)"}
+                 20: "analyze_lazy_kernel<4>", 21: "analyze_lazy_kernel<4> (work queue)",
+                 22: "analyze_lazy_kernel<4> (work queue, size-binned)",
+                 23: "analyze_lazy_kernel<5> (work queue, size-binned)",
+                 24: "analyze_lazy_kernel<6> (work queue, size-binned)", 25: "analyze_lazy_kernel<5> (work queue)"}
 
 
 # DRAM read + write per system of the analysis kernel, from ncu captures

@@ -535,7 +535,7 @@ const Variant kVariants[] = {
     {0, 8, 64, launch_fast<8, 64>},   {0, 16, 64, launch_fast<16, 64>}, {0, 32, 64, launch_fast<32, 64>},
     {1, 4, 16, launch_reg<4, 4>},     {1, 8, 16, launch_reg<8, 2>},     {1, 16, 16, launch_reg<16, 1>},
     {1, 16, 32, launch_reg<16, 2>},   {1, 32, 32, launch_reg<32, 1>},   {1, 32, 64, launch_reg<32, 2>},
-    {2, 16, 16, launch_lazy},
+    {2, 16, 16, launch_lazy<4>}, {3, 16, 16, launch_lazy<5>}, {4, 16, 16, launch_lazy<6>},
 };
 
 LaunchFn find_variant(int impl, int G, int maxn)
@@ -560,6 +560,8 @@ const LaunchCfg kLaunchCfgs[] = {
     {1, 16, 16, 0, 16, 256, 2, 1}, {1, 32, 32, 1, 32, 256, 2, 1}, {1, 8, 16, 0, 16, 256, 2, 1},
     // register tables with lazy per-chain work (analyze_lazy.cu): static shares, queue, queue by size
     {2, 16, 16, 1, 32, 256, 0, 0}, {2, 16, 16, 1, 32, 256, 2, 0}, {2, 16, 16, 1, 32, 256, 2, 1},
+    // the same with 5 and 6 resident blocks per SM (fewer registers per thread)
+    {3, 16, 16, 1, 32, 256, 2, 1}, {4, 16, 16, 1, 32, 256, 2, 1}, {3, 16, 16, 1, 32, 256, 2, 0},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
 static_assert(kDefaultLaunchCfg < (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0])), "default configuration");
@@ -614,7 +616,7 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     if (rc != PAAM_OK) return rc;
     ++k;
     // the lazy kernel also defers systems inside the 32-bit bound that are not narrow
-    const bool lazy_defers = cfg.impl_small == 2 && b->stats[ST_DMAX] >= kLazyNarrowD;
+    const bool lazy_defers = cfg.impl_small >= 2 && b->stats[ST_DMAX] >= kLazyNarrowD;
     if (b->max_chains > cfg.maxn_small || lazy_defers) {
         rc = bigfn(b, pb, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
         if (rc != PAAM_OK) return rc;

@@ -31,14 +31,14 @@ using namespace paam_reg;
 
 constexpr int LG = 16; // lanes per system = largest chain count
 
+// per chain, stored at the chain's position in the analysis order
 struct LazySmem {
     uint4 rel[LG];    // {hp, hpp, hps, first segment relative to the system's first}
     uint4 rec[LG];    // {D, base = B + E, own = S* + delta blk (capped at D + 1), deps = delta eps}
-    uint4 seg[LG];    // {-, Amin*, blk, delta}
+    uint4 seg[LG];    // {chain index, Amin*, blk, delta}
     uint32_t emax[LG]; // longest callback, for Lemma 4's blocking
     uint32_t m[LG];    // M*, for the same-bucket blocking with several buckets
     int32_t bucket[LG];
-    uint8_t order[LG];
 };
 
 // ceil(t / T) + 1 (Lemma 1) times c, capped at 2^27 - 1 so that 16 lanes' sum fits 32 bits
@@ -199,10 +199,9 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     if (val) {
         const uint64_t own = (uint64_t)Sv + (uint64_t)dlv * blk;
         const uint64_t cap = (uint64_t)Dv + 1; // values above D act the same as D + 1
-        s.rel[j] = make_uint4(hp, hpp, hps, seg0);
-        s.rec[j] = make_uint4(Dv, Bv + Ev, (uint32_t)(own < cap ? own : cap), (uint32_t)((uint64_t)dlv * eps));
-        s.seg[j] = make_uint4(0u, Amn, blk, dlv);
-        s.order[pos] = (uint8_t)j;
+        s.rel[pos] = make_uint4(hp, hpp, hps, seg0);
+        s.rec[pos] = make_uint4(Dv, Bv + Ev, (uint32_t)(own < cap ? own : cap), (uint32_t)((uint64_t)dlv * eps));
+        s.seg[pos] = make_uint4((uint32_t)j, Amn, blk, dlv);
     }
     __syncwarp(gm);
 
@@ -211,20 +210,18 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     Mask sched = 0, dep = 0;
     const uint32_t k2 = (uint32_t)kappa2;
     for (int step = 0; step < n; ++step) {
-        const int c = s.order[step];
-        const uint4 rl = s.rel[c];
+        const uint4 rl = s.rel[step], rc = s.rec[step], sg = s.seg[step];
+        const int c = (int)sg.x;
         const Mask cbit = 1u << c;
         if ((rl.x | (rl.y & spins)) & ~sched) { // a needed H*_h is not available
             dep |= cbit;
             if (rank_row) break; // a candidate fails at its first unschedulable chain
             continue;
         }
-        const uint4 rc = s.rec[c];
         const uint32_t D32 = rc.x, base = rc.y, own = rc.z, deps = rc.w;
         const uint32_t ccoef = ((rl.x >> j) & 1) ? Ehp : (((rl.y >> j) & 1) ? Ehpp : 0u);
         const uint32_t acoef = ((rl.z >> j) & 1) ? Sv : 0u;
         uint32_t Hs = kInfR; // Lemma 2's per-segment sum; unbounded unless computed below
-        const uint4 sg = s.seg[c];
         const uint32_t dl = sg.w;
         bool capped = false;
         if (dl) {
@@ -326,10 +323,12 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     __syncwarp(gm);
 }
 
-__global__ void __launch_bounds__(256, 4) analyze_lazy_kernel(BatchDev b, AnalysisParams p, int64_t *R, uint8_t *st,
-                                                              uint8_t *verdict, int32_t *big_list,
-                                                              int32_t *big_count, int32_t *wide_list,
-                                                              int32_t *wide_count)
+// BLOCKS resident blocks of 256 threads per SM: the register budget per thread
+template <int BLOCKS>
+__global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, AnalysisParams p, int64_t *R,
+                                                                   uint8_t *st, uint8_t *verdict, int32_t *big_list,
+                                                                   int32_t *big_count, int32_t *wide_list,
+                                                                   int32_t *wide_count)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int groups = blockDim.x / LG;
@@ -345,6 +344,7 @@ __global__ void __launch_bounds__(256, 4) analyze_lazy_kernel(BatchDev b, Analys
 
 } // namespace
 
+template <int BLOCKS>
 int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                 const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream)
 {
@@ -352,7 +352,7 @@ int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8
     if (threads % 32 != 0 || threads > 256) return PAAM_E_INVAL;
     const int groups = threads / LG;
     const size_t smem = sizeof(LazySmem) * groups;
-    auto kern = analyze_lazy_kernel;
+    auto kern = analyze_lazy_kernel<BLOCKS>;
     PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -366,3 +366,10 @@ int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8
     PAAM_CUDA_TRY(cudaGetLastError());
     return PAAM_OK;
 }
+
+template int launch_lazy<4>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                            const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_lazy<5>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                            const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_lazy<6>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                            const int32_t *, const int32_t *, int64_t, int, cudaStream_t);

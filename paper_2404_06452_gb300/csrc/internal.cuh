@@ -232,6 +232,8 @@ int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, cudaStream_t st
 // per system, first pass only (list == count == nullptr).  Systems over 16
 // chains, or with a deadline at or above kLazyNarrowD inside the 32-bit
 // bound, go to b->list_big; systems outside the 32-bit bound to b->list_wide.
+// BLOCKS: resident blocks of 256 threads per SM the register budget is set for (4, 5, 6).
+template <int BLOCKS>
 int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                 const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
 constexpr unsigned long long kLazyNarrowD = (1ull << 27) - 16;
@@ -242,9 +244,10 @@ int launch_reg(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_
                const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
 extern const LaunchCfg kLaunchCfgs[];
 extern const int kNumLaunchCfgs;
-// Configuration of a batch before any autotuning: 16-lane register tables,
-// work queue (the fastest on the 1M-system and the 10k x 256 search workloads)
-constexpr int kDefaultLaunchCfg = 12;
+// Configuration of a batch before any autotuning: the lazy register-table
+// kernel with six resident blocks per SM, work queue, systems by size (the
+// fastest on the 1M-system and the 10k x 256 search workloads)
+constexpr int kDefaultLaunchCfg = 24;
 
 // Evaluations any one fixed-point recurrence may take before the analysis
 // kernels stop it with PAAM_ST_ITERCAP.  Validation refuses systems whose
