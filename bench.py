@@ -440,7 +440,12 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
 
     import paam_gen
 
-    flops_row = 2.0 * (1024 * 256 + 256 * 256 + 256 * 256 + 256 * 64)  # one forward pass, one row
+    # the method's own flops: training runs the full 1,024-wide first layer forward,
+    # and backward the weight gradients of every layer plus the input gradients of
+    # layers 2-4; the ranking reads 16 features for each of a system's chains, so its
+    # first layer has K = 16 x (largest chain count), rounded up to 64 (256 for 16-chain systems)
+    fwd = lambda kx: 2.0 * (kx * 256 + 256 * 256 + 256 * 256 + 256 * 64)
+    flops_train_row = fwd(1024) + fwd(1024) + 2.0 * (256 * 256 + 256 * 256 + 256 * 64)
     sources = tuple(sources)
     chunk = 1_000_000
     model, t_train, t_label, losses, rows = None, 0.0, 0.0, [], 0
@@ -493,6 +498,7 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
     pkg.search(ctx, b, r)
     t_ex, (first_x, cand_x) = _timed(lambda: pkg.search(ctx, b, r), 3)
     S = sy.n_sys
+    kx = min(1024, (16 * int(sy.chains_per_system().max()) + 63) // 64 * 64)  # the first layer's K
     order_k = torch.empty((S, top_k), dtype=torch.int32, device="cuda")
     order_all = torch.empty((S, K), dtype=torch.int32, device="cuda")
     first = torch.empty(S, dtype=torch.int32, device="cuda")
@@ -539,7 +545,8 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
     return {
         "train": {"systems": rows, "sources": list(sources), "epochs": epochs, "lr": lr, "minibatch": 8192,
                   "label_analysis_s": round(t_label, 4), "train_s": round(t_train, 4),
-                  "train_tflops": 3 * flops_row * rows * epochs / t_train / 1e12, "chunk_loss": losses,
+                  "train_tflops": flops_train_row * rows * epochs / t_train / 1e12,
+                  "train_flops_per_row": flops_train_row, "chunk_loss": losses,
                   "heldout_mae_R_over_D": mae},
         "workload": f"cfg4s: {S} systems x {K} candidate orders",
         "exhaustive_systems_per_s": S / t_ex, "exhaustive_ms": t_ex * 1e3,
@@ -547,7 +554,7 @@ def surrogate_bench(pkg, ctx, train_sys, n_search, top_k, epochs=TRAIN_EPOCHS, l
         "top_k": top_k, "pinned_seed_slots": SEARCH_PINNED,
         "guided_systems_per_s": S / t_g, "guided_ms": t_g * 1e3,
         "speedup_vs_exhaustive": t_ex / t_g, "speedup_vs_early_exit": t_ee / t_g,
-        "infer_ms": t_inf * 1e3, "infer_tflops": flops_row * S * K / t_inf / 1e12,
+        "infer_ms": t_inf * 1e3, "infer_tflops": fwd(kx) * S * K / t_inf / 1e12, "infer_flops_per_candidate": fwd(kx),
         "false_accepts": false_accepts, "recall": recall, "recall_network_only": recall_net,
         "recall_first_k_slots": slot_recall,
         "recall_random_k": rand_recall, "recall_at_k": recall_at,
