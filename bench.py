@@ -53,6 +53,8 @@ def parse():
                     help="only measure the device preemption cost, ITERS iterations per kernel kind")
     ap.add_argument("--kappa-iters", type=int, default=300, help="preemption-cost iterations in the full run")
     ap.add_argument("--launch-config", type=int, default=None, help="fixed launch configuration (no autotune)")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3"],
+                    help="the analysis workload of the timed step (default: the 1M-system one)")
     ap.add_argument("--no-workloads", action="store_true", help="skip the other analysis workloads (cfg1, cfg3)")
     ap.add_argument("--workload-steps", type=int, default=20, help="timed steps of each other workload")
     return ap.parse_args()
@@ -172,6 +174,12 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
 TRAFFIC_PER_SYSTEM = {12: 934.004992e6 / 500_000, 17: 937.245184e6 / 500_000}
 # the same for the other workloads, keyed by (workload, launch configuration)
 TRAFFIC_OTHER = {}
+
+
+def traffic_per_system(workload: str, cfg_index: int):
+    if workload == "cfg2":
+        return TRAFFIC_PER_SYSTEM.get(cfg_index)
+    return TRAFFIC_OTHER.get((workload, cfg_index))
 # Executed warp-instructions per system of the same kernels and captures
 # (smsp__inst_executed.sum / 500,000 systems): the instruction-issue side of
 # the kernel, against the issue peak of 152 SMs x 4 schedulers x 1 per clock.
@@ -240,7 +248,7 @@ def workload_bench(pkg, ctx, cfg, steps, warmup, e2e_steps, with_cpu):
     ms = float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
     alg = algorithmic_bytes(sy)
     pk = peaks()
-    traffic = TRAFFIC_OTHER.get((cfg, cfg_index))
+    traffic = traffic_per_system(cfg, cfg_index)
     out = {"workload": w["desc"], "systems": sy.n_sys, "chains": sy.n_chain, "steps": steps, "warmup": warmup,
            "ms_per_step": ms, "chains_per_s": sy.n_chain / (ms / 1e3), "systems_per_s": sy.n_sys / (ms / 1e3),
            "launch_config": cfg_index, "kernel": CONFIG_KERNEL.get(cfg_index, "analysis kernel"),
@@ -857,12 +865,12 @@ def run_ours(args):
     alg = algorithmic_bytes(sy)
     kern_ms = ms_per_step  # one analysis kernel per step
     achieved = alg / (kern_ms / 1e3) / 1e9
-    traffic = TRAFFIC_PER_SYSTEM.get(cfg_index)
+    traffic = traffic_per_system(WORKLOAD, cfg_index)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None if traffic is None else traffic * sy.n_sys,
                 "traffic_src": "ncu capture of 500k systems, scaled per system" if traffic else None,
                 "peak_src": pk["src"],
-                "issue": None if cfg_index not in WARP_INST_PER_SYSTEM else {
+                "issue": None if WORKLOAD != "cfg2" or cfg_index not in WARP_INST_PER_SYSTEM else {
                     "bound": "issue", "unit": "warp-instructions/s",
                     "achieved": WARP_INST_PER_SYSTEM[cfg_index] * sy.n_sys / (kern_ms / 1e3),
                     "peak": ISSUE_PEAK,
@@ -924,7 +932,7 @@ def run_ours(args):
     workloads = None
     if rank == 0 and world == 1 and not args.no_workloads:
         workloads = {cfg: workload_bench(pkg, ctx, cfg, args.workload_steps, max(3, args.warmup), 3,
-                                         not args.no_cpu_baseline) for cfg in EXTRA_WORKLOADS}
+                                         not args.no_cpu_baseline) for cfg in EXTRA_WORKLOADS if cfg != WORKLOAD}
 
     # ---- priority search and surrogate (single GPU, rank 0) -------------------
     search = surrogate = None
@@ -964,7 +972,10 @@ def run_ours(args):
 
 
 def main():
+    global WORKLOAD, WORKLOAD_DESC
     args = parse()
+    if args.workload != WORKLOAD:
+        WORKLOAD, WORKLOAD_DESC = args.workload, EXTRA_WORKLOADS[args.workload]["desc"]
     if args.impl == "reference":
         run_reference(args)
     else:
