@@ -158,35 +158,33 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     const Mask corem = __match_any_sync(gm, co) >> sh;
     if (!xprio) ep = __reduce_max_sync(xm, pr); // criticality-as-priority: highest chain priority on the executor
     const bool one_bucket = p.n_buckets == 1;
+    // higher chain priority and higher executor priority, one comparison each per chain
     Mask higher = 0, ehigher = 0;
-    int pos = 0;
-    uint32_t blk = 0;
-    for (int t = 0; t < n; ++t) {
+#pragma unroll
+    for (int t = 0; t < LG; ++t) {
         const int32_t pt = __shfl_sync(gm, pr, t, LG), et = __shfl_sync(gm, ep, t, LG);
-        const uint32_t mt = __shfl_sync(gm, Mv, t, LG);
-        const bool hi = pt > pr;
-        const Mask bit = 1u << t;
-        higher |= hi ? bit : 0u;
-        ehigher |= et > ep ? bit : 0u;
-        pos += (et > ep) || (et == ep && hi); // executor priority, then chain priority
-        // with one bucket every user shares it: the longest lower-priority request (R2-R3)
-        if (one_bucket && pt < pr && ((users >> t) & 1) && mt > blk) blk = mt;
+        higher |= (t < n && pt > pr) ? 1u << t : 0u;
+        ehigher |= (t < n && et > ep) ? 1u << t : 0u;
     }
+    // position in the analysis order: executor priority, then chain priority
+    const Mask eqx = __match_any_sync(gm, ep) >> sh; // equal executor priority
+    const int pos = __popc(ehigher) + __popc(eqx & higher & all);
     const Mask hp = samex & higher;                 // hp(c), Lemma 4
     const Mask hpp = corem & ~samex & ehigher;      // hpp(c), Theorem 1
     const Mask hps = users & higher;                // hps(c), Eq. 3
     const bool user = (users >> j) & 1;
-    if (!user) blk = 0;
     s.emax[j] = Emx;
-    uint32_t Bv = 0;
+    s.m[j] = Mv;
+    uint32_t Bv = 0, blk = 0;
     __syncwarp(gm);
     for (Mask lo = samex & ~higher & ~jbit & all; lo; lo &= lo - 1) // Lemma 4: one LP callback on the executor
         Bv = umax(Bv, s.emax[__ffs(lo) - 1]);
+    if (one_bucket && user) // every user shares the bucket: the longest lower-priority request (R2-R3)
+        for (Mask lo = users & ~higher & ~jbit; lo; lo &= lo - 1) blk = umax(blk, s.m[__ffs(lo) - 1]);
     if (!one_bucket) { // bucket = floor(rank * n_buckets / |U|), rank among the users (R2)
         const int32_t bk = user ? (int32_t)((uint32_t)__popc(hps) * (uint32_t)p.n_buckets / (uint32_t)__popc(users))
                                 : -1;
         s.bucket[j] = bk;
-        s.m[j] = Mv;
         __syncwarp(gm);
         if (user)
             for (Mask lo = users & ~higher & ~jbit; lo; lo &= lo - 1) {
