@@ -147,10 +147,19 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)item;
         return;
     }
-    if (__reduce_max_sync(gm, Dv) >= kNarrow - LG) { // inside it but not narrow
+    const uint32_t dmax = __reduce_max_sync(gm, Dv);
+    if (dmax >= kNarrow - LG) { // inside it but not narrow
         if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
         return;
     }
+    // The system's iteration bound: a recurrence of Eq. 3 or Eq. 6 rises strictly until
+    // it converges or passes its deadline, and after its first step only when some
+    // arrival count ceil(t / T_h) + 1 (Lemma 1) has grown, at most ceil(Dmax / T_h) times
+    // per chain h while t <= Dmax; so none takes more than L = sum_h ceil(Dmax / T_h) + 2
+    // evaluations.  With L within kIterCap (always, for a validated batch) the loops run
+    // without counters; otherwise every loop stops at kIterCap (PAAM_ST_ITERCAP).
+    const uint32_t L = __reduce_add_sync(gm, val ? rarrivals(dmax, tm2, mg, lg) - 1u : 0u) + 2u;
+    const bool counted = L > kIterCap;
 
     // ---- relations (Lemma 4, Theorem 1, Eq. 3), analysis order ---------------
     const unsigned xm = __match_any_sync(gm, ex); // lanes of the same executor (unique keys past n)
@@ -207,6 +216,8 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     uint32_t Ehp = Ev, Ehpp = Ev + (sp ? 0u : (uint32_t)((uint64_t)dlv * eps)), Rv = 0;
     Mask sched = 0, dep = 0;
     const uint32_t k2 = (uint32_t)kappa2;
+    auto chains = [&](auto counted_tag) {
+    constexpr bool CNT = decltype(counted_tag)::value;
     for (int step = 0; step < n; ++step) {
         const uint4 rl = s.rel[step], rc = s.rec[step], sg = s.seg[step];
         const int c = (int)sg.x;
@@ -244,7 +255,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
                             inf = true;
                             break;
                         }
-                        if (ev++ == kIterCap) {
+                        if (CNT && ev++ == kIterCap) {
                             inf = capped = true;
                             break;
                         }
@@ -271,7 +282,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             // every deadline is below 2^27 - 16: in the loop base <= R <= D, each group
             // sum is capped at 2^27 where it is added (a capped term already exceeds D)
             for (;;) {
-                if (ev++ == kIterCap) break;
+                if (CNT && ev++ == kIterCap) break;
                 const uint32_t cs = __reduce_add_sync(gm, capped_term(R, tm2, mg, lg, ccoef));
                 const uint32_t as = __reduce_add_sync(gm, capped_term(R, tm2, mg, lg, acoef));
                 hs = 0;
@@ -300,6 +311,11 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             if (rank_row) break;
         }
     }
+    };
+    if (counted)
+        chains(std::true_type{});
+    else
+        chains(std::false_type{});
 
     // ---- outputs -------------------------------------------------------------
     if (rank_row) {
