@@ -165,11 +165,21 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     uint32_t dmax = 0;
 #pragma unroll
     for (int k = 0; k < CPL; ++k) dmax = Dv[k] > dmax ? Dv[k] : dmax;
-    const bool narrow = rmax<G>(dmax, gm) < kNarrow - G * CPL;
+    const uint32_t dsys = rmax<G>(dmax, gm);
+    const bool narrow = dsys < kNarrow - G * CPL;
     if (!fits) {
         if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)item;
         return;
     }
+    // The system's iteration bound (see the header of paam_rta_load_systems): no
+    // recurrence of Eq. 3 or Eq. 6 takes more than L = sum_h ceil(Dmax / T_h) + 2
+    // evaluations.  With L within kIterCap (always, for a validated batch) the loops
+    // run without counters; otherwise every loop stops at kIterCap (PAAM_ST_ITERCAP).
+    uint32_t lpart = 0;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k)
+        if (val[k]) lpart += rarrivals(dsys, tm2[k], mg[k], lg[k]) - 1u;
+    const bool counted = __reduce_add_sync(gm, umin(lpart, kIterCap + 1u)) + 2u > kIterCap;
     if (!xprio) { // criticality-as-priority: highest chain priority on the executor
         int32_t best[CPL];
 #pragma unroll
@@ -284,6 +294,17 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     need_exact = ror<G>(need_exact, gm);
     __syncwarp(gm);
 
+    uint32_t Ehp[CPL], Ehpp[CPL], Rv[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        Ehp[k] = Ev[k];
+        Ehpp[k] = Ev[k] + (sp[k] ? 0u : (uint32_t)((uint64_t)dlv[k] * eps));
+        Rv[k] = 0;
+    }
+    Mask sched = 0, dep = 0;
+    // the fixed points: counted loops only where the bound above exceeds kIterCap
+    auto fixed_points = [&](auto counted_tag) {
+    constexpr bool CNT = decltype(counted_tag)::value;
     if constexpr (SAFE) {
         // ---- every segment's Lemma 2 bound, callback by callback: the chain's sum
         // (Eq. 3) and its longest hold; then B_c from the holds (safe Lemma 4)
@@ -310,7 +331,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                             inf = true;
                             break;
                         }
-                        if (ev++ == kIterCap) {
+                        if (CNT && ev++ == kIterCap) {
                             inf = capped = true;
                             break;
                         }
@@ -374,7 +395,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                         inf = true;
                         break;
                     }
-                    if (ev++ == kIterCap) {
+                    if (CNT && ev++ == kIterCap) {
                         inf = true;
                         break;
                     }
@@ -399,7 +420,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                         inf = true;
                         break;
                     }
-                    if (ev++ == kIterCap) {
+                    if (CNT && ev++ == kIterCap) {
                         inf = true;
                         break;
                     }
@@ -414,19 +435,11 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                 Hsum += h;
             }
         }
-        if (lane == 0 && (!inf || ev > kIterCap)) s.seg[c].x = ev > kIterCap ? kCapR : (uint32_t)Hsum;
+        if (lane == 0 && (!inf || (CNT && ev > kIterCap))) s.seg[c].x = CNT && ev > kIterCap ? kCapR : (uint32_t)Hsum;
         __syncwarp(gm);
     }
 
     // ---- Theorem 1 (Eq. 6), chain by chain ----------------------------------
-    uint32_t Ehp[CPL], Ehpp[CPL], Rv[CPL];
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) {
-        Ehp[k] = Ev[k];
-        Ehpp[k] = Ev[k] + (sp[k] ? 0u : (uint32_t)((uint64_t)dlv[k] * eps));
-        Rv[k] = 0;
-    }
-    Mask sched = 0, dep = 0;
     for (int step = 0; step < n; ++step) {
         const int c = s.order[step];
         const Mask hp = s.hp[c], hpp = s.hpp[c], hps = s.hps[c];
@@ -466,7 +479,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             uint32_t R32 = (uint32_t)R, hs32 = 0;
             if (R <= Dc) {
                 for (;;) {
-                    if (ev++ == kIterCap) break;
+                    if (CNT && ev++ == kIterCap) break;
                     uint64_t cpu = 0, acc = 0;
 #pragma unroll
                     for (int k = 0; k < CPL; ++k) {
@@ -494,7 +507,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             hs = hs32;
         } else {
             while (R <= Dc) {
-                if (ev++ == kIterCap) break;
+                if (CNT && ev++ == kIterCap) break;
                 uint64_t cpu = 0, acc = 0;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
@@ -527,7 +540,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                     if (sp[k]) Ehpp[k] = Ev[k] + (uint32_t)hs;
                 }
         } else {
-            if (ev > kIterCap) // the recurrence was cut short (PAAM_ST_ITERCAP)
+            if (CNT && ev > kIterCap) // the recurrence was cut short (PAAM_ST_ITERCAP)
 #pragma unroll
                 for (int k = 0; k < CPL; ++k)
                     if (lane + G * k == c) Rv[k] = kCapR;
@@ -535,6 +548,11 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         }
         if (TARGET && c == tgt) break; // chains after the target cannot change its result
     }
+    };
+    if (counted)
+        fixed_points(std::true_type{});
+    else
+        fixed_points(std::false_type{});
 
     // ---- outputs --------------------------------------------------------------
     if constexpr (TARGET) {

@@ -159,11 +159,18 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             return;
         }
     }
-    const bool narrow = rmax<G>(Dv, gm) < kNarrow - G;
+    const uint32_t dsys = rmax<G>(Dv, gm);
+    const bool narrow = dsys < kNarrow - G;
     if (!fits) {
         if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)item;
         return;
     }
+    // The system's iteration bound (see the header of paam_rta_load_systems): no
+    // recurrence of Eq. 3 or Eq. 6 takes more than L = sum_h ceil(Dmax / T_h) + 2
+    // evaluations.  With L within kIterCap (always, for a validated batch) the loops
+    // run without counters; otherwise every loop stops at kIterCap (PAAM_ST_ITERCAP).
+    const bool counted =
+        __reduce_add_sync(gm, val ? umin(rarrivals(dsys, tm2, mg, lg) - 1u, kIterCap + 1u) : 0u) + 2u > kIterCap;
     if (!xprio) { // criticality-as-priority: highest chain priority on the executor
         int32_t best = INT32_MIN;
         for (int t = 0; t < n; ++t) {
@@ -263,8 +270,13 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     for (int u = 0; u < NACC; ++u) need_exact[u] = ror<G>(need_exact[u], gm);
     __syncwarp(gm);
 
-    // ---- exact per-segment fixed points (Lemma 2), per accelerator ----------
     Mask capm = 0; // chains whose recurrence reached kIterCap evaluations
+    uint32_t Ehp = Ev, Ehpp = Ev + (sp ? 0u : (uint32_t)((uint64_t)dlt * eps)), Rv = 0;
+    Mask sched = 0, dep = 0;
+    // the fixed points: counted loops only where the bound above exceeds kIterCap
+    auto fixed_points = [&](auto counted_tag) {
+    constexpr bool CNT = decltype(counted_tag)::value;
+    // ---- exact per-segment fixed points (Lemma 2), per accelerator ----------
 #pragma unroll 1
     for (int u = 0; u < NACC; ++u) {
         for (Mask nm = need_exact[u]; nm; nm &= nm - 1) {
@@ -286,7 +298,7 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
                         inf = true;
                         break;
                     }
-                    if (ev++ == kIterCap) {
+                    if (CNT && ev++ == kIterCap) {
                         inf = true;
                         capm |= (Mask)1 << c;
                         break;
@@ -304,8 +316,6 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     }
 
     // ---- Theorem 1 (Eq. 6), chain by chain ----------------------------------
-    uint32_t Ehp = Ev, Ehpp = Ev + (sp ? 0u : (uint32_t)((uint64_t)dlt * eps)), Rv = 0;
-    Mask sched = 0, dep = 0;
     for (int step = 0; step < n; ++step) {
         const int c = s.order[step];
         const Mask hp = s.hp[c], hpp = s.hpp[c];
@@ -341,7 +351,7 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         bool ok = false;
         uint32_t ev = 0;
         while (R <= Dc) {
-            if (ev++ == kIterCap) {
+            if (CNT && ev++ == kIterCap) {
                 capm |= cbit;
                 break;
             }
@@ -373,6 +383,11 @@ __device__ void acc_system(const BatchDev &b, const AnalysisParams &p, int64_t i
             break;
         }
     }
+    };
+    if (counted)
+        fixed_points(std::true_type{});
+    else
+        fixed_points(std::false_type{});
 
     // ---- outputs --------------------------------------------------------------
     if (rank_row) {
