@@ -161,7 +161,9 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
                  20: "analyze_lazy_kernel<4>", 21: "analyze_lazy_kernel<4> (work queue)",
                  22: "analyze_lazy_kernel<4> (work queue, size-binned)",
                  23: "analyze_lazy_kernel<5> (work queue, size-binned)",
-                 24: "analyze_lazy_kernel<6> (work queue, size-binned)", 25: "analyze_lazy_kernel<5> (work queue)"}
+                 24: "analyze_lazy_kernel<6> (work queue, size-binned)", 25: "analyze_lazy_kernel<5> (work queue)",
+                 26: "analyze_lazy_kernel<16, 6> + analyze_lazy_kernel<32, 6> (work queue, size-binned)",
+                 27: "analyze_lazy_kernel<16, 4> + analyze_lazy_kernel<32, 6> (work queue, size-binned)"}
 
 
 # DRAM read + write per system of the analysis kernel, from ncu captures

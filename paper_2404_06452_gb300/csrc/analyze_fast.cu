@@ -562,6 +562,8 @@ const LaunchCfg kLaunchCfgs[] = {
     {2, 16, 16, 1, 32, 256, 0, 0}, {2, 16, 16, 1, 32, 256, 2, 0}, {2, 16, 16, 1, 32, 256, 2, 1},
     // the same with 5 and 6 resident blocks per SM (fewer registers per thread)
     {3, 16, 16, 1, 32, 256, 2, 1}, {4, 16, 16, 1, 32, 256, 2, 1}, {3, 16, 16, 1, 32, 256, 2, 0},
+    // the same first passes with the 32-lane lazy kernel over the deferral list
+    {4, 16, 16, kImplBigLazy32, 32, 256, 2, 1}, {2, 16, 16, kImplBigLazy32, 32, 256, 2, 1},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
 static_assert(kDefaultLaunchCfg < (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0])), "default configuration");
@@ -570,7 +572,7 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
                           uint8_t *status, uint8_t *verdict, cudaStream_t stream, int *n_kernels)
 {
     LaunchFn small = find_variant(cfg.impl_small, cfg.g_small, cfg.maxn_small);
-    LaunchFn bigfn = find_variant(cfg.impl_big, cfg.g_big, 64);
+    LaunchFn bigfn = cfg.impl_big == kImplBigLazy32 ? launch_reg<32, 2> : find_variant(cfg.impl_big, cfg.g_big, 64);
     if (!small || !bigfn) return PAAM_E_INVAL;
     int k = 0;
     const int64_t items = p.K > 0 ? b->n_sys * (int64_t)p.K : b->n_sys;
@@ -617,7 +619,21 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     ++k;
     // the lazy kernel also defers systems inside the 32-bit bound that are not narrow
     const bool lazy_defers = cfg.impl_small >= 2 && b->stats[ST_DMAX] >= kLazyNarrowD;
-    if (b->max_chains > cfg.maxn_small || lazy_defers) {
+    if ((b->max_chains > cfg.maxn_small || lazy_defers) && cfg.impl_big == kImplBigLazy32) {
+        // 17..32 chains in the 32-lane lazy kernel, then the rest of the list (over 32
+        // chains) in the 64-chain register tables, with static shares
+        rc = launch_lazy32<6>(b, pb, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
+        if (rc != PAAM_OK) return rc;
+        ++k;
+        if (b->max_chains > 32) {
+            AnalysisParams ph = pb;
+            ph.queue_batch = 0;
+            ph.min_chains = 33;
+            rc = launch_reg<32, 2>(b, ph, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
+            if (rc != PAAM_OK) return rc;
+            ++k;
+        }
+    } else if (b->max_chains > cfg.maxn_small || lazy_defers) {
         rc = bigfn(b, pb, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
         if (rc != PAAM_OK) return rc;
         ++k;

@@ -29,9 +29,13 @@
 namespace {
 using namespace paam_reg;
 
-constexpr int LG = 16; // lanes per system = largest chain count
+// LG lanes per system = its largest chain count: 16 (the first pass over every
+// system) or 32 (a pass over the first pass's deferral list, for systems of 17
+// to 32 chains; larger ones are left on the list for the 64-chain kernel, and
+// systems that are not narrow go to the int64 kernel)
 
 // per chain, stored at the chain's position in the analysis order
+template <int LG>
 struct LazySmem {
     uint4 rel[LG];    // {hp, hpp, hps, first segment relative to the system's first}
     uint4 rec[LG];    // {D, base = B + E, own = S* + delta blk (capped at D + 1), deps = delta eps}
@@ -48,7 +52,8 @@ __device__ __forceinline__ uint32_t capped_term(uint32_t t, uint32_t tm2, uint32
     return v < kNarrow - 1 ? (uint32_t)v : kNarrow - 1;
 }
 
-__device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t item, LazySmem &s, int lane,
+template <int LG>
+__device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t item, LazySmem<LG> &s, int lane,
                             unsigned gm, int64_t *__restrict__ R_out, uint8_t *__restrict__ st_out,
                             uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
                             int32_t *wide_list, int32_t *wide_count)
@@ -63,8 +68,8 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     }
     const int64_t c0 = b.sys_chain_off[sys];
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
-    if (n > LG) {
-        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
+    if (n > LG) { // the 64-chain kernel's; the first pass appends it to its list
+        if (LG == 16 && lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
         return;
     }
     const int16_t *rank_row = p.K > 0 ? p.ranks + (sys * p.Kc + cand_of(p, sys, cand)) * p.nmax : nullptr;
@@ -128,7 +133,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         dlv = (uint32_t)dl;
         seg0 = (uint32_t)(q0 - seg_base);
     }
-    const unsigned sh = threadIdx.x & 16u; // the group's first lane in the warp
+    const unsigned sh = LG == 32 ? 0u : (threadIdx.x & 16u); // the group's first lane in the warp
     const Mask users = __ballot_sync(gm, val && dlv != 0) >> sh;
     const Mask spins = __ballot_sync(gm, sp) >> sh;
     const Mask all = (n >= 32) ? ~0u : ((1u << n) - 1u);
@@ -148,8 +153,11 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         return;
     }
     const uint32_t dmax = __reduce_max_sync(gm, Dv);
-    if (dmax >= kNarrow - LG) { // inside it but not narrow
-        if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
+    if (dmax >= kNarrow - LG) { // inside it but not narrow: the 64-chain kernel (first pass) or the int64 kernel
+        if (lane == 0) {
+            if (LG == 16) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
+            else wide_list[atomicAdd(wide_count, 1)] = (int32_t)item;
+        }
         return;
     }
     // The system's iteration bound: a recurrence of Eq. 3 or Eq. 6 rises strictly until
@@ -158,7 +166,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     // per chain h while t <= Dmax; so none takes more than L = sum_h ceil(Dmax / T_h) + 2
     // evaluations.  With L within kIterCap (always, for a validated batch) the loops run
     // without counters; otherwise every loop stops at kIterCap (PAAM_ST_ITERCAP).
-    const uint32_t L = __reduce_add_sync(gm, val ? rarrivals(dmax, tm2, mg, lg) - 1u : 0u) + 2u;
+    const uint32_t L = __reduce_add_sync(gm, val ? umin(rarrivals(dmax, tm2, mg, lg) - 1u, kIterCap + 1u) : 0u) + 2u;
     const bool counted = L > kIterCap;
 
     // ---- relations (Lemma 4, Theorem 1, Eq. 3), analysis order ---------------
@@ -337,10 +345,12 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     __syncwarp(gm);
 }
 
-// BLOCKS resident blocks of 256 threads per SM: the register budget per thread
-template <int BLOCKS>
+// BLOCKS resident blocks of 256 threads per SM: the register budget per thread.
+// Items are all of the launch (list == nullptr) or list[0 .. *count).
+template <int LG, int BLOCKS>
 __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, AnalysisParams p, int64_t *R,
-                                                                   uint8_t *st, uint8_t *verdict, int32_t *big_list,
+                                                                   uint8_t *st, uint8_t *verdict, const int32_t *list,
+                                                                   const int32_t *count, int32_t *big_list,
                                                                    int32_t *big_count, int32_t *wide_list,
                                                                    int32_t *wide_count)
 {
@@ -348,25 +358,25 @@ __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, A
     const int groups = blockDim.x / LG;
     const int grp = threadIdx.x / LG;
     const int lane = threadIdx.x % LG;
-    LazySmem &s = reinterpret_cast<LazySmem *>(smem_raw)[grp];
+    LazySmem<LG> &s = reinterpret_cast<LazySmem<LG> *>(smem_raw)[grp];
     const unsigned gm = rgroup_mask<LG>();
-    const int64_t n_items = p.K > 0 ? b.n_sys * p.K : b.n_sys;
+    const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for_each_item<LG>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
-        lazy_system(b, p, i, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
+        const int64_t item = list ? (int64_t)list[i] : i;
+        lazy_system<LG>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
     });
 }
 
 } // namespace
 
-template <int BLOCKS>
-int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
-                const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream)
+template <int LG, int BLOCKS>
+int launch_lazy_pass(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                     const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream)
 {
-    if (list || count) return PAAM_E_INVAL; // first pass only: every item of the launch
     if (threads % 32 != 0 || threads > 256) return PAAM_E_INVAL;
     const int groups = threads / LG;
-    const size_t smem = sizeof(LazySmem) * groups;
-    auto kern = analyze_lazy_kernel<BLOCKS>;
+    const size_t smem = sizeof(LazySmem<LG>) * groups;
+    auto kern = analyze_lazy_kernel<LG, BLOCKS>;
     PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -375,10 +385,26 @@ int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8
     const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, bt->list_big, bt->counts,
-                                                      bt->list_wide, bt->counts + 1);
+    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, list, count, bt->list_big,
+                                                      bt->counts, bt->list_wide, bt->counts + 1);
     PAAM_CUDA_TRY(cudaGetLastError());
     return PAAM_OK;
+}
+
+template <int BLOCKS>
+int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream)
+{
+    if (list || count) return PAAM_E_INVAL; // first pass only: every item of the launch
+    return launch_lazy_pass<16, BLOCKS>(bt, p, R, st, verdict, nullptr, nullptr, max_items, threads, stream);
+}
+
+template <int BLOCKS>
+int launch_lazy32(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                  const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream)
+{
+    if (!list || !count) return PAAM_E_INVAL; // the pass over the deferral list
+    return launch_lazy_pass<32, BLOCKS>(bt, p, R, st, verdict, list, count, max_items, threads, stream);
 }
 
 template int launch_lazy<4>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
@@ -387,3 +413,7 @@ template int launch_lazy<5>(const paam_batch *, const AnalysisParams &, int64_t 
                             const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
 template int launch_lazy<6>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
                             const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_lazy32<4>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                              const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
+template int launch_lazy32<6>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
+                              const int32_t *, const int32_t *, int64_t, int, cudaStream_t);

@@ -69,6 +69,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     }
     const int64_t c0 = b.sys_chain_off[sys];
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
+    if (n < p.min_chains) return; // an earlier pass over the same list took it
     int tgt = -1;
     if constexpr (TARGET) {
         tgt = p.target[sys * p.Kc + cand_of(p, sys, cand)];

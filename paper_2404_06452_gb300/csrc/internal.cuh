@@ -61,6 +61,9 @@ struct AnalysisParams {
     // that chain is schedulable, the analysis stops once it is done, and
     // first_ok is not touched.
     const int16_t *target;
+    // Register-table kernels (analyze_reg.cu): skip systems with fewer chains (the
+    // 64-chain pass after the 32-lane lazy pass over the same deferral list)
+    int32_t min_chains;
 };
 
 // Item i of a launch: system index and candidate index (0 outside candidate mode).
@@ -237,6 +240,16 @@ template <int BLOCKS>
 int launch_lazy(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                 const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
 constexpr unsigned long long kLazyNarrowD = (1ull << 27) - 16;
+// The same kernel with 32 lanes per system over b->list_big (count b->counts[0]):
+// systems of up to 32 chains inside the narrow bound; larger ones stay on the
+// list for the 64-chain kernel (AnalysisParams::min_chains = 33), systems that
+// are not narrow go to b->list_wide.
+template <int BLOCKS>
+int launch_lazy32(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                  const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
+// impl_big value of a launch configuration whose deferral list goes to the 32-lane
+// lazy kernel and then, for systems over 32 chains, to the 64-chain register tables
+constexpr int kImplBigLazy32 = 9;
 
 // Register-table kernels (analyze_reg.cu): G lanes per system, CPL chains per lane.
 template <int G, int CPL>
