@@ -103,33 +103,40 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         if (xprio) ep = xprio[x0 + ex];
         sp = b.spin[g] != 0;
         const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
-        uint64_t E = 0, Emax = 0, S = 0, M = 0, Amin = ~0ull;
+        // sums and extremes in 32 bits over values capped at 2^30 (a capped value
+        // takes its chain's sum to the 32-bit bound, and the system to the int64 kernel)
+        const int64_t *Ep = b.E + cb0;
+        const int ncb = (int)(cb1 - cb0);
+        uint32_t E = 0, Emax = 0, S = 0, M = 0, Amin = 0xFFFFFFFFu;
 #pragma unroll 4
-        for (int64_t cb = cb0; cb < cb1; ++cb) {
-            const uint64_t e = (uint64_t)b.E[cb];
-            E += e;
-            Emax = e > Emax ? e : Emax;
+        for (int i = 0; i < ncb; ++i) {
+            const uint32_t e = (uint64_t)Ep[i] < kFitR ? (uint32_t)Ep[i] : (uint32_t)kFitR;
+            E = umin(E + e, (uint32_t)kFitR);
+            Emax = umax(Emax, e);
         }
         const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
+        const int64_t *Ap = b.A + q0;
+        const int nq = (int)(q1 - q0);
+        const uint32_t k2c = kappa2 < kFitR ? (uint32_t)kappa2 : (uint32_t)kFitR;
 #pragma unroll 4
-        for (int64_t q = q0; q < q1; ++q) {
-            const uint64_t a = (uint64_t)b.A[q] + kappa2; // A* = A + 2 kappa
-            S += a;
-            M = a > M ? a : M;
-            Amin = a < Amin ? a : Amin;
+        for (int i = 0; i < nq; ++i) {
+            const uint32_t a = ((uint64_t)Ap[i] < kFitR ? (uint32_t)Ap[i] : (uint32_t)kFitR) + k2c; // A* = A + 2 kappa
+            S = umin(S + a, (uint32_t)kFitR);
+            M = umax(M, a);
+            Amin = umin(Amin, a);
         }
-        const uint64_t dl = (uint64_t)(q1 - q0);
+        const uint64_t dl = (uint64_t)nq;
         fit = ((uint64_t)T < kFitR && (uint64_t)D < kFitR && E < kFitR && S < kFitR && dl < kFitR &&
                (eps == 0 || dl <= (kFitR - 1) / eps))
                   ? 1u
                   : 0u;
         if (fit) rdivisor((uint32_t)T, tm2, mg, lg);
         Dv = (uint32_t)D;
-        Ev = (uint32_t)E;
-        Sv = (uint32_t)S;
-        Emx = (uint32_t)Emax;
-        Mv = (uint32_t)M;
-        Amn = dl ? (uint32_t)(Amin < kFitR ? Amin : 0) : 0;
+        Ev = E;
+        Sv = S;
+        Emx = Emax;
+        Mv = M;
+        Amn = dl ? (Amin < kFitR ? Amin : 0u) : 0u;
         dlv = (uint32_t)dl;
         seg0 = (uint32_t)(q0 - seg_base);
     }
@@ -227,14 +234,15 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     auto chains = [&](auto counted_tag) {
     constexpr bool CNT = decltype(counted_tag)::value;
     for (int step = 0; step < n; ++step) {
-        const uint4 rl = s.rel[step], rc = s.rec[step], sg = s.seg[step];
-        const int c = (int)sg.x;
-        const Mask cbit = 1u << c;
+        const uint4 rl = s.rel[step];
         if ((rl.x | (rl.y & spins)) & ~sched) { // a needed H*_h is not available
-            dep |= cbit;
+            dep |= 1u << s.seg[step].x;
             if (rank_row) break; // a candidate fails at its first unschedulable chain
             continue;
         }
+        const uint4 rc = s.rec[step], sg = s.seg[step];
+        const int c = (int)sg.x;
+        const Mask cbit = 1u << c;
         const uint32_t D32 = rc.x, base = rc.y, own = rc.z, deps = rc.w;
         const uint32_t ccoef = ((rl.x >> j) & 1) ? Ehp : (((rl.y >> j) & 1) ? Ehpp : 0u);
         const uint32_t acoef = ((rl.z >> j) & 1) ? Sv : 0u;
