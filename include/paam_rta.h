@@ -515,6 +515,19 @@ int paam_tc_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int 
 int paam_diag_gelu(const float *z, float *gelu, float *grad, int64_t n, void *stream);
 
 /*
+ * The multiply-shift divisor the analysis kernels build for every period T
+ * (Lemma 1, Eq. 2: ceil(t / T) is taken as a multiply-high and a shift),
+ * exposed for testing: for i < n, l[i] = ceil(log2 T[i]) and m[i] =
+ * ceil(2^(31 + l[i]) / T[i]), with which floor(x / T) = floor(x m / 2^(31 + l))
+ * for every x < 2^31 (Granlund and Montgomery 1994, Theorem 4.2).  T, m and l
+ * are uint32 device arrays of n elements; each T[i] must lie in [1, 2^30)
+ * (outside it the outputs are unspecified, nothing is read or written beyond
+ * the arrays).  Enqueued on `stream`.  PAAM_E_INVAL for n < 0 or a NULL
+ * array with n > 0.  Not part of the paper.
+ */
+int paam_diag_divisor(const uint32_t *T, uint32_t *m, uint32_t *l, int64_t n, void *stream);
+
+/*
  * Diagnostics: number of CUDA kernels this library has launched in this
  * process (all contexts).  Not part of the paper; used to report how many
  * of the library's own kernels ran inside a timed region.

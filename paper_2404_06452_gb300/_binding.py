@@ -106,6 +106,7 @@ def lib():
             "paam_tc_gemm_bf16": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, _c_void_p, _c_void_p]),
             "paam_diag_gelu": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int64, _c_void_p]),
+            "paam_diag_divisor": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int64, _c_void_p]),
             "paam_measure_preemption": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _c_void_p,
                                                        _c_void_p]),
             "paam_rta_end_to_end": (ctypes.c_int, [_c_void_p, _c_void_p, ctypes.c_int64, _c_void_p, _c_void_p,
@@ -138,7 +139,7 @@ def exported_symbols() -> list:
             "paam_tc_gemm_bf16", "paam_rta_search_ordered", "paam_model_create", "paam_model_free",
             "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
             "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
-            "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_rta_end_to_end",
+            "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_diag_divisor", "paam_rta_end_to_end",
             "paam_measure_preemption", "paam_rta_audsley_order", "paam_rta_analyze_host",
             "paam_rta_autotune_search"]
 
@@ -387,6 +388,15 @@ def paam_diag_gelu(z, gelu=None, grad=None, stream=None):
     """The network's activation and its derivative at device fp32 ``z``."""
     _check(lib().paam_diag_gelu(_ptr(z), _ptr(gelu), _ptr(grad), int(z.numel()), _stream_ptr(stream)),
            "paam_diag_gelu")
+
+
+def paam_diag_divisor(T, m, l, stream=None):
+    """Multiply-shift divisor {m, l} of Lemma 1's arrival count for every
+    device uint32 period in ``T`` (written to device uint32 ``m`` and ``l``)."""
+    n = int(T.numel())
+    if m.numel() != n or l.numel() != n:
+        raise ValueError("paam_diag_divisor: T, m and l must have the same length")
+    _check(lib().paam_diag_divisor(_ptr(T), _ptr(m), _ptr(l), n, _stream_ptr(stream)), "paam_diag_divisor")
 
 
 def paam_rta_search_ordered(ctx: Context, batch: Batch, opts: AnalysisOpts, ranks, order, stop_at_first: bool,

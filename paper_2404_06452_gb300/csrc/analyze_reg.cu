@@ -732,3 +732,28 @@ int paam_launch_reg_safe(const paam_batch *bt, const AnalysisParams &p, int64_t 
     PAAM_CUDA_TRY(cudaGetLastError());
     return PAAM_OK;
 }
+
+namespace {
+__global__ void diag_divisor_kernel(const uint32_t *T, uint32_t *m, uint32_t *l, int64_t n)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint32_t tm2, mi, li;
+        rdivisor(T[i], tm2, mi, li);
+        m[i] = mi;
+        l[i] = li;
+    }
+}
+} // namespace
+
+extern "C" int paam_diag_divisor(const uint32_t *T, uint32_t *m, uint32_t *l, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && (!T || !m || !l))) return PAAM_E_INVAL;
+    if (n == 0) return PAAM_OK;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    diag_divisor_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(T, m, l, n);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    paam_count_launch();
+    return PAAM_OK;
+}

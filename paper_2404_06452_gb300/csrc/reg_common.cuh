@@ -121,10 +121,51 @@ __device__ __forceinline__ int rlowest(Mask m)
 // with N = 31).  Since 2x < 2^32 that is the high word of (2x) m shifted right
 // by l: one multiply-high and one 32-bit shift.  The divisor is kept as
 // {tm2 = 2 (T - 1), m, l}.
+//
+// m without a 64-bit division: for T = 2^l, m = 2^31.  Otherwise 3 <= T < 2^30,
+// tn = T 2^(32 - l) lies in (2^31, 2^32) and 2^(31 + l) / T = 2^63 / tn, which is
+// not an integer (T has an odd factor), so m = floor(2^63 / tn) + 1.  The
+// quotient q = floor(2^63 / tn) < 2^32 comes from a single-precision reciprocal
+// estimate r (relative error below 2^-21 with the conversion of tn): q0 = r 2^63
+// is within 2^10 of q, the remainder 2^63 - q0 tn then has magnitude below 2^42,
+// and q0 + trunc(r (2^63 - q0 tn)) is within 2 of q; two compare-and-step
+// corrections each way on the exact remainder make it exact (Newton's step on
+// the reciprocal followed by remainder correction, as in long division).
+__device__ __forceinline__ float rcp_estimate(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t rmagic(uint32_t T, uint32_t l)
+{
+    if ((T & (T - 1u)) == 0u) return 1u << 31;
+    const uint32_t tn = T << (32u - l);
+    const float r = rcp_estimate((float)tn);
+    int64_t q = (int64_t)__float2uint_rz(r * 0x1p63f);
+    int64_t rem = (int64_t)((1ull << 63) - (uint64_t)q * tn);
+    q += (int64_t)__float2int_rz((float)rem * r);
+    rem = (int64_t)((1ull << 63) - (uint64_t)q * tn);
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        if (rem < 0) {
+            --q;
+            rem += tn;
+        }
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+        if (rem >= (int64_t)tn) {
+            ++q;
+            rem -= tn;
+        }
+    return (uint32_t)q + 1u;
+}
+
 __device__ __forceinline__ void rdivisor(uint32_t T, uint32_t &tm2, uint32_t &m, uint32_t &l)
 {
     l = T > 1 ? 32u - (uint32_t)__clz(T - 1u) : 0u;
-    m = (uint32_t)(((1ull << (31 + l)) + T - 1u) / T);
+    m = rmagic(T, l);
     tm2 = 2u * (T - 1u);
 }
 
