@@ -10,6 +10,7 @@
 static std::atomic<uint64_t> g_launches{0};
 
 void paam_count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void paam_uncount_launch(unsigned n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 extern "C" uint64_t paam_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 

@@ -19,6 +19,8 @@ void paam_note_cuda_error(cudaError_t e, const char *expr, const char *file, int
 
 // Counts kernel launches made by this library (paam_launch_count()).
 void paam_count_launch(unsigned n = 1);
+// launches counted while a stream was being captured (they run when the graph is launched)
+void paam_uncount_launch(unsigned n);
 
 struct AnalysisParams {
     int32_t n_buckets;

@@ -23,7 +23,8 @@ struct paam_model {
     int64_t step;
     void *block;
     size_t block_bytes;
-    float *W[4], *bias[4], *mW[4], *vW[4], *mb[4], *vb[4], *gW[4], *gb[4];
+    float *W[4], *bias[4], *mW[4], *vW[4], *mb[4], *vb[4];
+    float *gW[4], *gb[4]; // gradients of the last paam_surrogate_grad call
     __nv_bfloat16 *Wb[4], *WbT[4];
 };
 
@@ -59,145 +60,227 @@ __global__ void labels_kernel(BatchDev b, const int64_t *R, const uint8_t *statu
     }
 }
 
-// ---- minibatch gather: rows idx[r] (-1 = padding) of X, L into Xb, Lb (16
-// bytes per thread and load); counts the valid labels into *count
-__global__ void gather_kernel(const __nv_bfloat16 *X, const float *L, const int64_t *idx, int rows,
-                              __nv_bfloat16 *Xb, float *Lb, float *count)
+// ---- minibatch gather: rows idx[r] (-1 = padding) of X into Xb and, transposed,
+// XbT ([1024][rows]), and of L into Lb; counts the valid labels into *count.
+// One block per 64 x 64 tile (grid: 16 column tiles x rows / 64 row tiles):
+// 16-byte loads and row-major stores, the transposed stores as 16-byte runs
+// of 8 rows, read column-wise from a shared-memory copy of the tile.
+constexpr int kTT = 64;
+constexpr int kTP = kTT + 8; // row pitch of a shared tile (u16): 16-byte aligned rows
+
+__device__ __forceinline__ void store_tile_t(const unsigned short (*t)[kTP], __nv_bfloat16 *out, int64_t ld,
+                                             int64_t c0, int64_t r0)
 {
-    const int r = blockIdx.x;
-    if (r >= rows) return;
-    const int64_t src = idx[r];
-    const uint4 *x4 = reinterpret_cast<const uint4 *>(X + (src >= 0 ? src : 0) * XW);
-    uint4 *o4 = reinterpret_cast<uint4 *>(Xb + (int64_t)r * XW);
-    for (int k = threadIdx.x; k < XW / 8; k += blockDim.x) o4[k] = src >= 0 ? x4[k] : make_uint4(0, 0, 0, 0);
+    // out[(c0 + c) * ld + r0 + 8 rc + i] = t[8 rc + i][c]: a warp writes 32 columns
+    for (int e = threadIdx.x; e < kTT * kTT / 8; e += blockDim.x) {
+        const int c = e % kTT, rc = e / kTT;
+        uint4 v;
+        unsigned short *h = reinterpret_cast<unsigned short *>(&v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) h[i] = t[8 * rc + i][c];
+        *reinterpret_cast<uint4 *>(out + (c0 + c) * ld + r0 + 8 * rc) = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) gather_kernel(const __nv_bfloat16 *X, const float *L, const int64_t *idx,
+                                                     int rows, __nv_bfloat16 *Xb, __nv_bfloat16 *XbT, float *Lb,
+                                                     float *count)
+{
+    __shared__ __align__(16) unsigned short t[kTT][kTP];
+    static_assert(kTT * kTT / 8 == 2 * 256, "two 16-byte loads per thread");
+    const int c0 = blockIdx.x * kTT, r0 = blockIdx.y * kTT;
+    uint4 v[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int e = threadIdx.x + 256 * j, r = e / (kTT / 8), part = e % (kTT / 8);
+        const int64_t src = idx[r0 + r];
+        v[j] = src >= 0 ? *reinterpret_cast<const uint4 *>(X + src * XW + c0 + 8 * part) : make_uint4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int e = threadIdx.x + 256 * j, r = e / (kTT / 8), part = e % (kTT / 8);
+        *reinterpret_cast<uint4 *>(Xb + (int64_t)(r0 + r) * XW + c0 + 8 * part) = v[j];
+        *reinterpret_cast<uint4 *>(&t[r][8 * part]) = v[j];
+    }
+    if (XbT) {
+        __syncthreads();
+        store_tile_t(t, XbT, rows, c0, r0);
+    }
+    if (blockIdx.x != 0) return;
+    // the tile's labels: 64 rows x 16 float4
+    static_assert(kTT * NCH / 4 == 4 * 256, "four label loads per thread");
+    float4 y[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int e = threadIdx.x + 256 * j, r = e / (NCH / 4), q = e % (NCH / 4);
+        const int64_t src = idx[r0 + r];
+        y[j] = src >= 0 ? *reinterpret_cast<const float4 *>(L + src * NCH + 4 * q) : make_float4(-1.f, -1.f, -1.f, -1.f);
+    }
     float cnt = 0.0f;
-    for (int c = threadIdx.x; c < NCH; c += blockDim.x) {
-        const float y = src >= 0 ? L[src * NCH + c] : -1.0f;
-        Lb[(int64_t)r * NCH + c] = y;
-        cnt += y >= 0.0f ? 1.0f : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int e = threadIdx.x + 256 * j, r = e / (NCH / 4), q = e % (NCH / 4);
+        *reinterpret_cast<float4 *>(Lb + (int64_t)(r0 + r) * NCH + 4 * q) = y[j];
+        cnt += (y[j].x >= 0.0f) + (y[j].y >= 0.0f) + (y[j].z >= 0.0f) + (y[j].w >= 0.0f);
     }
     for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
     if ((threadIdx.x & 31) == 0 && cnt > 0.0f) atomicAdd(count, cnt);
 }
 
-// ---- masked mean-squared error and its gradient
-__global__ void loss_kernel(const float *Y, const float *Lb, int rows, const float *count, __nv_bfloat16 *dY,
-                            float *loss_sum)
+// ---- masked mean-squared error and its gradient dY ([rows][64]) and dY^T
+// ([64][rows]); one block per 64 rows
+__global__ void __launch_bounds__(256) loss_kernel(const float *Y, const float *Lb, int rows, const float *count,
+                                                   __nv_bfloat16 *dY, __nv_bfloat16 *dYT, float *loss_sum)
 {
+    __shared__ __align__(16) unsigned short t[kTT][kTP];
+    __shared__ float part[8];
+    static_assert(kTT * NCH / 4 == 4 * 256, "four float4 per thread");
+    const int r0 = blockIdx.x * kTT;
+    float4 yv[4], lv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = (int64_t)r0 * NCH + 4 * (threadIdx.x + 256 * j);
+        yv[j] = *reinterpret_cast<const float4 *>(Y + i);
+        lv[j] = *reinterpret_cast<const float4 *>(Lb + i);
+    }
     const float inv = 1.0f / fmaxf(*count, 1.0f);
     float acc = 0.0f;
-    const int64_t n = (int64_t)rows * NCH;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float y = Lb[i];
-        const float d = y >= 0.0f ? Y[i] - y : 0.0f;
-        acc += d * d;
-        dY[i] = __float2bfloat16_rn(2.0f * d * inv);
-    }
-    // one atomic per block: warp sums, then the block's warps
-    __shared__ float part[32];
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float t = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
-        atomicAdd(loss_sum, t * inv);
-    }
-}
-
-// ---- bias gradients: row sums of a [rows][cols] bf16 matrix (one block per
-// row; cols a multiple of 8; eight values per 16-byte load, four loads in
-// flight per thread)
-__global__ void rowsum_kernel(const __nv_bfloat16 *A, int cols, float *out)
-{
-    __shared__ float part[8];
-    float acc = 0.0f;
-    const uint4 *a = reinterpret_cast<const uint4 *>(A + (int64_t)blockIdx.x * cols);
-    const int n8 = cols / 8;
-#pragma unroll 4
-    for (int k = threadIdx.x; k < n8; k += blockDim.x) {
-        const uint4 v = a[k];
-        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const float2 f = __bfloat1622float2(h[i]);
-            acc += f.x + f.y;
+    for (int j = 0; j < 4; ++j) {
+        const int e = threadIdx.x + 256 * j, r = e / (NCH / 4), c = 4 * (e % (NCH / 4));
+        const float yy[4] = {yv[j].x, yv[j].y, yv[j].z, yv[j].w}, ll[4] = {lv[j].x, lv[j].y, lv[j].z, lv[j].w};
+        unsigned short g[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float d = ll[q] >= 0.0f ? yy[q] - ll[q] : 0.0f;
+            acc += d * d;
+            g[q] = __bfloat16_as_ushort(__float2bfloat16_rn(2.0f * d * inv));
+            t[r][c + q] = g[q];
         }
+        uint2 w;
+        w.x = (unsigned)g[0] | ((unsigned)g[1] << 16);
+        w.y = (unsigned)g[2] | ((unsigned)g[3] << 16);
+        *reinterpret_cast<uint2 *>(dY + (int64_t)(r0 + r) * NCH + c) = w;
     }
+    __syncthreads();
+    store_tile_t(t, dYT, rows, 0, r0);
+    // one atomic per block: warp sums, then the block's warps
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        float s = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-        out[blockIdx.x] += s;
+        float tot = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
+        atomicAdd(loss_sum, tot * inv);
     }
 }
 
-// ---- out[c][r] = in[r][c] for a [rows][cols] bf16 matrix, through 32 x 32
-// shared-memory tiles (coalesced reads and writes); blocks of 32 x 8 threads
-__global__ void transpose_kernel(const __nv_bfloat16 *in, int rows, int cols, __nv_bfloat16 *out)
-{
-    __shared__ unsigned short t[32][33];
-    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-    const unsigned short *src = reinterpret_cast<const unsigned short *>(in);
-    unsigned short *dst = reinterpret_cast<unsigned short *>(out);
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int r = r0 + i, c = c0 + threadIdx.x;
-        if (r < rows && c < cols) t[i][threadIdx.x] = src[(int64_t)r * cols + c];
-    }
-    __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int c = c0 + i, r = r0 + threadIdx.x;
-        if (r < rows && c < cols) dst[(int64_t)c * rows + r] = t[threadIdx.x][i];
-    }
-}
-
-// ---- g[i] += sum over the split slices of part[z][i], in split order
-__global__ void splitk_reduce_kernel(const float *part, int64_t n, int z, float *g)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        float acc = 0.0f;
-        for (int k = 0; k < z; ++k) acc += part[(int64_t)k * n + i];
-        g[i] += acc;
-    }
-}
-
-// ---- AdamW (decoupled weight decay on weights only); refreshes the bf16 copies
-// All of a model's parameter blocks in one AdamW launch: block k covers
-// indices [off[k], off[k + 1]) of the concatenation.
-struct AdamSegs {
-    float *W[8], *m[8], *v[8], *g[8];
-    __nv_bfloat16 *Wb[8], *WbT[8];
-    int64_t off[9];
-    int rows[8], cols[8];
-    float wd[8];
-    int n;
+// ---- the gradients of one minibatch, and AdamW (decoupled weight decay on
+// weights only) with a refresh of the bf16 copies.
+// A weight gradient is the sum, in slice order, of the split-K slices its
+// GEMM stored (deterministic, no atomics); a bias gradient is the row sum of
+// the layer's transposed output gradient dT ([out][rows] bf16), taken by one
+// block per bias (16-byte loads, a fixed shuffle tree per warp, the warps'
+// sums in warp order).  Blocks [0, bias_blocks) take the biases, the others
+// four weights per thread.
+struct GradSegs {
+    float *W[4], *m[4], *v[4], *g[4];  // weights [out][in] (and moments, gradient out)
+    float *b[4], *mb[4], *vb[4], *gb[4];
+    __nv_bfloat16 *Wb[4], *WbT[4];
+    const float *part[4];              // [z][out * in] slices
+    const __nv_bfloat16 *dT[4];        // [out][rows]
+    int64_t woff[5];                   // weight index ranges in the concatenation (multiples of 4)
+    int boff[5];                       // bias index ranges
+    int z[4], rows_w[4], cols_w[4];
+    int rows;                          // minibatch rows (a multiple of 8)
+    int bias_blocks;
 };
 
-__global__ void adamw_all_kernel(AdamSegs a, float lr, float b1, float b2, float eps, float c1, float c2)
+__device__ __forceinline__ float adam_step(float &w, float &m, float &v, float g, float lr, float b1, float b2,
+                                           float eps, float c1, float c2, float wd)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.off[a.n]; t += stride) {
+    m = b1 * m + (1.0f - b1) * g;
+    v = b2 * v + (1.0f - b2) * g * g;
+    w -= lr * ((m / c1) / (sqrtf(v / c2) + eps) + wd * w);
+    return w;
+}
+
+// UPDATE: AdamW on every parameter; otherwise the gradients are stored into g / gb
+template <bool UPDATE>
+__global__ void __launch_bounds__(256) grad_adamw_kernel(GradSegs a, float lr, float b1, float b2, float eps,
+                                                         float c1, float c2, float wd)
+{
+    if ((int)blockIdx.x < a.bias_blocks) {
+        __shared__ float part[8];
+        const int j = blockIdx.x, lane = threadIdx.x & 31;
         int k = 0;
-        while (k + 1 < a.n && t >= a.off[k + 1]) ++k;
-        const int64_t i = t - a.off[k];
-        const float gi = a.g[k][i];
-        const float mi = b1 * a.m[k][i] + (1.0f - b1) * gi;
-        const float vi = b2 * a.v[k][i] + (1.0f - b2) * gi * gi;
-        a.m[k][i] = mi;
-        a.v[k][i] = vi;
-        float w = a.W[k][i];
-        w -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + a.wd[k] * w);
-        a.W[k][i] = w;
-        a.g[k][i] = 0.0f;
-        if (a.Wb[k]) {
-            const __nv_bfloat16 wb = __float2bfloat16_rn(w);
-            a.Wb[k][i] = wb;
-            if (a.WbT[k]) a.WbT[k][(i % a.cols[k]) * a.rows[k] + i / a.cols[k]] = wb;
+        while (k < 3 && j >= a.boff[k + 1]) ++k;
+        const int o = j - a.boff[k];
+        const uint4 *row = reinterpret_cast<const uint4 *>(a.dT[k] + (int64_t)o * a.rows);
+        float acc = 0.0f;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < a.rows / 8; q += blockDim.x) {
+            const uint4 v = row[q];
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 f = __bfloat1622float2(h[i]);
+                acc += f.x + f.y;
+            }
         }
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float g = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) g += part[w];
+            if (UPDATE)
+                adam_step(a.b[k][o], a.mb[k][o], a.vb[k][o], g, lr, b1, b2, eps, c1, c2, 0.0f);
+            else
+                a.gb[k][o] = g;
+        }
+        return;
+    }
+    const int64_t stride = (int64_t)(gridDim.x - a.bias_blocks) * blockDim.x * 4;
+    for (int64_t t = ((int64_t)(blockIdx.x - a.bias_blocks) * blockDim.x + threadIdx.x) * 4; t < a.woff[4];
+         t += stride) {
+        int k = 0;
+        while (k < 3 && t >= a.woff[k + 1]) ++k;
+        const int64_t i = t - a.woff[k], n = a.woff[k + 1] - a.woff[k];
+        const float *pp = a.part[k] + i;
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int z = a.z[k];
+#pragma unroll 8
+        for (int q = 0; q < z; ++q) {
+            const float4 p4 = *reinterpret_cast<const float4 *>(pp + (int64_t)q * n);
+            g.x += p4.x;
+            g.y += p4.y;
+            g.z += p4.z;
+            g.w += p4.w;
+        }
+        if (!UPDATE) {
+            *reinterpret_cast<float4 *>(a.g[k] + i) = g;
+            continue;
+        }
+        float4 w = *reinterpret_cast<const float4 *>(a.W[k] + i);
+        float4 mi = *reinterpret_cast<const float4 *>(a.m[k] + i);
+        float4 vi = *reinterpret_cast<const float4 *>(a.v[k] + i);
+        adam_step(w.x, mi.x, vi.x, g.x, lr, b1, b2, eps, c1, c2, wd);
+        adam_step(w.y, mi.y, vi.y, g.y, lr, b1, b2, eps, c1, c2, wd);
+        adam_step(w.z, mi.z, vi.z, g.z, lr, b1, b2, eps, c1, c2, wd);
+        adam_step(w.w, mi.w, vi.w, g.w, lr, b1, b2, eps, c1, c2, wd);
+        *reinterpret_cast<float4 *>(a.W[k] + i) = w;
+        *reinterpret_cast<float4 *>(a.m[k] + i) = mi;
+        *reinterpret_cast<float4 *>(a.v[k] + i) = vi;
+        const __nv_bfloat16 wb[4] = {__float2bfloat16_rn(w.x), __float2bfloat16_rn(w.y), __float2bfloat16_rn(w.z),
+                                     __float2bfloat16_rn(w.w)};
+        uint2 pk;
+        pk.x = (unsigned)__bfloat16_as_ushort(wb[0]) | ((unsigned)__bfloat16_as_ushort(wb[1]) << 16);
+        pk.y = (unsigned)__bfloat16_as_ushort(wb[2]) | ((unsigned)__bfloat16_as_ushort(wb[3]) << 16);
+        *reinterpret_cast<uint2 *>(a.Wb[k] + i) = pk;
+        const int cols = a.cols_w[k], rw = a.rows_w[k];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a.WbT[k][((i + q) % cols) * rw + (i + q) / cols] = wb[q];
     }
 }
 
@@ -413,7 +496,8 @@ struct Work {
     void *block;
     __nv_bfloat16 *Xb, *XbT, *Z[3], *H[3], *HT[3], *dY, *dYT, *dZ[3], *dZT[3];
     float *Lb, *Y, *count, *loss;
-    float *part; // split-K slices of a weight gradient (training)
+    float *part[4]; // per layer, the split-K slices of its weight gradient (training)
+    int z[4];       // slices per layer
     int32_t *err;
 };
 
@@ -440,16 +524,9 @@ DwPlan dw_plan(int out, int in, int rows, int n_sm)
     return d;
 }
 
-size_t dw_part_floats(int rows, int n_sm)
+size_t dw_part_floats(int l, int rows, int n_sm)
 {
-    size_t m = 0;
-    for (int l = 0; l < 4; ++l) {
-        const int out = l == 3 ? 64 : 256, in = l == 0 ? XW : 256;
-        const DwPlan d = dw_plan(out, in, rows, n_sm);
-        const size_t f = (size_t)d.z * out * in;
-        m = f > m ? f : m;
-    }
-    return m;
+    return (size_t)dw_plan(OUT[l], IN[l], rows, n_sm).z * OUT[l] * IN[l];
 }
 
 // xw: columns of the input buffer Xb (the full 1024 for training; inference
@@ -459,7 +536,9 @@ int work_alloc(Work &w, int rows, bool train, cudaStream_t s, int xw = XW, int n
     w = Work{};
     w.rows = rows;
     const size_t r = (size_t)rows;
-    const size_t part = train ? 4 * dw_part_floats(rows, n_sm > 0 ? n_sm : 1) : 0;
+    if (n_sm < 1) n_sm = 1;
+    size_t part = 0;
+    for (int l = 0; train && l < NL; ++l) part += 4 * dw_part_floats(l, rows, n_sm);
     size_t bytes = 2 * r * xw * (train ? 2 : 1) + 3 * 2 * r * 256 * (train ? 6 : 1) + 4 * r * 64 * (train ? 2 : 1) +
                    2 * 2 * r * 64 + 64 * 256 + part + 256;
     if (cudaMallocAsync(&w.block, bytes, s) != cudaSuccess) {
@@ -489,7 +568,10 @@ int work_alloc(Work &w, int rows, bool train, cudaStream_t s, int xw = XW, int n
         w.dY = (__nv_bfloat16 *)take(2 * r * 64);
         w.dYT = (__nv_bfloat16 *)take(2 * r * 64);
     }
-    if (train) w.part = (float *)take(part);
+    for (int l = 0; train && l < NL; ++l) {
+        w.part[l] = (float *)take(4 * dw_part_floats(l, rows, n_sm));
+        w.z[l] = dw_plan(OUT[l], IN[l], rows, n_sm).z;
+    }
     w.count = (float *)take(4);
     w.loss = (float *)take(4);
     w.err = (int32_t *)take(4);
@@ -583,14 +665,16 @@ int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool t
     return tc_gemm(g, w.err, s);
 }
 
-// gradients of the masked MSE into m->gW, m->gb (accumulated)
+// The masked MSE's gradients as the backward GEMMs leave them: per layer, the
+// split-K slices of the weight gradient in w.part[l] and the transposed output
+// gradient (dY^T, dZ^T) whose row sums are the bias gradient; grad_adamw
+// finishes them.
 int backward(paam_model *m, Work &w, cudaStream_t s)
 {
     const int rows = w.rows, sm = m->ctx->n_sm;
-    loss_kernel<<<grid_for((int64_t)rows * 64, 256, sm), 256, 0, s>>>(w.Y, w.Lb, rows, w.count, w.dY, w.loss);
-    transpose_kernel<<<dim3(NCH / 32, (rows + 31) / 32), dim3(32, 8), 0, s>>>(w.dY, rows, NCH, w.dYT);
+    loss_kernel<<<rows / kTT, 256, 0, s>>>(w.Y, w.Lb, rows, w.count, w.dY, w.dYT, w.loss);
     PAAM_CUDA_TRY(cudaGetLastError());
-    paam_count_launch(2);
+    paam_count_launch();
     // output layer: dW4 = dY^T H3, db4 = column sums of dY, dH3 = dY W4 (then the GELU derivative)
     const __nv_bfloat16 *dT = w.dYT; // [OUT[l]][rows]
     const __nv_bfloat16 *d = w.dY;   // [rows][OUT[l]]
@@ -601,18 +685,13 @@ int backward(paam_model *m, Work &w, cudaStream_t s)
         g.ep.mode = TC_EPI_STORE_F32;
         g.ep.M = OUT[l];
         g.ep.N = IN[l];
-        g.ep.C = w.part;
+        g.ep.C = w.part[l];
         g.ep.ldc = IN[l];
         g.ep.split_stride = (int64_t)OUT[l] * IN[l];
         g.splits = dp.splits;
         g.bn = dp.bn;
         int rc = tc_gemm(g, w.err, s);
         if (rc != PAAM_OK) return rc;
-        const int64_t nw = (int64_t)OUT[l] * IN[l];
-        splitk_reduce_kernel<<<grid_for(nw, 256, sm), 256, 0, s>>>(w.part, nw, dp.z, m->gW[l]);
-        rowsum_kernel<<<OUT[l], 256, 0, s>>>(dT, rows, m->gb[l]);
-        PAAM_CUDA_TRY(cudaGetLastError());
-        paam_count_launch(2);
         if (l == 0) break;
         TcGemm h = gemm(d, OUT[l], rows, m->WbT[l], OUT[l], IN[l], OUT[l]);
         h.ep.mode = TC_EPI_DGELU;
@@ -633,29 +712,127 @@ int backward(paam_model *m, Work &w, cudaStream_t s)
     return PAAM_OK;
 }
 
-int adamw(paam_model *m, const paam_train_opts *o, cudaStream_t s)
+// o != NULL: one AdamW step on the minibatch's gradients (bias corrections
+// c1 = 1 - beta1^t, c2 = 1 - beta2^t); o == NULL: the gradients into m->gW, m->gb
+int grad_adamw(paam_model *m, const Work &w, const paam_train_opts *o, float c1, float c2, cudaStream_t s)
 {
-    m->step += 1;
-    const float c1 = 1.0f - powf(o->beta1, (float)m->step), c2 = 1.0f - powf(o->beta2, (float)m->step);
-    AdamSegs a = {};
-    a.n = 2 * NL;
+    GradSegs a = {};
     int64_t off = 0;
+    int boff = 0;
     for (int l = 0; l < NL; ++l) {
-        const int w = 2 * l, b = 2 * l + 1; // the weights (decayed), then the biases (not decayed)
-        a.W[w] = m->W[l], a.m[w] = m->mW[l], a.v[w] = m->vW[l], a.g[w] = m->gW[l];
-        a.Wb[w] = m->Wb[l], a.WbT[w] = m->WbT[l], a.rows[w] = OUT[l], a.cols[w] = IN[l], a.wd[w] = o->weight_decay;
-        a.off[w] = off;
+        a.W[l] = m->W[l], a.m[l] = m->mW[l], a.v[l] = m->vW[l], a.g[l] = m->gW[l];
+        a.b[l] = m->bias[l], a.mb[l] = m->mb[l], a.vb[l] = m->vb[l], a.gb[l] = m->gb[l];
+        a.Wb[l] = m->Wb[l], a.WbT[l] = m->WbT[l];
+        a.part[l] = w.part[l];
+        a.z[l] = w.z[l];
+        a.dT[l] = l == 3 ? w.dYT : w.dZT[l];
+        a.rows_w[l] = OUT[l], a.cols_w[l] = IN[l];
+        a.woff[l] = off;
+        a.boff[l] = boff;
         off += (int64_t)IN[l] * OUT[l];
-        a.W[b] = m->bias[l], a.m[b] = m->mb[l], a.v[b] = m->vb[l], a.g[b] = m->gb[l];
-        a.Wb[b] = nullptr, a.WbT[b] = nullptr, a.rows[b] = 1, a.cols[b] = OUT[l], a.wd[b] = 0.0f;
-        a.off[b] = off;
-        off += OUT[l];
+        boff += OUT[l];
     }
-    a.off[2 * NL] = off;
-    adamw_all_kernel<<<grid_for(off, 256, m->ctx->n_sm), 256, 0, s>>>(a, o->lr, o->beta1, o->beta2, o->adam_eps, c1,
-                                                                      c2);
+    a.woff[NL] = off;
+    a.boff[NL] = boff;
+    a.rows = w.rows;
+    a.bias_blocks = boff; // one block per bias
+    const unsigned grid = (unsigned)a.bias_blocks + grid_for(off / 4, 256, m->ctx->n_sm);
+    if (o)
+        grad_adamw_kernel<true><<<grid, 256, 0, s>>>(a, o->lr, o->beta1, o->beta2, o->adam_eps, c1, c2,
+                                                     o->weight_decay);
+    else
+        grad_adamw_kernel<false><<<grid, 256, 0, s>>>(a, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f, 1.0f, 0.0f);
     PAAM_CUDA_TRY(cudaGetLastError());
     paam_count_launch();
+    return PAAM_OK;
+}
+
+// One training step: the minibatch gather (rows idx[0 .. rows)), forward,
+// backward and AdamW.
+int enqueue_step(paam_model *m, Work &w, const __nv_bfloat16 *X, const float *L, const int64_t *idx,
+                 const paam_train_opts *o, float c1, float c2, cudaStream_t s)
+{
+    const int rows = w.rows;
+    PAAM_CUDA_TRY(cudaMemsetAsync(w.count, 0, 4, s));
+    gather_kernel<<<dim3(XW / kTT, rows / kTT), 256, 0, s>>>(X, L, idx, rows, w.Xb, w.XbT, w.Lb, w.count);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    paam_count_launch();
+    int rc = forward(m, w, w.Xb, XW, true, s);
+    if (rc == PAAM_OK) rc = backward(m, w, s);
+    if (rc == PAAM_OK) rc = grad_adamw(m, w, o, c1, c2, s);
+    return rc;
+}
+
+// The training step as a CUDA graph: captured once, then launched per step
+// with two kernel arguments patched, the gather's index pointer and the
+// AdamW bias corrections (launches already enqueued keep their own values).
+struct StepGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t gather = nullptr, adam = nullptr;
+    cudaKernelNodeParams pg = {}, pa = {}; // as captured; the argument values live in the graph
+    unsigned kernels = 0;
+    ~StepGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+constexpr int kGatherArgs = 8, kAdamArgs = 8; // argument counts of gather_kernel, grad_adamw_kernel
+
+int capture_step(StepGraph &g, paam_model *m, Work &w, const __nv_bfloat16 *X, const float *L, const int64_t *idx,
+                 const paam_train_opts *o, float c1, float c2, cudaStream_t s)
+{
+    const uint64_t n0 = paam_launch_count();
+    PAAM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step(m, w, X, L, idx, o, c1, c2, s);
+    const cudaError_t ce = cudaStreamEndCapture(s, &g.graph);
+    g.kernels = (unsigned)(paam_launch_count() - n0);
+    paam_uncount_launch(g.kernels);
+    if (rc != PAAM_OK || ce != cudaSuccess || !g.graph) {
+        cudaGetLastError();
+        return rc != PAAM_OK ? rc : PAAM_E_CUDA;
+    }
+    size_t n = 0;
+    PAAM_CUDA_TRY(cudaGraphGetNodes(g.graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    PAAM_CUDA_TRY(cudaGraphGetNodes(g.graph, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        PAAM_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams p = {};
+        PAAM_CUDA_TRY(cudaGraphKernelNodeGetParams(nd, &p));
+        if (p.func == (void *)gather_kernel) {
+            g.gather = nd;
+            g.pg = p;
+        } else if (p.func == (void *)grad_adamw_kernel<true>) {
+            g.adam = nd;
+            g.pa = p;
+        }
+    }
+    if (!g.gather || !g.adam || !g.pg.kernelParams || !g.pa.kernelParams) return PAAM_E_CUDA;
+    PAAM_CUDA_TRY(cudaGraphInstantiate(&g.exec, g.graph, 0));
+    return PAAM_OK;
+}
+
+int patch_step(StepGraph &g, const int64_t *idx, float c1, float c2)
+{
+    void *ag[kGatherArgs], *aa[kAdamArgs];
+    for (int i = 0; i < kGatherArgs; ++i) ag[i] = g.pg.kernelParams[i];
+    for (int i = 0; i < kAdamArgs; ++i) aa[i] = g.pa.kernelParams[i];
+    ag[2] = (void *)&idx;
+    aa[5] = (void *)&c1;
+    aa[6] = (void *)&c2;
+    cudaKernelNodeParams p = g.pg;
+    p.kernelParams = ag;
+    p.extra = nullptr;
+    PAAM_CUDA_TRY(cudaGraphExecKernelNodeSetParams(g.exec, g.gather, &p));
+    p = g.pa;
+    p.kernelParams = aa;
+    p.extra = nullptr;
+    PAAM_CUDA_TRY(cudaGraphExecKernelNodeSetParams(g.exec, g.adam, &p));
     return PAAM_OK;
 }
 
@@ -710,6 +887,7 @@ extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const in
         if (cudaMemsetAsync(w.err, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
     }
     std::vector<int64_t> idx((size_t)(steps * rows));
+    StepGraph sg;
     uint64_t rng = o->seed ^ 0x5DEECE66DULL ^ (uint64_t)m->step;
     for (int e = 0; e < o->epochs && rc == PAAM_OK; ++e) {
         // minibatch order: a fresh permutation of the systems, padded with -1
@@ -724,14 +902,12 @@ extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const in
             cudaMemsetAsync(w.loss, 0, 4, s) != cudaSuccess)
             rc = PAAM_E_CUDA;
         for (int64_t st = 0; st < steps && rc == PAAM_OK; ++st) {
-            if (cudaMemsetAsync(w.count, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
-            gather_kernel<<<rows, 128, 0, s>>>(X, L, idx_dev + st * rows, rows, w.Xb, w.Lb, w.count);
-            transpose_kernel<<<dim3(XW / 32, rows / 32), dim3(32, 8), 0, s>>>(w.Xb, rows, XW, w.XbT);
-            if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-            paam_count_launch(2);
-            if (rc == PAAM_OK) rc = forward(m, w, w.Xb, XW, true, s);
-            if (rc == PAAM_OK) rc = backward(m, w, s);
-            if (rc == PAAM_OK) rc = adamw(m, o, s);
+            m->step += 1;
+            const float c1 = 1.0f - powf(o->beta1, (float)m->step), c2 = 1.0f - powf(o->beta2, (float)m->step);
+            const int64_t *ix = idx_dev + st * rows;
+            rc = sg.exec ? patch_step(sg, ix, c1, c2) : capture_step(sg, m, w, X, L, ix, o, c1, c2, s);
+            if (rc == PAAM_OK && cudaGraphLaunch(sg.exec, s) != cudaSuccess) rc = PAAM_E_CUDA;
+            if (rc == PAAM_OK) paam_count_launch(sg.kernels);
         }
         float loss = 0.0f;
         if (rc == PAAM_OK && (cudaMemcpyAsync(&loss, w.loss, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -870,18 +1046,15 @@ extern "C" int paam_surrogate_grad(paam_ctx *ctx, paam_model *m, const void *X, 
         cudaMemsetAsync(w.err, 0, 4, s) != cudaSuccess || cudaMemsetAsync(w.count, 0, 4, s) != cudaSuccess ||
         cudaMemsetAsync(w.loss, 0, 4, s) != cudaSuccess)
         rc = PAAM_E_CUDA;
-    for (int l = 0; l < NL && rc == PAAM_OK; ++l)
-        if (cudaMemsetAsync(m->gW[l], 0, 4 * (size_t)IN[l] * OUT[l], s) != cudaSuccess ||
-            cudaMemsetAsync(m->gb[l], 0, 4 * (size_t)OUT[l], s) != cudaSuccess)
-            rc = PAAM_E_CUDA;
     if (rc == PAAM_OK) {
-        gather_kernel<<<rows, 128, 0, s>>>((const __nv_bfloat16 *)X, L, idx, rows, w.Xb, w.Lb, w.count);
-        transpose_kernel<<<dim3(XW / 32, rows / 32), dim3(32, 8), 0, s>>>(w.Xb, rows, XW, w.XbT);
+        gather_kernel<<<dim3(XW / kTT, rows / kTT), 256, 0, s>>>((const __nv_bfloat16 *)X, L, idx, rows, w.Xb,
+                                                                 w.XbT, w.Lb, w.count);
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-        paam_count_launch(2);
+        paam_count_launch();
     }
     if (rc == PAAM_OK) rc = forward(m, w, w.Xb, XW, true, s);
     if (rc == PAAM_OK) rc = backward(m, w, s);
+    if (rc == PAAM_OK) rc = grad_adamw(m, w, nullptr, 1.0f, 1.0f, s);
     size_t o = 0;
     for (int l = 0; l < NL && rc == PAAM_OK; ++l) {
         const size_t nw = (size_t)IN[l] * OUT[l];
@@ -895,10 +1068,6 @@ extern "C" int paam_surrogate_grad(paam_ctx *ctx, paam_model *m, const void *X, 
     int32_t herr = 0;
     cudaMemcpyAsync(&loss, w.loss, 4, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&herr, w.err, 4, cudaMemcpyDeviceToHost, s);
-    for (int l = 0; l < NL; ++l) { // leave no gradient behind for a later training step
-        cudaMemsetAsync(m->gW[l], 0, 4 * (size_t)IN[l] * OUT[l], s);
-        cudaMemsetAsync(m->gb[l], 0, 4 * (size_t)OUT[l], s);
-    }
     cudaFreeAsync(idx, s);
     cudaFreeAsync(w.block, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = PAAM_E_CUDA;
