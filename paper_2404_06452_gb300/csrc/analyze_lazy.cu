@@ -39,9 +39,11 @@ template <int LG>
 struct LazySmem {
     uint4 rel[LG];    // {hp, hpp, hps, first segment relative to the system's first}
     uint4 rec[LG];    // {D, base = B + E, own = S* + delta blk (capped at D + 1), deps = delta eps}
-    uint4 seg[LG];    // {chain index, Amin*, blk, delta}
+    uint4 seg[LG];    // {chain index, lb (Lemma 2's lower bound, below), blk, delta}
     uint32_t emax[LG]; // longest callback, for Lemma 4's blocking
     uint32_t m[LG];    // M*, for the same-bucket blocking with several buckets
+    uint32_t msort[LG]; // M* of the users (0 for the others) by chain-priority rank, one bucket
+    uint32_t ssort[LG]; // S* of the users (0 for the others, capped at 2^27 - 1) by chain-priority rank
     int32_t bucket[LG];
 };
 
@@ -198,13 +200,40 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     const Mask hps = users & higher;                // hps(c), Eq. 3
     const bool user = (users >> j) & 1;
     s.emax[j] = Emx;
-    s.m[j] = Mv;
+    if (!one_bucket) s.m[j] = Mv;
+    const int prank = __popc(higher); // rank by chain priority, 0 = highest
+    if (val) {
+        s.ssort[prank] = user ? umin(Sv, kNarrow - 1) : 0u;
+        if (one_bucket) s.msort[prank] = user ? Mv : 0u;
+    }
     uint32_t Bv = 0, blk = 0;
     __syncwarp(gm);
+    // sum_h S*_h over hps(c), the users of higher priority: a prefix sum in priority
+    // order, saturating at 2^27 (a larger sum only ever meets bounds below it)
+    uint32_t sums = j < n ? s.ssort[j] : 0u;
+#pragma unroll
+    for (int d = 1; d < LG; d <<= 1) {
+        const uint32_t w = __shfl_up_sync(gm, sums, d, LG);
+        if (j >= d) sums = umin(sums + w, kNarrow);
+    }
+    sums = __shfl_up_sync(gm, sums, 1, LG);
+    if (j == 0) sums = 0u;
+    sums = __shfl_sync(gm, sums, prank < LG ? prank : 0, LG);
     for (Mask lo = samex & ~higher & ~jbit & all; lo; lo &= lo - 1) // Lemma 4: one LP callback on the executor
         Bv = umax(Bv, s.emax[__ffs(lo) - 1]);
-    if (one_bucket && user) // every user shares the bucket: the longest lower-priority request (R2-R3)
-        for (Mask lo = users & ~higher & ~jbit; lo; lo &= lo - 1) blk = umax(blk, s.m[__ffs(lo) - 1]);
+    if (one_bucket) { // every user shares the bucket: the longest lower-priority request (R2-R3)
+        // the largest M* over the users of rank > r: a suffix maximum in priority order
+        uint32_t v = j < n ? s.msort[j] : 0u;
+#pragma unroll
+        for (int d = 1; d < LG; d <<= 1) {
+            const uint32_t w = __shfl_down_sync(gm, v, d, LG);
+            if (j + d < LG) v = umax(v, w);
+        }
+        uint32_t below = __shfl_down_sync(gm, v, 1, LG);
+        if (j + 1 >= LG) below = 0u;
+        below = __shfl_sync(gm, below, prank < LG ? prank : 0, LG);
+        if (user) blk = below;
+    }
     if (!one_bucket) { // bucket = floor(rank * n_buckets / |U|), rank among the users (R2)
         const int32_t bk = user ? (int32_t)((uint32_t)__popc(hps) * (uint32_t)p.n_buckets / (uint32_t)__popc(users))
                                 : -1;
@@ -223,7 +252,11 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         const uint64_t cap = (uint64_t)Dv + 1; // values above D act the same as D + 1
         s.rel[pos] = make_uint4(hp, hpp, hps, seg0);
         s.rec[pos] = make_uint4(Dv, Bv + Ev, (uint32_t)(own < cap ? own : cap), (uint32_t)((uint64_t)dlv * eps));
-        s.seg[pos] = make_uint4((uint32_t)j, Amn, blk, dlv);
+        // Lemma 2's sum is at least own + lb, lb = f delta sum_h S*_h (every segment's fixed
+        // point is at least x + f sum_h S*_h with x = A* + blk, f = 2 if x >= 1, as mu >= 2
+        // for t >= 1), kept capped at 2^27 like the interference sums it is compared with
+        const uint64_t lb = (((uint64_t)Amn + blk) >= 1 ? 2 : 1) * (uint64_t)dlv * sums;
+        s.seg[pos] = make_uint4((uint32_t)j, lb < kNarrow ? (uint32_t)lb : kNarrow, blk, dlv);
     }
     __syncwarp(gm);
 
@@ -254,9 +287,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             // at most own + sum_h mu_h(D) S_h there, and every segment's fixed point is at
             // least x + f sum_h S_h with x = A* + blk, f = 2 if x >= 1 (mu >= 2 for t >= 1)
             const uint32_t hchd = umin(__reduce_add_sync(gm, capped_term(D32, tm2, mg, lg, acoef)), kNarrow);
-            const uint32_t sums = umin(__reduce_add_sync(gm, umin(acoef, kNarrow - 1)), kNarrow);
-            const uint64_t f = ((uint64_t)sg.y + sg.z) >= 1 ? 2 : 1;
-            if (f * dl * sums < hchd) {
+            if (sg.y < hchd) {
                 const uint32_t lim = umin(own + hchd, D32 + 1); // the sum matters only below this
                 const uint32_t blkc = sg.z;
                 const int64_t qb = seg_base + rl.w;
