@@ -45,6 +45,8 @@ struct LazySmem {
     uint32_t msort[LG]; // M* of the users (0 for the others) by chain-priority rank, one bucket
     uint32_t ssort[LG]; // S* of the users (0 for the others, capped at 2^27 - 1) by chain-priority rank
     int32_t bucket[LG];
+    int64_t c0, sys, seg_base; // kept here across the chain steps, not in registers
+    int32_t cand;
 };
 
 // ceil(t / T) + 1 (Lemma 1) times c, capped at 2^27 - 1 so that 16 lanes' sum fits 32 bits
@@ -141,6 +143,12 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         Amn = dl ? (Amin < kFitR ? Amin : 0u) : 0u;
         dlv = (uint32_t)dl;
         seg0 = (uint32_t)(q0 - seg_base);
+    }
+    if (lane == 0) {
+        s.c0 = c0;
+        s.sys = sys;
+        s.seg_base = seg_base;
+        s.cand = cand;
     }
     const unsigned sh = LG == 32 ? 0u : (threadIdx.x & 16u); // the group's first lane in the warp
     const Mask users = __ballot_sync(gm, val && dlv != 0) >> sh;
@@ -279,30 +287,63 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         const uint32_t D32 = rc.x, base = rc.y, own = rc.z, deps = rc.w;
         const uint32_t ccoef = ((rl.x >> j) & 1) ? Ehp : (((rl.y >> j) & 1) ? Ehpp : 0u);
         const uint32_t acoef = ((rl.z >> j) & 1) ? Sv : 0u;
-        uint32_t Hs = kInfR; // Lemma 2's per-segment sum; unbounded unless computed below
         const uint32_t dl = sg.w;
-        bool capped = false;
-        if (dl) {
-            // Lemma 2 matters only if its sum can fall below Eq. 4 at some R <= D: Eq. 4 is
-            // at most own + sum_h mu_h(D) S_h there, and every segment's fixed point is at
-            // least x + f sum_h S_h with x = A* + blk, f = 2 if x >= 1 (mu >= 2 for t >= 1)
-            const uint32_t hchd = umin(__reduce_add_sync(gm, capped_term(D32, tm2, mg, lg, acoef)), kNarrow);
-            if (sg.y < hchd) {
-                const uint32_t lim = umin(own + hchd, D32 + 1); // the sum matters only below this
-                const uint32_t blkc = sg.z;
-                const int64_t qb = seg_base + rl.w;
+        // start: B + E + H* with the interference part of Eq. 4 empty; Lemma 2's sum is
+        // never below own = S* + delta blk (each segment's fixed point is at least its
+        // A* + blk), so H* starts at own + delta eps either way
+        uint32_t R = base + (dl ? own + deps : 0u);
+        uint32_t hs = 0, ev = 0;
+        bool ok = false, capped = false;
+        if (R <= D32) {
+            // Lemma 2's sum is at least own + lb: while Eq. 4's interference part is at
+            // most lb, the minimum of Eq. 3 and Eq. 4 is Eq. 4; the exact per-segment fixed
+            // points are taken at the first evaluation where it is larger, if any
+            uint32_t lb = dl ? sg.y : kInfR; // kInfR once they are taken
+            uint32_t Hs = kInfR;             // Lemma 2's per-segment sum: unbounded, or not needed yet
+            // every deadline is below 2^27 - 16: in the loop base <= R <= D, each group
+            // sum is capped at 2^27 where it is added (a capped term already exceeds D)
+            for (;;) { // twice at most: before and after the fixed points are taken
+                bool need = false;
+                for (;;) {
+                    if (CNT && ev++ == kIterCap) break;
+                    const uint32_t cs = __reduce_add_sync(gm, capped_term(R, tm2, mg, lg, ccoef));
+                    const uint32_t as = umin(__reduce_add_sync(gm, capped_term(R, tm2, mg, lg, acoef)), kNarrow);
+                    hs = 0;
+                    if (dl) {
+                        if (as > lb) { // this evaluation is taken again once Lemma 2's sum is known
+                            need = true;
+                            if (CNT) --ev;
+                            break;
+                        }
+                        hs = umin(Hs, own + as) + deps; // Eq. 1 with min(Eq. 3, Eq. 4)
+                    }
+                    const uint32_t Rn = base + umin(hs, kNarrow) + umin(cs, kNarrow);
+                    if (Rn == R) {
+                        ok = true;
+                        break;
+                    }
+                    R = Rn;
+                    if (R > D32) break;
+                }
+                if (!need) break;
+                lb = kInfR;
+                // the sum matters only below Eq. 4 at R = D (and below D + 1)
+                const uint32_t hchd = umin(__reduce_add_sync(gm, capped_term(D32, tm2, mg, lg, acoef)), kNarrow);
+                const uint32_t lim = umin(own + hchd, D32 + 1);
+                const uint32_t blkc = s.seg[step].z;
+                const int64_t qb = s.seg_base + s.rel[step].w;
                 uint32_t H32 = 0;
                 bool inf = false;
                 for (uint32_t q = 0; q < dl && !inf; ++q) {
                     const uint32_t hb = (uint32_t)b.A[qb + q] + k2 + blkc;
                     uint32_t h = hb; // the recurrence starts with the first two terms
-                    uint32_t ev = 0;
+                    uint32_t evs = 0;
                     for (;;) {
                         if (h > D32 || H32 + h >= lim) {
                             inf = true;
                             break;
                         }
-                        if (CNT && ev++ == kIterCap) {
+                        if (CNT && evs++ == kIterCap) {
                             inf = capped = true;
                             break;
                         }
@@ -313,38 +354,14 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
                     }
                     H32 += h;
                 }
+                if (capped) break; // a segment recurrence was cut short
                 if (!inf) Hs = H32;
             }
         }
-        if (capped) { // a segment recurrence was cut short: no bound (PAAM_ST_ITERCAP)
+        if (capped) { // no bound (PAAM_ST_ITERCAP)
             if (j == c) Rv = kCapR;
             if (rank_row) break;
             continue;
-        }
-        // start: B + E + H* with the interference part of Eq. 4 empty
-        uint32_t R = base + (dl ? umin(Hs, own) + deps : 0u);
-        uint32_t hs = 0, ev = 0;
-        bool ok = false;
-        if (R <= D32) {
-            // every deadline is below 2^27 - 16: in the loop base <= R <= D, each group
-            // sum is capped at 2^27 where it is added (a capped term already exceeds D)
-            for (;;) {
-                if (CNT && ev++ == kIterCap) break;
-                const uint32_t cs = __reduce_add_sync(gm, capped_term(R, tm2, mg, lg, ccoef));
-                const uint32_t as = __reduce_add_sync(gm, capped_term(R, tm2, mg, lg, acoef));
-                hs = 0;
-                if (dl) {
-                    const uint32_t hch = own + umin(as, kNarrow); // Eq. 4
-                    hs = umin(Hs, hch) + deps;                    // Eq. 1 with min(Eq. 3, Eq. 4)
-                }
-                const uint32_t Rn = base + umin(hs, kNarrow) + umin(cs, kNarrow);
-                if (Rn == R) {
-                    ok = true;
-                    break;
-                }
-                R = Rn;
-                if (R > D32) break;
-            }
         }
         if (ok) {
             sched |= cbit;
@@ -365,6 +382,9 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         chains(std::false_type{});
 
     // ---- outputs -------------------------------------------------------------
+    {
+    const int64_t c0 = s.c0, sys = s.sys;
+    const int32_t cand = s.cand;
     if (rank_row) {
         if (lane == 0) {
             const bool ok = sched == all;
@@ -381,6 +401,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
                             : (Rv == kCapR ? PAAM_ST_ITERCAP : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
     }
     if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
+    }
     __syncwarp(gm);
 }
 
