@@ -422,6 +422,9 @@ __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, A
     const unsigned gm = rgroup_mask<LG>();
     const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for_each_item<LG>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
+        // first pass over a batch's systems, handed out in increasing order: the group
+        // that starts a window of the size binning prefetches the next window's tables
+        if (!list && p.K == 0 && lane == 0 && i % kBinWindow == 0) prefetch_window(b, p.sys_order, i + kBinWindow);
         const int64_t item = list ? (int64_t)list[i] : i;
         lazy_system<LG>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
     });

@@ -306,7 +306,6 @@ static size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 namespace {
 
 constexpr int kBins = PAAM_MAX_CHAINS + 1;
-constexpr int kBinWindow = 8192;
 
 __device__ __forceinline__ int size_bin(const int64_t *off, int64_t s)
 {

@@ -229,6 +229,10 @@ struct LaunchCfg {
     int binned; // 1: hand systems out by chain count within windows (batch->sys_order)
 };
 
+// Systems per window of the size binning (b->sys_order is sorted within each
+// window of this many consecutive systems).
+constexpr int kBinWindow = 8192;
+
 // Builds b->sys_order (api.cu): a counting sort of the systems by chain count
 // within each window of consecutive systems.
 int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, cudaStream_t stream);

@@ -115,6 +115,49 @@ __device__ __forceinline__ int rlowest(Mask m)
         return __ffs((int)m) - 1;
 }
 
+// Asks L2 to fetch elements [i0, i1) of an array of `elem`-byte elements, in
+// 1 MB bulk requests; the range is shrunk to whole 16-byte units inside it
+// (a bulk prefetch starts and ends on 16-byte boundaries), so nothing outside
+// the elements is named.
+__device__ __forceinline__ void prefetch_l2(const void *base, int elem, int64_t i0, int64_t i1)
+{
+    if (!base || i1 <= i0) return;
+    uintptr_t a = (uintptr_t)base + (uintptr_t)(i0 * elem), e = (uintptr_t)base + (uintptr_t)(i1 * elem);
+    a = (a + 15) & ~(uintptr_t)15;
+    e &= ~(uintptr_t)15;
+    while (a < e) {
+        const uint32_t sz = e - a < (1u << 20) ? (uint32_t)(e - a) : (1u << 20);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(sz) : "memory");
+        a += sz;
+    }
+}
+
+// The tables of systems [s0, s0 + kBinWindow) (callbacks, segments, chains,
+// executors), prefetched into L2 ahead of the groups that will read them.
+__device__ __forceinline__ void prefetch_window(const BatchDev &b, const int32_t *order, int64_t s0)
+{
+    if (s0 >= b.n_sys) return;
+    const int64_t s1 = s0 + kBinWindow < b.n_sys ? s0 + kBinWindow : b.n_sys;
+    const int64_t c0 = b.sys_chain_off[s0], c1 = b.sys_chain_off[s1];
+    const int64_t x0 = b.sys_exec_off[s0], x1 = b.sys_exec_off[s1];
+    const int64_t cb0 = b.chain_cb_off[c0], cb1 = b.chain_cb_off[c1];
+    const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
+    prefetch_l2(order, 4, s0, s1);
+    prefetch_l2(b.sys_chain_off, 8, s0, s1 + 1);
+    prefetch_l2(b.sys_exec_off, 8, s0, s1 + 1);
+    prefetch_l2(b.chain_cb_off, 8, c0, c1 + 1);
+    prefetch_l2(b.T, 8, c0, c1);
+    prefetch_l2(b.D, 8, c0, c1);
+    prefetch_l2(b.prio, 4, c0, c1);
+    prefetch_l2(b.exec, 4, c0, c1);
+    prefetch_l2(b.spin, 1, c0, c1);
+    prefetch_l2(b.exec_core, 4, x0, x1);
+    prefetch_l2(b.exec_prio, 4, x0, x1);
+    prefetch_l2(b.E, 8, cb0, cb1);
+    prefetch_l2(b.cb_seg_off, 8, cb0, cb1 + 1);
+    prefetch_l2(b.A, 8, q0, q1);
+}
+
 // Lemma 1 (Eq. 2): ceil(t / T) + 1 for t, T < 2^30.  With x = t + T - 1 < 2^31,
 // l = ceil(log2 T) and m = ceil(2^(31 + l) / T), floor(x / T) = floor(x m /
 // 2^(31 + l)) for every x < 2^31 (Granlund and Montgomery 1994, Theorem 4.2
