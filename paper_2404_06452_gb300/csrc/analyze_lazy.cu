@@ -44,6 +44,8 @@ struct LazySmem {
     uint32_t m[LG];    // M*, for the same-bucket blocking with several buckets
     uint32_t msort[LG]; // M* of the users (0 for the others) by chain-priority rank, one bucket
     uint32_t ssort[LG]; // S* of the users (0 for the others, capped at 2^27 - 1) by chain-priority rank
+    uint32_t inv[LG];   // by priority value (values below LG): the chain of that priority
+    uint32_t exm[LG];   // by executor priority value: the chains of that executor priority
     int32_t bucket[LG];
     int64_t c0, sys, seg_base; // kept here across the chain steps, not in registers
     int32_t cand;
@@ -192,16 +194,45 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     const Mask corem = __match_any_sync(gm, co) >> sh;
     if (!xprio) ep = __reduce_max_sync(xm, pr); // criticality-as-priority: highest chain priority on the executor
     const bool one_bucket = p.n_buckets == 1;
-    // higher chain priority and higher executor priority, one comparison each per chain
+    const Mask eqx = __match_any_sync(gm, ep) >> sh; // equal executor priority
+    // higher chain priority and higher executor priority
     Mask higher = 0, ehigher = 0;
+    if (__reduce_and_sync(gm, (!val || ((uint32_t)pr < (uint32_t)LG && (uint32_t)ep < (uint32_t)LG)) ? 1u : 0u)) {
+        // priorities below LG (a permutation of 0..n-1, and executor priorities taken
+        // from them): the chains of each priority value go to slot value, and the set
+        // above a value is the OR of the slots past it, a suffix scan over the group
+        s.inv[j] = 0u;
+        s.exm[j] = 0u;
+        __syncwarp(gm);
+        if (val) {
+            s.inv[pr] = jbit; // distinct priorities: one chain per slot
+            s.exm[ep] = eqx;  // every chain of this executor priority writes the same mask
+        }
+        __syncwarp(gm);
+        uint32_t a = s.inv[j], e = s.exm[j];
 #pragma unroll
-    for (int t = 0; t < LG; ++t) {
-        const int32_t pt = __shfl_sync(gm, pr, t, LG), et = __shfl_sync(gm, ep, t, LG);
-        higher |= (t < n && pt > pr) ? 1u << t : 0u;
-        ehigher |= (t < n && et > ep) ? 1u << t : 0u;
+        for (int d = 1; d < LG; d <<= 1) {
+            const uint32_t aw = __shfl_down_sync(gm, a, d, LG), ew = __shfl_down_sync(gm, e, d, LG);
+            if (j + d < LG) {
+                a |= aw;
+                e |= ew;
+            }
+        }
+        a = __shfl_down_sync(gm, a, 1, LG); // slots past this one
+        e = __shfl_down_sync(gm, e, 1, LG);
+        if (j + 1 >= LG) a = e = 0u;
+        higher = __shfl_sync(gm, a, val ? pr : 0, LG);
+        ehigher = __shfl_sync(gm, e, val ? ep : 0, LG);
+        if (!val) higher = ehigher = all;
+    } else { // one comparison each per chain
+#pragma unroll
+        for (int t = 0; t < LG; ++t) {
+            const int32_t pt = __shfl_sync(gm, pr, t, LG), et = __shfl_sync(gm, ep, t, LG);
+            higher |= (t < n && pt > pr) ? 1u << t : 0u;
+            ehigher |= (t < n && et > ep) ? 1u << t : 0u;
+        }
     }
     // position in the analysis order: executor priority, then chain priority
-    const Mask eqx = __match_any_sync(gm, ep) >> sh; // equal executor priority
     const int pos = __popc(ehigher) + __popc(eqx & higher & all);
     const Mask hp = samex & higher;                 // hp(c), Lemma 4
     const Mask hpp = corem & ~samex & ehigher;      // hpp(c), Theorem 1

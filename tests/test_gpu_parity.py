@@ -53,6 +53,26 @@ def test_cfg1_shape_with_spin_and_random_executor_priorities():
         assert_same(gpu_analyze(sy, **p), oracle.analyze(sy, threads=8, **p))
 
 
+def test_priorities_outside_zero_to_n():
+    """Chain and executor priorities spread far beyond 0..n-1 (some negative) in
+    every other system: only their order matters (Sec. II-A), so results equal
+    those of the original permutations, and the oracle's, on both relation paths
+    of the kernels (small priority values and general ones) within one launch."""
+    import dataclasses
+
+    sy = g.generate("cfg2", n_sys=20000, p_spin=0.3, exec_prio_mode=1, seed=41)
+    far = np.repeat(np.arange(sy.n_sys) % 2 == 1, sy.chains_per_system())
+    far_x = np.repeat(np.arange(sy.n_sys) % 2 == 1, np.diff(sy.sys_exec_off))
+    prio = np.where(far, sy.prio.astype(np.int64) * 1_000_003 - 700_000_000, sy.prio).astype(np.int32)
+    xprio = np.where(far_x, sy.exec_prio.astype(np.int64) * 999_983 - 5_000_000, sy.exec_prio).astype(np.int32)
+    sy2 = dataclasses.replace(sy, prio=prio, exec_prio=xprio)
+    for p in PARAMS[:2]:
+        a, b = gpu_analyze(sy, **p), gpu_analyze(sy2, **p)
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+        assert_same(b, oracle.analyze(sy2, threads=8, **p))
+
+
 def test_device_view_matches_host_view():
     sy = g.generate("cfg3", n_sys=20000)
     a = gpu_analyze(sy, n_buckets=2)
