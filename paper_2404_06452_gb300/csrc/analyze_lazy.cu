@@ -35,6 +35,8 @@ using namespace paam_reg;
 // systems that are not narrow go to the int64 kernel)
 
 // per chain, stored at the chain's position in the analysis order
+constexpr int kPrefetchSlice = 256; // systems per L2 prefetch (a divisor of kBinWindow)
+
 template <int LG>
 struct LazySmem {
     uint4 rel[LG];    // {hp, hpp, hps, first segment relative to the system's first}
@@ -453,9 +455,12 @@ __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, A
     const unsigned gm = rgroup_mask<LG>();
     const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for_each_item<LG>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
-        // first pass over a batch's systems, handed out in increasing order: the group
-        // that starts a window of the size binning prefetches the next window's tables
-        if (!list && p.K == 0 && lane == 0 && i % kBinWindow == 0) prefetch_window(b, p.sys_order, i + kBinWindow);
+        // first pass over a batch's systems, handed out in increasing order (within
+        // windows of the size binning): the group that starts each slice of
+        // kPrefetchSlice items prefetches the same slice of the next window's systems,
+        // so the prefetches of a window are spread over many SMs
+        if (!list && p.K == 0 && lane == 0 && i % kPrefetchSlice == 0)
+            prefetch_systems(b, p.sys_order, i + kBinWindow, kPrefetchSlice);
         const int64_t item = list ? (int64_t)list[i] : i;
         lazy_system<LG>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
     });

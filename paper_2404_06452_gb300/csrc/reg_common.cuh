@@ -132,12 +132,12 @@ __device__ __forceinline__ void prefetch_l2(const void *base, int elem, int64_t 
     }
 }
 
-// The tables of systems [s0, s0 + kBinWindow) (callbacks, segments, chains,
+// The tables of systems [s0, s0 + count) (callbacks, segments, chains,
 // executors), prefetched into L2 ahead of the groups that will read them.
-__device__ __forceinline__ void prefetch_window(const BatchDev &b, const int32_t *order, int64_t s0)
+__device__ __forceinline__ void prefetch_systems(const BatchDev &b, const int32_t *order, int64_t s0, int64_t count)
 {
     if (s0 >= b.n_sys) return;
-    const int64_t s1 = s0 + kBinWindow < b.n_sys ? s0 + kBinWindow : b.n_sys;
+    const int64_t s1 = s0 + count < b.n_sys ? s0 + count : b.n_sys;
     const int64_t c0 = b.sys_chain_off[s0], c1 = b.sys_chain_off[s1];
     const int64_t x0 = b.sys_exec_off[s0], x1 = b.sys_exec_off[s1];
     const int64_t cb0 = b.chain_cb_off[c0], cb1 = b.chain_cb_off[c1];
