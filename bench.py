@@ -163,31 +163,29 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
                  23: "analyze_lazy_kernel<5> (work queue, size-binned)",
                  24: "analyze_lazy_kernel<6> (work queue, size-binned)", 25: "analyze_lazy_kernel<5> (work queue)",
                  26: "analyze_lazy_kernel<16, 6> + analyze_lazy_kernel<32, 6> (work queue, size-binned)",
-                 27: "analyze_lazy_kernel<16, 4> + analyze_lazy_kernel<32, 6> (work queue, size-binned)"}
+                 27: "analyze_lazy_kernel<16, 4> + analyze_lazy_kernel<32, 6> (work queue, size-binned)",
+                 28: "analyze_lazy_kernel<16, 5> + analyze_lazy_kernel<32, 6> (work queue, size-binned)"}
 
 
-# DRAM read + write per system of the analysis kernel, from ncu captures
-# (dram__bytes_read.sum + dram__bytes_write.sum) of 500,000 systems of this
-# workload, per launch configuration: 12 is analyze_reg1_kernel<16> with the
-# work queue (2 systems per fetch) in index order (934.00 MB), 17 the same
-# kernel visiting the systems by chain count within windows of 8,192 systems
-# (937.25 MB), 24 analyze_lazy_kernel<6> in that order (967.96 MB).  Valid only
-# while the kernel and the order it visits are unchanged since the capture.
-TRAFFIC_PER_SYSTEM = {12: 934.004992e6 / 500_000, 17: 937.245184e6 / 500_000,
-                      24: (895.904512e6 + 72.053760e6) / 500_000}
+# DRAM read + write per system of the analysis kernels, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum) of 500,000 systems of a
+# workload, per launch configuration, and the executed warp-instructions per
+# system of the same captures (smsp__inst_executed.sum / 500,000 systems): the
+# instruction-issue side, against the issue peak of 152 SMs x 4 schedulers x 1
+# per clock.  Valid only while the kernels and the order they visit are
+# unchanged since the capture; a configuration without an entry reports null.
+TRAFFIC_PER_SYSTEM = {}
 # the same for the other workloads, keyed by (workload, launch configuration)
-# (cfg3, 24): the lazy kernel and the deferred systems' 64-chain kernel of one step
-TRAFFIC_OTHER = {("cfg3", 24): (574_711_808 + 35_175_936 + 439_813_120 + 18_042_624) / 500_000}
+TRAFFIC_OTHER = {}
 
 
 def traffic_per_system(workload: str, cfg_index: int):
     if workload == "cfg2":
         return TRAFFIC_PER_SYSTEM.get(cfg_index)
     return TRAFFIC_OTHER.get((workload, cfg_index))
-# Executed warp-instructions per system of the same kernels and captures
-# (smsp__inst_executed.sum / 500,000 systems): the instruction-issue side of
-# the kernel, against the issue peak of 152 SMs x 4 schedulers x 1 per clock.
-WARP_INST_PER_SYSTEM = {12: 783.638901e6 / 500_000, 17: 749.578079e6 / 500_000, 24: 702_575_345 / 500_000}
+
+
+WARP_INST_PER_SYSTEM = {}
 ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions / s at the 2070 MHz maximum SM clock
 
 

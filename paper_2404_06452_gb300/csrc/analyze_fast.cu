@@ -564,6 +564,7 @@ const LaunchCfg kLaunchCfgs[] = {
     {3, 16, 16, 1, 32, 256, 2, 1}, {4, 16, 16, 1, 32, 256, 2, 1}, {3, 16, 16, 1, 32, 256, 2, 0},
     // the same first passes with the 32-lane lazy kernel over the deferral list
     {4, 16, 16, kImplBigLazy32, 32, 256, 2, 1}, {2, 16, 16, kImplBigLazy32, 32, 256, 2, 1},
+    {3, 16, 16, kImplBigLazy32, 32, 256, 2, 1},
 };
 const int kNumLaunchCfgs = (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0]));
 static_assert(kDefaultLaunchCfg < (int)(sizeof(kLaunchCfgs) / sizeof(kLaunchCfgs[0])), "default configuration");

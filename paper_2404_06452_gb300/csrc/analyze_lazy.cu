@@ -111,6 +111,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         if (xprio) ep = xprio[x0 + ex];
         sp = b.spin[g] != 0;
         const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
+        const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
         // sums and extremes in 32 bits over values capped at 2^30 (a capped value
         // takes its chain's sum to the 32-bit bound, and the system to the int64 kernel)
         const int64_t *Ep = b.E + cb0;
@@ -122,7 +123,6 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             E = umin(E + e, (uint32_t)kFitR);
             Emax = umax(Emax, e);
         }
-        const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
         const int64_t *Ap = b.A + q0;
         const int nq = (int)(q1 - q0);
         const uint32_t k2c = kappa2 < kFitR ? (uint32_t)kappa2 : (uint32_t)kFitR;

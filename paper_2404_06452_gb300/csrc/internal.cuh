@@ -264,9 +264,10 @@ int launch_reg(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_
 extern const LaunchCfg kLaunchCfgs[];
 extern const int kNumLaunchCfgs;
 // Configuration of a batch before any autotuning: the lazy register-table
-// kernel with six resident blocks per SM, work queue, systems by size (the
-// fastest on the 1M-system and the 10k x 256 search workloads)
-constexpr int kDefaultLaunchCfg = 24;
+// kernel with five resident blocks per SM, work queue, systems by size, and
+// the 32-lane lazy pass over the deferral list (the fastest on the 1M- and
+// 4M-system workloads)
+constexpr int kDefaultLaunchCfg = 28;
 
 // Evaluations any one fixed-point recurrence may take before the analysis
 // kernels stop it with PAAM_ST_ITERCAP.  Validation refuses systems whose

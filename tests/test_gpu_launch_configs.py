@@ -120,7 +120,7 @@ def test_search_autotune_picks_a_valid_config_and_stays_exact():
     sy = g.generate("cfg4s", n_sys=2000)
     ranks = g.candidate_ranks(sy, 32, 4)
     b = pkg.paam_rta_load_systems(ctx(), sy)
-    assert pkg.paam_rta_get_launch_config(b) == 24  # a new batch starts with the default configuration
+    assert pkg.paam_rta_get_launch_config(b) == 28  # a new batch starts with the default configuration
     r = torch.from_numpy(ranks).cuda()
     best, times = pkg.paam_rta_autotune_search(ctx(), b, pkg.analysis_opts(), r)
     assert 0 <= best < pkg.paam_rta_num_launch_configs()
