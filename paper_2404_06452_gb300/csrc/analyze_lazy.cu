@@ -39,7 +39,7 @@ constexpr int kPrefetchSlice = 256; // systems per L2 prefetch (a divisor of kBi
 
 template <int LG>
 struct LazySmem {
-    uint4 rel[LG];    // {hp, hpp, hps, first segment relative to the system's first}
+    uint4 rel[LG];    // {hp, hpp, hps, needs = hp and the spinning hpp: all must be schedulable (DEP rule)}
     uint4 rec[LG];    // {D, base = B + E, own = S* + delta blk (capped at D + 1), deps = delta eps}
     uint4 seg[LG];    // {chain index, lb (Lemma 2's lower bound, below), blk, delta}
     uint32_t emax[LG]; // longest callback, for Lemma 4's blocking
@@ -48,6 +48,8 @@ struct LazySmem {
     uint32_t ssort[LG]; // S* of the users (0 for the others, capped at 2^27 - 1) by chain-priority rank
     uint32_t inv[LG];   // by priority value (values below LG): the chain of that priority
     uint32_t exm[LG];   // by executor priority value: the chains of that executor priority
+    uint32_t seg0[LG];  // by analysis position: first segment, relative to the system's first
+    uint32_t needs[LG]; // by chain: its DEP-rule set, read again for the status
     int32_t bucket[LG];
     int64_t c0, sys, seg_base; // kept here across the chain steps, not in registers
     int32_t cand;
@@ -291,7 +293,10 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     if (val) {
         const uint64_t own = (uint64_t)Sv + (uint64_t)dlv * blk;
         const uint64_t cap = (uint64_t)Dv + 1; // values above D act the same as D + 1
-        s.rel[pos] = make_uint4(hp, hpp, hps, seg0);
+        const Mask needs = hp | (hpp & spins);
+        s.rel[pos] = make_uint4(hp, hpp, hps, needs);
+        s.seg0[pos] = seg0;
+        s.needs[j] = needs;
         s.rec[pos] = make_uint4(Dv, Bv + Ev, (uint32_t)(own < cap ? own : cap), (uint32_t)((uint64_t)dlv * eps));
         // Lemma 2's sum is at least own + lb, lb = f delta sum_h S*_h (every segment's fixed
         // point is at least x + f sum_h S*_h with x = A* + blk, f = 2 if x >= 1, as mu >= 2
@@ -303,14 +308,13 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
 
     // ---- Theorem 1 (Eq. 6), chain by chain -----------------------------------
     uint32_t Ehp = Ev, Ehpp = Ev + (sp ? 0u : (uint32_t)((uint64_t)dlv * eps)), Rv = 0;
-    Mask sched = 0, dep = 0;
+    Mask sched = 0;
     const uint32_t k2 = (uint32_t)kappa2;
     auto chains = [&](auto counted_tag) {
     constexpr bool CNT = decltype(counted_tag)::value;
     for (int step = 0; step < n; ++step) {
         const uint4 rl = s.rel[step];
-        if ((rl.x | (rl.y & spins)) & ~sched) { // a needed H*_h is not available
-            dep |= 1u << s.seg[step].x;
+        if (rl.w & ~sched) { // a needed H*_h is not available (the chain is DEP)
             if (rank_row) break; // a candidate fails at its first unschedulable chain
             continue;
         }
@@ -364,7 +368,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
                 const uint32_t hchd = umin(__reduce_add_sync(gm, capped_term(D32, tm2, mg, lg, acoef)), kNarrow);
                 const uint32_t lim = umin(own + hchd, D32 + 1);
                 const uint32_t blkc = s.seg[step].z;
-                const int64_t qb = s.seg_base + s.rel[step].w;
+                const int64_t qb = s.seg_base + s.seg0[step];
                 uint32_t H32 = 0;
                 bool inf = false;
                 for (uint32_t q = 0; q < dl && !inf; ++q) {
@@ -430,8 +434,10 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     if (val) {
         const bool ok = (sched >> j) & 1;
         R_out[c0 + j] = ok ? (int64_t)Rv : -1;
+        // DEP: skipped at its step, i.e. some chain of its DEP-rule set (all earlier in
+        // the analysis order) is not schedulable
         st_out[c0 + j] = ok ? PAAM_ST_SCHED
-                            : (Rv == kCapR ? PAAM_ST_ITERCAP : (((dep >> j) & 1) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
+                            : (Rv == kCapR ? PAAM_ST_ITERCAP : ((s.needs[j] & ~sched) ? PAAM_ST_DEP : PAAM_ST_OVERRUN));
     }
     if (lane == 0 && verdict) verdict[sys] = sched == all ? 1 : 0;
     }
