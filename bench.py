@@ -174,9 +174,14 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
 # instruction-issue side, against the issue peak of 152 SMs x 4 schedulers x 1
 # per clock.  Valid only while the kernels and the order they visit are
 # unchanged since the capture; a configuration without an entry reports null.
-TRAFFIC_PER_SYSTEM = {}
-# the same for the other workloads, keyed by (workload, launch configuration)
-TRAFFIC_OTHER = {}
+# 26: analyze_lazy_kernel<16, 6> (1,023.8 MB), 28: analyze_lazy_kernel<16, 5> (959.2 MB);
+# neither defers a system of this workload.
+TRAFFIC_PER_SYSTEM = {26: (951_578_112 + 72_256_512) / 500_000, 28: (901_536_768 + 57_635_584) / 500_000}
+# the same for the other workloads, keyed by (workload, launch configuration): the
+# uneven workload's step is the first pass, the 32-lane pass over the deferral list
+# and the 64-chain register-table kernel for the systems above 32 chains
+TRAFFIC_OTHER = {("cfg3", 26): (868_313_600 + 40_677_888 + 346_370_304 + 16_324_864 + 108_700_672 + 897_792) / 500_000,
+                 ("cfg3", 28): (850_211_072 + 32_089_600 + 346_431_744 + 16_359_168 + 108_639_488 + 906_240) / 500_000}
 
 
 def traffic_per_system(workload: str, cfg_index: int):
@@ -185,7 +190,7 @@ def traffic_per_system(workload: str, cfg_index: int):
     return TRAFFIC_OTHER.get((workload, cfg_index))
 
 
-WARP_INST_PER_SYSTEM = {}
+WARP_INST_PER_SYSTEM = {26: 550_822_977 / 500_000, 28: 532_091_168 / 500_000}
 ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions / s at the 2070 MHz maximum SM clock
 
 
