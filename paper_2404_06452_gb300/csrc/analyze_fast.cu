@@ -639,7 +639,9 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
         if (rc != PAAM_OK) return rc;
         ++k;
     }
-    if (!batch_fits_32(b, p)) {
+    // the int64 kernel for the systems outside the 32-bit bound, and (the 32-lane lazy
+    // pass sends them there) for the deferred systems inside it that are not narrow
+    if (!batch_fits_32(b, p) || (lazy_defers && cfg.impl_big == kImplBigLazy32)) {
         rc = paam_launch_wide(b, pw, R, status, verdict, b->list_wide, b->counts + 1, items, stream);
         if (rc != PAAM_OK) return rc;
         ++k;

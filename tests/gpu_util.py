@@ -26,11 +26,26 @@ def gpu_analyze(sy, n_buckets=1, eps=0, kappa=0, device_view=False, autotune=Fal
     b = pkg.paam_rta_load_systems(c, src)
     if autotune:
         pkg.paam_rta_autotune(c, b, pkg.analysis_opts(n_buckets, eps, kappa))
-    R, st, v = pkg.analyze(c, b, n_buckets=n_buckets, eps=eps, kappa=kappa, blocking_mode=blocking_mode)
-    torch.cuda.synchronize()
-    out = dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy())
+    out = analyze_poisoned(c, b, n_buckets=n_buckets, eps=eps, kappa=kappa, blocking_mode=blocking_mode)
     b.free()
     return out
+
+
+def analyze_poisoned(c, b, n_buckets=1, eps=0, kappa=0, blocking_mode=0):
+    """``paam_rta_analyze_batch`` into outputs filled beforehand with values no
+    analysis writes (R = -7, status and verdict 0xEE), so that a chain or system
+    the kernels leave untouched shows up as a difference (fresh allocations can
+    hold an earlier call's correct results)."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    R = torch.full((b.n_chain,), -7, dtype=torch.int64, device="cuda")
+    st = torch.full((b.n_chain,), 0xEE, dtype=torch.uint8, device="cuda")
+    v = torch.full((b.n_sys,), 0xEE, dtype=torch.uint8, device="cuda")
+    pkg.paam_rta_analyze_batch(c, b, pkg.analysis_opts(n_buckets, eps, kappa, blocking_mode), R, st, v)
+    torch.cuda.synchronize()
+    return dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy())
 
 
 def assert_same(gpu, ref, idx_chain=None, idx_sys=None):

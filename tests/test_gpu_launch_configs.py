@@ -9,7 +9,7 @@ import oracle
 import paam_gen as g
 from paam_gen import tiny
 
-from gpu_util import assert_same, ctx
+from gpu_util import analyze_poisoned, assert_same, ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -61,10 +61,37 @@ def test_every_launch_config_bit_exact():
     b = pkg.paam_rta_load_systems(ctx(), sy)
     for i in range(pkg.paam_rta_num_launch_configs()):
         pkg.paam_rta_set_launch_config(b, i)
-        R, st, v = pkg.analyze(ctx(), b, n_buckets=2, eps=1000, kappa=500)
-        torch.cuda.synchronize()
-        assert_same(dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy()), ref)
+        assert_same(analyze_poisoned(ctx(), b, n_buckets=2, eps=1000, kappa=500), ref)
     b.free()
+
+
+def test_every_launch_config_between_the_narrow_and_32_bit_bounds():
+    """Systems with deadlines between the narrow bound of the 32-bit kernels
+    (2^27) and the 32-bit bound (2^30) among ordinary ones: the batch takes the
+    32-bit path, but those systems are deferred by the narrow kernels; every
+    configuration must still analyse each of them (bit-exact)."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    a = g.generate("cfg3", n_sys=3000)
+    rng = random.Random(23)
+    mid = [tiny.tiny_system(rng, n_min=2, n_max=40, cb_max=5, x_max=6, periods=tuple(range(2**27, 2**29, 2**22)),
+                            e_max=2**22, a_max=2**21, p_seg=0.5, p_spin=0.5, seg_max=2) for _ in range(200)]
+    b = tiny.to_systems(mid)
+    out, k = [], 0
+    for i in range(b.n_sys):
+        out.append(a.subset(np.arange(k, k + 15)))
+        out.append(b.subset(np.array([i])))
+        k += 15
+    sy = _concat(out)
+    assert sy.T.max() < 2**30 and sy.D.max() >= 2**27
+    ref = oracle.analyze(sy, threads=8)
+    bt = pkg.paam_rta_load_systems(ctx(), sy)
+    for i in range(pkg.paam_rta_num_launch_configs()):
+        pkg.paam_rta_set_launch_config(bt, i)
+        assert_same(analyze_poisoned(ctx(), bt), ref)
+    bt.free()
 
 
 def test_graph_replay_with_changing_outputs_and_options():
@@ -148,7 +175,5 @@ def test_safe_blocking_every_launch_config():
         b = pkg.paam_rta_load_systems(ctx(), sy)
         for i in range(pkg.paam_rta_num_launch_configs()):
             pkg.paam_rta_set_launch_config(b, i)
-            R, st, v = pkg.analyze(ctx(), b, blocking_mode=1, **p)
-            torch.cuda.synchronize()
-            assert_same(dict(R=R.cpu().numpy(), status=st.cpu().numpy(), verdict=v.cpu().numpy()), ref)
+            assert_same(analyze_poisoned(ctx(), b, blocking_mode=1, **p), ref)
         b.free()
