@@ -620,9 +620,10 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     ++k;
     // the lazy kernel also defers systems inside the 32-bit bound that are not narrow
     const bool lazy_defers = cfg.impl_small >= 2 && b->stats[ST_DMAX] >= kLazyNarrowD;
-    if ((b->max_chains > cfg.maxn_small || lazy_defers) && cfg.impl_big == kImplBigLazy32) {
+    const bool lazy_passes = (b->max_chains > cfg.maxn_small || lazy_defers) && cfg.impl_big == kImplBigLazy32;
+    if (lazy_passes) {
         // 17..32 chains in the 32-lane lazy kernel, then the rest of the list (over 32
-        // chains) in the 64-chain register tables, with static shares
+        // chains) in the 64-chain lazy kernel, with static shares
         rc = launch_lazy32<6>(b, pb, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
         if (rc != PAAM_OK) return rc;
         ++k;
@@ -630,7 +631,7 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
             AnalysisParams ph = pb;
             ph.queue_batch = 0;
             ph.min_chains = 33;
-            rc = launch_reg<32, 2>(b, ph, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
+            rc = launch_lazy64(b, ph, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
             if (rc != PAAM_OK) return rc;
             ++k;
         }
@@ -641,7 +642,7 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     }
     // the int64 kernel for the systems outside the 32-bit bound, and (the 32-lane lazy
     // pass sends them there) for the deferred systems inside it that are not narrow
-    if (!batch_fits_32(b, p) || (lazy_defers && cfg.impl_big == kImplBigLazy32)) {
+    if (!batch_fits_32(b, p) || (lazy_passes && b->stats[ST_DMAX] >= kLazyDeferWideD)) {
         rc = paam_launch_wide(b, pw, R, status, verdict, b->list_wide, b->counts + 1, items, stream);
         if (rc != PAAM_OK) return rc;
         ++k;

@@ -253,9 +253,18 @@ constexpr unsigned long long kLazyNarrowD = (1ull << 27) - 16;
 template <int BLOCKS>
 int launch_lazy32(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                   const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
+// The same analysis with one warp per system and two chains per lane
+// (analyze_lazy64.cu) over b->list_big after the 32-lane pass: systems of
+// AnalysisParams::min_chains (33) to 64 chains inside the narrow bound; those
+// that are not narrow (a deadline at or above kLazyDeferWideD) go to b->list_wide.
+int launch_lazy64(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                  const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
 // impl_big value of a launch configuration whose deferral list goes to the 32-lane
-// lazy kernel and then, for systems over 32 chains, to the 64-chain register tables
+// lazy kernel and then, for systems over 32 chains, to the 64-chain lazy kernel
 constexpr int kImplBigLazy32 = 9;
+// the lowest deadline that the deferral passes of such a configuration send to the
+// int64 kernel (the 64-chain pass's narrow bound)
+constexpr unsigned long long kLazyDeferWideD = (1ull << 27) - 64;
 
 // Register-table kernels (analyze_reg.cu): G lanes per system, CPL chains per lane.
 template <int G, int CPL>

@@ -65,27 +65,36 @@ def test_every_launch_config_bit_exact():
     b.free()
 
 
-def test_every_launch_config_between_the_narrow_and_32_bit_bounds():
-    """Systems with deadlines between the narrow bound of the 32-bit kernels
-    (2^27) and the 32-bit bound (2^30) among ordinary ones: the batch takes the
-    32-bit path, but those systems are deferred by the narrow kernels; every
-    configuration must still analyse each of them (bit-exact)."""
-    import torch
-
-    import paper_2404_06452_gb300 as pkg
-
+def _with_wide_deadlines(periods, n_min, n_max, implicit, seed):
     a = g.generate("cfg3", n_sys=3000)
-    rng = random.Random(23)
-    mid = [tiny.tiny_system(rng, n_min=2, n_max=40, cb_max=5, x_max=6, periods=tuple(range(2**27, 2**29, 2**22)),
-                            e_max=2**22, a_max=2**21, p_seg=0.5, p_spin=0.5, seg_max=2) for _ in range(200)]
+    rng = random.Random(seed)
+    mid = [tiny.tiny_system(rng, n_min=n_min, n_max=n_max, cb_max=5, x_max=6, periods=periods, e_max=2**21,
+                            a_max=2**20, p_seg=0.5, p_spin=0.5, seg_max=2, implicit_deadline=implicit)
+           for _ in range(200)]
     b = tiny.to_systems(mid)
     out, k = [], 0
     for i in range(b.n_sys):
         out.append(a.subset(np.arange(k, k + 15)))
         out.append(b.subset(np.array([i])))
         k += 15
-    sy = _concat(out)
-    assert sy.T.max() < 2**30 and sy.D.max() >= 2**27
+    return _concat(out)
+
+
+@pytest.mark.parametrize("case", ["deadlines 2^26..2^29", "deadline 2^27 - 40, 33-64 chains"])
+def test_every_launch_config_between_the_narrow_and_32_bit_bounds(case):
+    """Systems with deadlines at or above the narrow bounds of the 32-bit
+    kernels (2^27 less 16, 32 or 64 by kernel) among ordinary ones: the batch
+    takes the 32-bit path, but the narrow kernels defer those systems; every
+    configuration must still analyse each of them (bit-exact)."""
+    import paper_2404_06452_gb300 as pkg
+
+    if case.startswith("deadlines"):
+        sy = _with_wide_deadlines(tuple(range(2**27, 2**29, 2**22)), 2, 40, False, 23)
+        assert sy.D.max() >= 2**27
+    else:  # below the first pass's bound, above the 64-chain pass's
+        sy = _with_wide_deadlines((2**27 - 40,), 33, 64, True, 29)
+        assert sy.D.max() == 2**27 - 40
+    assert sy.T.max() < 2**30
     ref = oracle.analyze(sy, threads=8)
     bt = pkg.paam_rta_load_systems(ctx(), sy)
     for i in range(pkg.paam_rta_num_launch_configs()):
