@@ -623,13 +623,19 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
     const bool lazy_passes = (b->max_chains > cfg.maxn_small || lazy_defers) && cfg.impl_big == kImplBigLazy32;
     if (lazy_passes) {
         // 17..32 chains in the 32-lane lazy kernel, then the rest of the list (over 32
-        // chains) in the 64-chain lazy kernel, with static shares
+        // chains) in the 64-chain lazy kernel, one system per fetch from the work queue
+        // (the first pass's counter, reset: that pass is done)
         rc = launch_lazy32<6>(b, pb, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
         if (rc != PAAM_OK) return rc;
         ++k;
         if (b->max_chains > 32) {
             AnalysisParams ph = pb;
             ph.queue_batch = 0;
+            if (cfg.queue > 0 && b->queue) {
+                PAAM_CUDA_TRY(cudaMemsetAsync(b->queue, 0, sizeof(unsigned long long), stream));
+                ph.queue = b->queue;
+                ph.queue_batch = 1;
+            }
             ph.min_chains = 33;
             rc = launch_lazy64(b, ph, R, status, verdict, b->list_big, b->counts, items, cfg.threads, stream);
             if (rc != PAAM_OK) return rc;
