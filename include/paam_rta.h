@@ -363,6 +363,29 @@ int paam_surrogate_infer(paam_ctx *ctx, const paam_model *model, const paam_batc
                          int32_t top_k, int32_t *ranked, float *scores, void *stream);
 int paam_surrogate_predict(paam_ctx *ctx, const paam_model *model, const paam_batch *batch, int32_t n_buckets,
                            int64_t kappa_ns, float *pred, void *stream);
+
+/*
+ * paam_surrogate_search: the priority-assignment search with exact verdicts,
+ * guided by the network (the admission test of Sec. IV-A on each visited
+ * candidate, the analysis of Sec. IV-F).  Per system, candidates 0 ..
+ * n_pinned-1 (the pinned seeds) are analysed first, in slot order; for the
+ * systems none of them admits, the network scores the other K - n_pinned
+ * candidates, and its 32 best (in increasing score) and then the rest (in
+ * index order) are analysed, each system stopping at its first admitted
+ * candidate.  Every candidate of a system is visited
+ * unless an earlier one is admitted, so first_ok[s] >= 0 exactly when
+ * paam_rta_search_priorities finds an admitted candidate of s; first_ok[s] is
+ * then the one found first in this order (a candidate index), else -1.
+ * ranks and nmax as for paam_rta_search_priorities (K candidates per system,
+ * at most 64 chains); o as for the analysis (its n_buckets and kappa_ns also
+ * feed the features); first_ok device int32 [n_sys].  Blocks until done.
+ * PAAM_E_INVAL for bad arguments (n_pinned outside 0..K, a rank row that is
+ * not a permutation), PAAM_E_STATE for a model or batch of another context,
+ * PAAM_E_RANGE for n_sys * K above 2^31 - 1.
+ */
+int paam_surrogate_search(paam_ctx *ctx, const paam_model *model, const paam_batch *batch,
+                          const paam_analysis_opts *opts, const int16_t *ranks, int32_t K, int32_t nmax,
+                          int32_t n_pinned, int32_t *first_ok, void *stream);
 int paam_surrogate_grad(paam_ctx *ctx, paam_model *model, const void *X, const float *L, int32_t rows,
                         float *grads_host, float *loss_host);
 

@@ -98,6 +98,9 @@ def lib():
                                                     ctypes.c_int32, _c_void_p, _c_void_p, _c_void_p]),
             "paam_surrogate_predict": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
                                                       ctypes.c_int64, _c_void_p, _c_void_p]),
+            "paam_surrogate_search": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, P(AnalysisOpts), _c_void_p,
+                                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _c_void_p,
+                                                     _c_void_p]),
             "paam_surrogate_grad": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
                                                    _c_void_p, _c_void_p]),
             "paam_surrogate_features": (ctypes.c_int, [_c_void_p, _c_void_p, _c_void_p, ctypes.c_int32,
@@ -138,7 +141,7 @@ def exported_symbols() -> list:
             "paam_rta_get_launch_config", "paam_rta_analyze_noalloc", "paam_rta_search_priorities",
             "paam_tc_gemm_bf16", "paam_rta_search_ordered", "paam_model_create", "paam_model_free",
             "paam_model_num_params", "paam_model_get_params", "paam_model_set_params", "paam_model_save",
-            "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict",
+            "paam_model_load", "paam_surrogate_train", "paam_surrogate_infer", "paam_surrogate_predict", "paam_surrogate_search",
             "paam_surrogate_grad", "paam_surrogate_features", "paam_diag_gelu", "paam_diag_divisor", "paam_rta_end_to_end",
             "paam_measure_preemption", "paam_rta_audsley_order", "paam_rta_analyze_host",
             "paam_rta_autotune_search"]
@@ -468,6 +471,18 @@ def paam_surrogate_train(ctx: Context, batch: Batch, R, status, opts: TrainOpts,
     _check(lib().paam_surrogate_train(ctx.handle, batch.handle, _ptr(R), _ptr(status), ctypes.byref(opts),
                                       ctypes.byref(h)), "paam_surrogate_train")
     return model if model is not None else Model(ctx, h)
+
+
+def paam_surrogate_search(ctx: Context, model: Model, batch: Batch, opts: AnalysisOpts, ranks, first_ok,
+                          n_pinned: int = 0, stream=None):
+    """The exact search guided by the network over the candidates ``ranks``
+    ([S, K, nmax] device int16): the first ``n_pinned`` slots, then the others in
+    the network's order, each system stopping at its first admitted candidate;
+    ``first_ok`` ([S] device int32) gets that candidate or -1."""
+    S, K, nmax = ranks.shape
+    _check(lib().paam_surrogate_search(ctx.handle, model.handle, batch.handle, ctypes.byref(opts), _ptr(ranks),
+                                       int(K), int(nmax), int(n_pinned), _ptr(first_ok), _stream_ptr(stream)),
+           "paam_surrogate_search")
 
 
 def paam_surrogate_infer(ctx: Context, model: Model, batch: Batch, ranks, top_k: int, ranked, scores=None,

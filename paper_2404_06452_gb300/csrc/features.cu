@@ -30,14 +30,15 @@ struct FeatSmem {
 
 __global__ void __launch_bounds__(256) features_kernel(BatchDev b, const int16_t *ranks, int32_t K, int32_t nmax,
                                                        int64_t sys0, int64_t n_items, int32_t n_buckets,
-                                                       int64_t kappa, int32_t slots, __nv_bfloat16 *X)
+                                                       int64_t kappa, int32_t slots, __nv_bfloat16 *X,
+                                                       const int32_t *sys_list)
 {
     __shared__ FeatSmem sm[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     FeatSmem &s = sm[warp];
     const int64_t gw = (int64_t)blockIdx.x * 8 + warp, nw = (int64_t)gridDim.x * 8;
     for (int64_t item = gw; item < n_items; item += nw) {
-        const int64_t sys = sys0 + item / K;
+        const int64_t sys = sys_list ? (int64_t)sys_list[sys0 + item / K] : sys0 + item / K;
         const int32_t cand = (int32_t)(item % K);
         const int64_t c0 = b.sys_chain_off[sys];
         const int n = (int)(b.sys_chain_off[sys + 1] - c0);
@@ -199,7 +200,7 @@ template <int L>
 __global__ void __launch_bounds__(CF_THREADS) cand_features_kernel(BatchDev b, const int16_t *ranks, int32_t K,
                                                                    int32_t nmax, int64_t sys0, int64_t n_systems,
                                                                    int32_t n_buckets, int64_t kappa, int32_t slots,
-                                                                   __nv_bfloat16 *X)
+                                                                   __nv_bfloat16 *X, const int32_t *sys_list)
 {
     __shared__ CandSmem s;
     constexpr int SEGS = CF_THREADS / L;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(CF_THREADS) cand_features_kernel(BatchDev b, c
     const unsigned lt = (1u << lane) - 1u;                        // lanes under this one in the warp
     const unsigned gt = ~lt & ~(1u << lane);
     for (int64_t si = blockIdx.x; si < n_systems; si += gridDim.x) {
-        const int64_t sys = sys0 + si;
+        const int64_t sys = sys_list ? (int64_t)sys_list[sys0 + si] : sys0 + si;
         const int64_t c0 = b.sys_chain_off[sys];
         const int n = (int)(b.sys_chain_off[sys + 1] - c0);
         const int64_t x0 = b.sys_exec_off[sys];
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(CF_THREADS) cand_features_kernel(BatchDev b, c
 
 int paam_launch_features(const paam_batch *b, const int16_t *ranks, int32_t K, int32_t nmax, int64_t sys0,
                          int64_t n_items, int32_t n_buckets, int64_t kappa, int32_t width, __nv_bfloat16 *X,
-                         cudaStream_t stream)
+                         cudaStream_t stream, const int32_t *sys_list)
 {
     if (n_items <= 0) return PAAM_OK;
     if (width % NF || width / NF < b->max_chains || width > NCH * NF) return PAAM_E_INVAL;
@@ -447,15 +448,15 @@ int paam_launch_features(const paam_batch *b, const int16_t *ranks, int32_t K, i
         if (blocks > (int64_t)per_sm * b->ctx->n_sm) blocks = (int64_t)per_sm * b->ctx->n_sm;
         if (l16)
             cand_features_kernel<16><<<(unsigned)blocks, CF_THREADS, 0, stream>>>(
-                batch_dev(b), ranks, K, nmax, sys0, n_systems, n_buckets, kappa, slots, X);
+                batch_dev(b), ranks, K, nmax, sys0, n_systems, n_buckets, kappa, slots, X, sys_list);
         else
             cand_features_kernel<32><<<(unsigned)blocks, CF_THREADS, 0, stream>>>(
-                batch_dev(b), ranks, K, nmax, sys0, n_systems, n_buckets, kappa, slots, X);
+                batch_dev(b), ranks, K, nmax, sys0, n_systems, n_buckets, kappa, slots, X, sys_list);
     } else {
         int64_t blocks = (n_items + 7) / 8;
         if (blocks > 32 * (int64_t)b->ctx->n_sm) blocks = 32 * (int64_t)b->ctx->n_sm;
         features_kernel<<<(unsigned)blocks, 256, 0, stream>>>(batch_dev(b), ranks, K, nmax, sys0, n_items,
-                                                              n_buckets, kappa, slots, X);
+                                                              n_buckets, kappa, slots, X, sys_list);
     }
     PAAM_CUDA_TRY(cudaGetLastError());
     paam_count_launch();

@@ -233,6 +233,15 @@ struct LaunchCfg {
 // window of this many consecutive systems).
 constexpr int kBinWindow = 8192;
 
+// paam_rta_search_ordered continued from a given state (search.cu): first_ok
+// holds K (nothing admitted yet) or -1 (skip the system) per system; the
+// systems' slots are visited in `order` (the library's own, not checked) with
+// stop at the first admitted candidate, and first_ok then holds its candidate
+// index or -1.
+int paam_search_ordered_from(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o, const int16_t *ranks,
+                             int32_t Kc, int32_t nmax, const int32_t *order, int32_t K, int32_t *first_ok,
+                             cudaStream_t stream);
+
 // Builds b->sys_order (api.cu): a counting sort of the systems by chain count
 // within each window of consecutive systems.
 int paam_launch_bin_by_size(const paam_batch *b, int32_t *order, cudaStream_t stream);

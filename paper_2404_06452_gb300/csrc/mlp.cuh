@@ -29,12 +29,14 @@ struct TcEpilogue {
     int ldh;
     __nv_bfloat16 *HT;             // H transposed ([N][M]), optional
     int ldht;
-    // TC_EPI_ROWMAX: row r belongs to system sys0 + r / rows_per_sys, whose
-    // chain count (sys_off[s + 1] - sys_off[s]) is the number of valid columns;
-    // C[r] must start non-negative (the maximum is taken on the float bits)
+    // TC_EPI_ROWMAX: row r belongs to system sys0 + r / rows_per_sys (with
+    // sys_list, to system sys_list[sys0 + r / rows_per_sys]), whose chain count
+    // (sys_off[s + 1] - sys_off[s]) is the number of valid columns; C[r] must
+    // start non-negative (the maximum is taken on the float bits)
     const int64_t *sys_off;
     int64_t sys0;
     int rows_per_sys;
+    const int32_t *sys_list;
     // TC_EPI_STORE_F32 with splits > 1: each split stores its partial product
     // into its own [M][ldc] slice, C + split * split_stride (summed afterwards
     // in a fixed order, so the result does not depend on scheduling)
@@ -65,11 +67,11 @@ int tc_gemm(const TcGemm &g, int32_t *err, cudaStream_t stream);
 
 
 // Surrogate input features (features.cu): rows item = (system - sys0) * K +
-// candidate for items [0, n_items) of systems starting at sys0; ranks NULL =
-// the systems' own priorities (K = 1).  X is [n_items][width] bf16 with width =
+// candidate for items [0, n_items) of systems starting at sys0 (with sys_list,
+// of systems sys_list[sys0 ..]); ranks NULL = the systems' own priorities (K = 1).  X is [n_items][width] bf16 with width =
 // 16 x (chain slots), a multiple of 16 of at least 16 x the batch's largest
 // chain count and at most 1024; slots past a system's chains are zero, so a
 // first layer may read only the first width columns of its 1024-wide input.
 int paam_launch_features(const paam_batch *b, const int16_t *ranks, int32_t K, int32_t nmax, int64_t sys0,
                          int64_t n_items, int32_t n_buckets, int64_t kappa, int32_t width, __nv_bfloat16 *X,
-                         cudaStream_t stream);
+                         cudaStream_t stream, const int32_t *sys_list = nullptr);

@@ -64,7 +64,8 @@ __device__ __forceinline__ void epilogue_chunk(const TcEpilogue &ep, int row, in
         break;
     }
     case TC_EPI_ROWMAX: {
-        const int64_t sys = ep.sys0 + row / ep.rows_per_sys;
+        const int64_t sys = ep.sys_list ? (int64_t)ep.sys_list[ep.sys0 + row / ep.rows_per_sys]
+                                        : ep.sys0 + row / ep.rows_per_sys;
         const int n = (int)(ep.sys_off[sys + 1] - ep.sys_off[sys]);
         if (col0 >= n) break;
         add_bias(ep, col0, full, a);

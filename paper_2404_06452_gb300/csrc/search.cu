@@ -22,13 +22,14 @@ __global__ void search_init(int32_t *first_ok, int64_t n_sys, int32_t K, uint8_t
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_cand; i += stride) cand_ok[i] = 0;
 }
 
-// slot of the first admitted candidate -> its candidate index (or -1)
+// slot of the first admitted candidate -> its candidate index (or -1; a system
+// that started at -1, with nothing to visit, keeps it)
 __global__ void search_final(int32_t *first_ok, int64_t n_sys, int32_t K, const int32_t *order)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sys; i += stride) {
         const int32_t v = first_ok[i];
-        first_ok[i] = v >= K ? -1 : (order ? order[i * K + v] : v);
+        first_ok[i] = (v < 0 || v >= K) ? -1 : (order ? order[i * K + v] : v);
     }
 }
 
@@ -49,10 +50,14 @@ extern "C" int paam_rta_search_priorities(paam_ctx *ctx, const paam_batch *b, co
                                    stream_);
 }
 
-extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o,
-                                       const int16_t *ranks, int32_t Kc, int32_t nmax, const int32_t *order,
-                                       int32_t K, int32_t stop_at_first, uint8_t *cand_ok, int32_t *first_ok,
-                                       void *stream_)
+namespace {
+
+// resume: first_ok holds, per system, K (nothing admitted yet) or -1 (skip the
+// system); its slots are visited with stop_at_first, the order is trusted (the
+// library's own) and nothing else is initialised.
+int search_ordered_impl(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o, const int16_t *ranks,
+                        int32_t Kc, int32_t nmax, const int32_t *order, int32_t K, int32_t stop_at_first,
+                        uint8_t *cand_ok, int32_t *first_ok, void *stream_, bool resume)
 {
     if (!ctx || !b || !o || !first_ok) return PAAM_E_INVAL;
     if (b->ctx != ctx) return PAAM_E_STATE;
@@ -88,10 +93,12 @@ extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const
     int blocks = (int)((items + threads - 1) / threads);
     if (blocks > 8 * ctx->n_sm) blocks = 8 * ctx->n_sm;
     if (cudaMemsetAsync(err, 0, sizeof(int32_t), stream) != cudaSuccess) rc = PAAM_E_CUDA;
-    search_init<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K, cand_ok, b->n_sys * (int64_t)Kc);
-    if (order) check_order<<<blocks, threads, 0, stream>>>(order, items, Kc, err);
+    if (!resume) {
+        search_init<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K, cand_ok, b->n_sys * (int64_t)Kc);
+        if (order) check_order<<<blocks, threads, 0, stream>>>(order, items, Kc, err);
+    }
     if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-    if (order && rc == PAAM_OK) { // an out-of-range slot must not reach the analysis kernels
+    if (order && !resume && rc == PAAM_OK) { // an out-of-range slot must not reach the analysis kernels
         int32_t herr = 0;
         if (cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess)
@@ -121,7 +128,7 @@ extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const
     if (rc == PAAM_OK) {
         search_final<<<blocks, threads, 0, stream>>>(first_ok, b->n_sys, K, order);
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-        paam_count_launch((unsigned)nk + (order ? 3 : 2));
+        paam_count_launch((unsigned)nk + (resume ? 1 : (order ? 3 : 2)));
     }
     int32_t herr = 0;
     if (cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, stream) != cudaSuccess) rc = PAAM_E_CUDA;
@@ -129,6 +136,24 @@ extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const
     if (cudaStreamSynchronize(stream) != cudaSuccess) rc = PAAM_E_CUDA;
     if (rc == PAAM_OK && herr != 0) rc = herr;
     return rc;
+}
+
+} // namespace
+
+extern "C" int paam_rta_search_ordered(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o,
+                                       const int16_t *ranks, int32_t Kc, int32_t nmax, const int32_t *order,
+                                       int32_t K, int32_t stop_at_first, uint8_t *cand_ok, int32_t *first_ok,
+                                       void *stream_)
+{
+    return search_ordered_impl(ctx, b, o, ranks, Kc, nmax, order, K, stop_at_first, cand_ok, first_ok, stream_,
+                               false);
+}
+
+int paam_search_ordered_from(paam_ctx *ctx, const paam_batch *b, const paam_analysis_opts *o, const int16_t *ranks,
+                             int32_t Kc, int32_t nmax, const int32_t *order, int32_t K, int32_t *first_ok,
+                             cudaStream_t stream)
+{
+    return search_ordered_impl(ctx, b, o, ranks, Kc, nmax, order, K, 1, nullptr, first_ok, stream, true);
 }
 
 // The search's own autotuner: every launch configuration timed on the search

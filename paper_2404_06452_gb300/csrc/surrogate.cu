@@ -296,15 +296,22 @@ __global__ void to_bf16_kernel(const float *W, int64_t n, int rows, int cols, __
 }
 
 // ---- per system: the top_k candidates in increasing score (ties: lower
-// index), the first n_pinned candidate slots ahead of every scored one
+// index), the first n_pinned candidate slots ahead of every scored one.  Row i
+// of score is system i (with sys_list, system sys_list[i]); the picks after the
+// first `skip` go to that system's row of ranked (row_len entries per row, 0:
+// top_k - skip), followed, when row_len is longer, by the candidates not picked
+// in index order.
 __global__ void topk_kernel(const float *score, int64_t n_sys, int32_t K, int32_t n_pinned, int32_t top_k,
-                            int32_t *ranked)
+                            int32_t *ranked, const int32_t *sys_list = nullptr, int32_t skip = 0,
+                            int32_t row_len = 0)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t sys = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (sys >= n_sys) return;
     const float *s = score + sys * K;
-    int32_t *out = ranked + sys * top_k;
+    const int64_t row = sys_list ? (int64_t)sys_list[sys] : sys;
+    const int32_t len = row_len > 0 ? row_len : top_k - skip;
+    int32_t *out = ranked + row * len;
     // pick repeatedly the smallest (score, index) above the previous pick
     float last_s = -INFINITY;
     int last_i = -1;
@@ -327,9 +334,24 @@ __global__ void topk_kernel(const float *score, int64_t n_sys, int32_t K, int32_
                 best_i = oi;
             }
         }
-        if (lane == 0) out[t] = best_i;
+        if (lane == 0 && t >= skip) out[t - skip] = best_i;
         last_s = best_s;
         last_i = best_i;
+    }
+    if (len <= top_k - skip) return;
+    // the rest: exactly the candidates above the last pick, in index order
+    int base = top_k - skip;
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int k = k0 + lane;
+        bool rest = false;
+        if (k < K) {
+            const float v = k < n_pinned ? -INFINITY : (isnan(s[k]) ? INFINITY : s[k]);
+            rest = v > last_s || (v == last_s && k > last_i);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, rest);
+        const int at = base + __popc(m & ((1u << lane) - 1u));
+        if (rest && at < len) out[at] = k;
+        base += __popc(m);
     }
 }
 
@@ -623,6 +645,7 @@ struct ScoreOut {
     const int64_t *sys_off;
     int64_t sys0;
     int K;
+    const int32_t *sys_list; // rows' systems through this list (NULL: consecutive from sys0)
 };
 
 int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool train, cudaStream_t s,
@@ -661,6 +684,7 @@ int forward(const paam_model *m, Work &w, const __nv_bfloat16 *X, int kx, bool t
         g.ep.sys_off = so->sys_off;
         g.ep.sys0 = so->sys0;
         g.ep.rows_per_sys = so->K;
+        g.ep.sys_list = so->sys_list;
     }
     return tc_gemm(g, w.err, s);
 }
@@ -931,27 +955,26 @@ extern "C" int paam_surrogate_train(paam_ctx *ctx, const paam_batch *b, const in
 // ---------------------------------------------------------------------------
 // inference
 // ---------------------------------------------------------------------------
-extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const paam_batch *b, const int16_t *ranks,
-                                    int32_t K, int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t n_pinned,
-                                    int32_t top_k, int32_t *ranked, float *scores, void *stream_)
+namespace {
+
+// Scores and ranks the K candidates of n_list systems: systems 0 .. n_list - 1,
+// or with sys_list (device) the systems sys_list[0 .. n_list).  Each system's
+// picks after the first `skip` go to its row of ranked (rows by system index,
+// row_len entries; 0: top_k - skip), then the candidates not picked in index
+// order (topk_kernel); scores (optional, device [n_list][K]) by list position.
+int infer_rank(paam_ctx *ctx, const paam_model *m, const paam_batch *b, const int16_t *ranks, int32_t K,
+               int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t n_pinned, int32_t top_k, int32_t skip,
+               const int32_t *sys_list, int64_t n_list, int32_t *ranked, float *scores, cudaStream_t s,
+               int32_t row_len = 0)
 {
-    if (!ctx || !m || !b || (b->n_sys > 0 && (!ranks || !ranked))) return PAAM_E_INVAL;
-    if (m->ctx != ctx || b->ctx != ctx) return PAAM_E_STATE;
-    if (K < 1 || top_k < 1 || top_k > K || n_pinned < 0 || n_pinned > K || nmax < b->max_chains || n_buckets < 1 ||
-        kappa_ns < 0 ||
-        kappa_ns > PAAM_MAX_OVERHEAD)
-        return PAAM_E_INVAL;
-    if (b->max_chains > NCH) return PAAM_E_UNSUPPORTED;
-    if (b->n_sys == 0) return PAAM_OK;
-    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
-    cudaStream_t s = (cudaStream_t)stream_;
+    if (n_list == 0) return PAAM_OK;
     // candidates are scored in equal chunks of whole systems of at most about
     // kInferRows rows: each chunk pays a fixed cost (launches, the weight load
     // of every persistent CTA, the last tile's epilogue running alone), so
     // chunks are as large as the scratch allows
-    const int64_t total = b->n_sys * (int64_t)K;
+    const int64_t total = n_list * (int64_t)K;
     const int64_t n_chunks = (total + kInferRows - 1) / kInferRows;
-    const int64_t chunk = (b->n_sys + n_chunks - 1) / n_chunks;
+    const int64_t chunk = (n_list + n_chunks - 1) / n_chunks;
     const int rows = (int)(chunk * K);
     const int kx = input_width(b);
     Work w;
@@ -960,7 +983,7 @@ extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const pa
     float *sc = scores;
     void *tmp = nullptr;
     if (!sc) {
-        if (cudaMallocAsync(&tmp, 4 * (size_t)b->n_sys * K, s) != cudaSuccess) {
+        if (cudaMallocAsync(&tmp, 4 * (size_t)n_list * K, s) != cudaSuccess) {
             cudaGetLastError();
             cudaFreeAsync(w.block, s);
             return PAAM_E_NOMEM;
@@ -968,17 +991,18 @@ extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const pa
         sc = (float *)tmp;
     }
     if (cudaMemsetAsync(w.err, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
-    for (int64_t s0 = 0; s0 < b->n_sys && rc == PAAM_OK; s0 += chunk) {
-        const int64_t ns = (s0 + chunk <= b->n_sys) ? chunk : b->n_sys - s0;
+    for (int64_t s0 = 0; s0 < n_list && rc == PAAM_OK; s0 += chunk) {
+        const int64_t ns = (s0 + chunk <= n_list) ? chunk : n_list - s0;
         const int64_t items = ns * K;
         Work wc = w;
         wc.rows = (int)items;
-        rc = paam_launch_features(b, ranks, K, nmax, s0, items, n_buckets, kappa_ns, kx, wc.Xb, s);
-        const ScoreOut so = {sc + s0 * K, b->sys_chain_off, s0, K};
+        rc = paam_launch_features(b, ranks, K, nmax, s0, items, n_buckets, kappa_ns, kx, wc.Xb, s, sys_list);
+        const ScoreOut so = {sc + s0 * K, b->sys_chain_off, s0, K, sys_list};
         if (rc == PAAM_OK) rc = forward(m, wc, wc.Xb, kx, false, s, &so);
     }
     if (rc == PAAM_OK) {
-        topk_kernel<<<(unsigned)((b->n_sys + 7) / 8), 256, 0, s>>>(sc, b->n_sys, K, n_pinned, top_k, ranked);
+        topk_kernel<<<(unsigned)((n_list + 7) / 8), 256, 0, s>>>(sc, n_list, K, n_pinned, top_k, ranked, sys_list,
+                                                                 skip, row_len);
         if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
         paam_count_launch();
     }
@@ -988,6 +1012,141 @@ extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const pa
     if (tmp) cudaFreeAsync(tmp, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = PAAM_E_CUDA;
     if (rc == PAAM_OK && herr != 0) rc = herr;
+    return rc;
+}
+
+int check_infer_args(const paam_model *m, const paam_batch *b, int32_t K, int32_t nmax, int32_t n_buckets,
+                     int64_t kappa_ns, int32_t n_pinned, int32_t top_k)
+{
+    if (K < 1 || top_k < 1 || top_k > K || n_pinned < 0 || n_pinned > K || nmax < b->max_chains || n_buckets < 1 ||
+        kappa_ns < 0 || kappa_ns > PAAM_MAX_OVERHEAD)
+        return PAAM_E_INVAL;
+    if (b->max_chains > NCH) return PAAM_E_UNSUPPORTED;
+    return PAAM_OK;
+}
+
+constexpr int32_t kGuidedPicks = 32; // candidates the guided search takes in the network's order
+
+// identity slot order over the first np candidates of every system
+__global__ void ident_order_kernel(int32_t *order, int64_t n_sys, int32_t np)
+{
+    const int64_t n = n_sys * np, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) order[i] = (int32_t)(i % np);
+}
+
+// systems without an admitted pinned candidate (fa < 0) go to list; first_ok gets
+// -1 (nothing left to visit) for the others and Kr (no candidate yet) for these
+__global__ void undecided_kernel(const int32_t *fa, int64_t n_sys, int32_t Kr, int32_t *list, int32_t *count,
+                                 int32_t *first_ok)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sys; i += stride) {
+        const bool open = fa[i] < 0;
+        first_ok[i] = open ? Kr : -1;
+        if (open) list[atomicAdd(count, 1)] = (int32_t)i;
+    }
+}
+
+__global__ void combine_kernel(const int32_t *fa, int64_t n_sys, int32_t *first_ok)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sys; i += stride)
+        if (fa[i] >= 0) first_ok[i] = fa[i];
+}
+
+} // namespace
+
+extern "C" int paam_surrogate_infer(paam_ctx *ctx, const paam_model *m, const paam_batch *b, const int16_t *ranks,
+                                    int32_t K, int32_t nmax, int32_t n_buckets, int64_t kappa_ns, int32_t n_pinned,
+                                    int32_t top_k, int32_t *ranked, float *scores, void *stream_)
+{
+    if (!ctx || !m || !b || (b->n_sys > 0 && (!ranks || !ranked))) return PAAM_E_INVAL;
+    if (m->ctx != ctx || b->ctx != ctx) return PAAM_E_STATE;
+    int rc = check_infer_args(m, b, K, nmax, n_buckets, kappa_ns, n_pinned, top_k);
+    if (rc != PAAM_OK) return rc;
+    if (b->n_sys == 0) return PAAM_OK;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    return infer_rank(ctx, m, b, ranks, K, nmax, n_buckets, kappa_ns, n_pinned, top_k, 0, nullptr, b->n_sys, ranked,
+                      scores, (cudaStream_t)stream_);
+}
+
+// The exact search guided by the network: the pinned candidates of every system
+// first, then, for the systems none of them admits, all other candidates in the
+// network's order, stopping at the first admitted one.  Every visited candidate
+// is analysed exactly, and a system's candidates are visited until one is
+// admitted or none is left, so first_ok[s] >= 0 exactly when the exhaustive
+// search admits a candidate of s.
+extern "C" int paam_surrogate_search(paam_ctx *ctx, const paam_model *m, const paam_batch *b,
+                                     const paam_analysis_opts *o, const int16_t *ranks, int32_t K, int32_t nmax,
+                                     int32_t n_pinned, int32_t *first_ok, void *stream_)
+{
+    if (!ctx || !m || !b || !o || (b->n_sys > 0 && (!ranks || !first_ok))) return PAAM_E_INVAL;
+    if (m->ctx != ctx || b->ctx != ctx) return PAAM_E_STATE;
+    int rc = check_infer_args(m, b, K, nmax, o->n_buckets, o->kappa_ns, n_pinned, K);
+    if (rc != PAAM_OK) return rc;
+    if (b->n_sys * (int64_t)K > (int64_t)INT32_MAX) return PAAM_E_RANGE;
+    if (b->n_sys == 0) return PAAM_OK;
+    PAAM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream_;
+    const int64_t n = b->n_sys;
+    const int32_t Kr = K - n_pinned; // candidates left after the pinned ones
+    // scratch: pinned order or network order ([n][max(n_pinned, Kr)]), the pinned
+    // phase's results, the list of open systems and its length
+    const int32_t w = n_pinned > Kr ? n_pinned : Kr;
+    void *blk = nullptr;
+    const size_t ob = 4 * (size_t)n * (w > 0 ? w : 1);
+    if (cudaMallocAsync(&blk, ob + 8 * (size_t)n + 256, s) != cudaSuccess) {
+        cudaGetLastError();
+        return PAAM_E_NOMEM;
+    }
+    int32_t *order = (int32_t *)blk;
+    int32_t *fa = (int32_t *)((char *)blk + ob);
+    int32_t *list = fa + n;
+    int32_t *count = list + n;
+    const unsigned grid = grid_for(n * (w > 0 ? w : 1), 256, ctx->n_sm);
+    if (cudaMemsetAsync(count, 0, 4, s) != cudaSuccess) rc = PAAM_E_CUDA;
+    // 1. the pinned candidates, in slot order, stopping at the first admitted one
+    if (rc == PAAM_OK && n_pinned > 0) {
+        ident_order_kernel<<<grid, 256, 0, s>>>(order, n, n_pinned);
+        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        paam_count_launch();
+        if (rc == PAAM_OK) rc = paam_rta_search_ordered(ctx, b, o, ranks, K, nmax, order, n_pinned, 1, nullptr, fa, s);
+    } else if (rc == PAAM_OK && cudaMemsetAsync(fa, 0xff, 4 * (size_t)n, s) != cudaSuccess) { // -1: none admitted
+        rc = PAAM_E_CUDA;
+    }
+    // 2. the systems left open, and the network's order of their other candidates
+    int32_t n_open = 0;
+    if (rc == PAAM_OK) {
+        undecided_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>(fa, n, Kr, list, count, first_ok);
+        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        paam_count_launch();
+        if (rc == PAAM_OK && (cudaMemcpyAsync(&n_open, count, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                              cudaStreamSynchronize(s) != cudaSuccess))
+            rc = PAAM_E_CUDA;
+    }
+    if (rc == PAAM_OK && n_open > 0 && Kr > 0) {
+        // every row valid (the closed systems' rows are never read: their slots are pruned)
+        if (cudaMemsetAsync(order, 0, 4 * (size_t)n * Kr, s) != cudaSuccess) rc = PAAM_E_CUDA;
+        // the network's kGuidedPicks best in increasing score, then the others in index
+        // order (a full ranking costs a selection per candidate; an admissible system is
+        // found among the best few, an inadmissible one needs every candidate anyway)
+        const int32_t picks = Kr < kGuidedPicks ? Kr : kGuidedPicks;
+        if (rc == PAAM_OK)
+            rc = infer_rank(ctx, m, b, ranks, K, nmax, o->n_buckets, o->kappa_ns, n_pinned, n_pinned + picks,
+                            n_pinned, list, n_open, order, nullptr, s, Kr);
+        // 3. those candidates in that order, stopping at the first admitted one; the
+        // closed systems (first_ok -1) are skipped before their set-up
+        if (rc == PAAM_OK) rc = paam_search_ordered_from(ctx, b, o, ranks, K, nmax, order, Kr, first_ok, s);
+    } else if (rc == PAAM_OK && n_open > 0) { // nothing left to visit
+        if (cudaMemsetAsync(first_ok, 0xff, 4 * (size_t)n, s) != cudaSuccess) rc = PAAM_E_CUDA;
+    }
+    if (rc == PAAM_OK) {
+        combine_kernel<<<grid_for(n, 256, ctx->n_sm), 256, 0, s>>>(fa, n, first_ok);
+        if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
+        paam_count_launch();
+    }
+    cudaFreeAsync(blk, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == PAAM_OK) rc = PAAM_E_CUDA;
     return rc;
 }
 

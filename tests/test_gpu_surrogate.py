@@ -364,6 +364,43 @@ def test_infer_ranks_by_score_and_guided_search_is_exact():
     b.free()
 
 
+@pytest.mark.parametrize("which", ["trained", "untrained"])
+def test_exact_guided_search_gives_the_exhaustive_verdicts(which):
+    """paam_surrogate_search (pinned seeds, then the network's order, each system
+    stopping at its first admitted candidate) admits exactly the systems the
+    exhaustive search admits, each with a candidate the oracle admits, and a
+    system admitted by a pinned seed with its lowest such slot; the network's
+    quality changes only the time (an untrained network gives the same verdicts).
+    Mixed sizes (cfg3, up to 64 chains) and a batch of 16-chain systems."""
+    import torch
+
+    import paper_2404_06452_gb300 as pkg
+
+    if which == "trained":
+        m, btrain, *_ = _trained_model()
+        btrain.free()
+    else:
+        m = pkg.Model.create(ctx(), seed=3)
+    for sy, K, pinned in ((g.generate("cfg4s", n_sys=600), 64, 2), (g.generate("cfg3", n_sys=300, seed=4), 16, 1)):
+        ranks = g.candidate_ranks(sy, K, 11, nmax=int(sy.chains_per_system().max()))
+        b = pkg.paam_rta_load_systems(ctx(), sy)
+        r = torch.from_numpy(ranks).cuda()
+        first = torch.full((sy.n_sys,), -7, dtype=torch.int32, device="cuda")
+        pkg.paam_surrogate_search(ctx(), m, b, pkg.analysis_opts(), r, first, n_pinned=pinned)
+        torch.cuda.synchronize()
+        f = first.cpu().numpy()
+        ex = oracle.search(sy, ranks, threads=8)
+        has = ex["first_ok"] >= 0
+        assert np.array_equal(f >= 0, has)
+        assert np.all(f >= -1) and np.all(f < K)
+        idx = np.nonzero(f >= 0)[0]
+        assert np.all(ex["cand_ok"][idx, f[idx]] == 1)  # every admitted candidate is admissible
+        seeded = ex["cand_ok"][:, :pinned].any(axis=1)
+        assert np.array_equal(f[seeded], ex["cand_ok"][seeded, :pinned].argmax(axis=1))
+        b.free()
+    m.free()
+
+
 def test_checkpoint_roundtrip(tmp_path):
     import torch
 
