@@ -179,9 +179,9 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
 TRAFFIC_PER_SYSTEM = {26: (951_578_112 + 72_256_512) / 500_000, 28: (901_536_768 + 57_635_584) / 500_000}
 # the same for the other workloads, keyed by (workload, launch configuration): the
 # uneven workload's step is the first pass, the 32-lane pass over the deferral list
-# and the 64-chain register-table kernel for the systems above 32 chains
-TRAFFIC_OTHER = {("cfg3", 26): (868_313_600 + 40_677_888 + 346_370_304 + 16_324_864 + 108_700_672 + 897_792) / 500_000,
-                 ("cfg3", 28): (850_211_072 + 32_089_600 + 346_431_744 + 16_359_168 + 108_639_488 + 906_240) / 500_000}
+# and the 64-chain lazy kernel for the systems above 32 chains
+TRAFFIC_OTHER = {("cfg3", 26): (869_097_984 + 40_553_216 + 346_428_672 + 16_412_416 + 109_226_496 + 1_887_744) / 500_000,
+                 ("cfg3", 28): (850_265_600 + 32_014_592 + 346_421_248 + 16_240_128 + 109_251_840 + 1_920_000) / 500_000}
 
 
 def traffic_per_system(workload: str, cfg_index: int):
