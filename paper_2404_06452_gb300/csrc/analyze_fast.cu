@@ -610,7 +610,7 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
         return rc;
     }
     if (b->acc) { // several accelerators: per-accelerator register tables, the int64 kernel for the rest
-        int rc = paam_launch_reg_acc(b, pm, R, status, verdict, items, stream);
+        int rc = paam_launch_lazy_acc(b, pm, R, status, verdict, items, stream);
         if (rc == PAAM_OK) rc = paam_launch_wide(b, pw, R, status, verdict, b->list_wide, b->counts + 1, items, stream);
         if (n_kernels) *n_kernels = 2;
         return rc;

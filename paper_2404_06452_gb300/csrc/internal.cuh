@@ -315,11 +315,13 @@ struct ValidateRange {
 int paam_launch_validate_range(const paam_batch *b, const int32_t *acc, const ValidateRange &r, int sentinels,
                                int32_t *err, unsigned long long *stats, cudaStream_t stream);
 
-// Register-table kernel for batches with several accelerators
-// (analyze_reg_acc.cu), systems of up to 16 chains inside the 32-bit bound;
-// the rest go to b->list_wide (count b->counts[1]) for the int64 kernel.
-int paam_launch_reg_acc(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
-                        int64_t max_items, cudaStream_t stream);
+// The lazy register-table analysis for batches with several accelerators
+// (analyze_lazy_acc.cu): 16 lanes per system, one chain per lane, instantiated
+// for the batch's accelerator count (2-4); systems over 16 chains, outside the
+// 32-bit bound or not narrow go to b->list_wide (count b->counts[1]) for the
+// int64 kernel.
+int paam_launch_lazy_acc(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                         int64_t max_items, cudaStream_t stream);
 
 // The safe blocking reading (blocking_mode 1) in the register-table kernel
 // (analyze_reg.cu): systems of up to 16 chains inside the 32-bit bound; the

@@ -1,5 +1,5 @@
 // reg_common.cuh -- helpers of the register-table analysis kernels
-// (analyze_reg.cu, analyze_reg_acc.cu): group masks and reductions, the
+// (analyze_reg.cu and the lazy kernels): group masks and reductions, the
 // 32-bit bounds, broadcasts of per-lane slots, Lemma 1's arrival count by
 // multiply-shift division.
 #pragma once
