@@ -62,7 +62,59 @@ __device__ __forceinline__ uint32_t capped_term(uint32_t t, uint32_t tm2, uint32
     return v < kNarrow - 1 ? (uint32_t)v : kNarrow - 1;
 }
 
-template <int LG>
+// The aggregates of chain g (Sec. II-C), which do not depend on the priorities:
+// sums and extremes in 32 bits over values capped at 2^30 (a capped value takes
+// the chain's sum to the 32-bit bound, and its system to the int64 kernel).
+struct ChainAgg {
+    uint32_t tm2, mg, lg, D, E, S, Emax, M, Amin, dl;
+    int64_t q0;
+    unsigned fit;
+};
+
+__device__ __forceinline__ void chain_aggregates(const BatchDev &b, int64_t g, uint64_t kappa2, uint64_t eps,
+                                                 ChainAgg &a)
+{
+    const int64_t T = b.T[g], D = b.D[g];
+    const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
+    const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
+    const int64_t *Ep = b.E + cb0;
+    const int ncb = (int)(cb1 - cb0);
+    uint32_t E = 0, Emax = 0, S = 0, M = 0, Amin = 0xFFFFFFFFu;
+#pragma unroll 4
+    for (int i = 0; i < ncb; ++i) {
+        const uint32_t e = (uint64_t)Ep[i] < kFitR ? (uint32_t)Ep[i] : (uint32_t)kFitR;
+        E = umin(E + e, (uint32_t)kFitR);
+        Emax = umax(Emax, e);
+    }
+    const int64_t *Ap = b.A + q0;
+    const int nq = (int)(q1 - q0);
+    const uint32_t k2c = kappa2 < kFitR ? (uint32_t)kappa2 : (uint32_t)kFitR;
+#pragma unroll 4
+    for (int i = 0; i < nq; ++i) {
+        const uint32_t v = ((uint64_t)Ap[i] < kFitR ? (uint32_t)Ap[i] : (uint32_t)kFitR) + k2c; // A* = A + 2 kappa
+        S = umin(S + v, (uint32_t)kFitR);
+        M = umax(M, v);
+        Amin = umin(Amin, v);
+    }
+    const uint64_t dl = (uint64_t)nq;
+    a.fit = ((uint64_t)T < kFitR && (uint64_t)D < kFitR && E < kFitR && S < kFitR && dl < kFitR &&
+             (eps == 0 || dl <= (kFitR - 1) / eps))
+                ? 1u
+                : 0u;
+    a.tm2 = a.mg = a.lg = 0;
+    if (a.fit) rdivisor((uint32_t)T, a.tm2, a.mg, a.lg);
+    a.D = (uint32_t)D;
+    a.E = E;
+    a.S = S;
+    a.Emax = Emax;
+    a.M = M;
+    a.Amin = dl ? (Amin < kFitR ? Amin : 0u) : 0u;
+    a.dl = (uint32_t)dl;
+    a.q0 = q0;
+}
+
+// REC: the aggregates come from p.chain_recs (candidate mode)
+template <int LG, bool REC = false>
 __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t item, LazySmem<LG> &s, int lane,
                             unsigned gm, int64_t *__restrict__ R_out, uint8_t *__restrict__ st_out,
                             uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
@@ -99,8 +151,6 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     const bool val = j < n;
     if (val) {
         const int64_t g = c0 + j;
-        const int64_t T = b.T[g], D = b.D[g];
-        ex = b.exec[g];
         if (rank_row) { // candidate priority order: rank 0 is the highest priority
             const int r = rank_row[j];
             rank_ok = (r >= 0 && r < n) ? 1u : 0u;
@@ -109,46 +159,32 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         } else {
             pr = b.prio[g];
         }
-        co = b.exec_core[x0 + ex];
-        if (xprio) ep = xprio[x0 + ex];
-        sp = b.spin[g] != 0;
-        const int64_t cb0 = b.chain_cb_off[g], cb1 = b.chain_cb_off[g + 1];
-        const int64_t q0 = b.cb_seg_off[cb0], q1 = b.cb_seg_off[cb1];
-        // sums and extremes in 32 bits over values capped at 2^30 (a capped value
-        // takes its chain's sum to the 32-bit bound, and the system to the int64 kernel)
-        const int64_t *Ep = b.E + cb0;
-        const int ncb = (int)(cb1 - cb0);
-        uint32_t E = 0, Emax = 0, S = 0, M = 0, Amin = 0xFFFFFFFFu;
-#pragma unroll 4
-        for (int i = 0; i < ncb; ++i) {
-            const uint32_t e = (uint64_t)Ep[i] < kFitR ? (uint32_t)Ep[i] : (uint32_t)kFitR;
-            E = umin(E + e, (uint32_t)kFitR);
-            Emax = umax(Emax, e);
+        if constexpr (REC) {
+            const uint4 *r = p.chain_recs + g * 4;
+            const uint4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
+            tm2 = r0.x, mg = r0.y, lg = r0.z, Dv = r0.w;
+            Ev = r1.x, Sv = r1.y, Emx = r1.z, Mv = r1.w;
+            Amn = r2.x, dlv = r2.y, seg0 = r2.z, fit = r2.w & 1u, sp = (r2.w >> 1) & 1u;
+            ex = (int32_t)r3.x, co = (int32_t)r3.y;
+            if (xprio) ep = xprio[x0 + ex];
+        } else {
+            ex = b.exec[g];
+            co = b.exec_core[x0 + ex];
+            if (xprio) ep = xprio[x0 + ex];
+            sp = b.spin[g] != 0;
+            ChainAgg a;
+            chain_aggregates(b, g, kappa2, eps, a);
+            fit = a.fit;
+            tm2 = a.tm2, mg = a.mg, lg = a.lg;
+            Dv = a.D;
+            Ev = a.E;
+            Sv = a.S;
+            Emx = a.Emax;
+            Mv = a.M;
+            Amn = a.Amin;
+            dlv = a.dl;
+            seg0 = (uint32_t)(a.q0 - seg_base);
         }
-        const int64_t *Ap = b.A + q0;
-        const int nq = (int)(q1 - q0);
-        const uint32_t k2c = kappa2 < kFitR ? (uint32_t)kappa2 : (uint32_t)kFitR;
-#pragma unroll 4
-        for (int i = 0; i < nq; ++i) {
-            const uint32_t a = ((uint64_t)Ap[i] < kFitR ? (uint32_t)Ap[i] : (uint32_t)kFitR) + k2c; // A* = A + 2 kappa
-            S = umin(S + a, (uint32_t)kFitR);
-            M = umax(M, a);
-            Amin = umin(Amin, a);
-        }
-        const uint64_t dl = (uint64_t)nq;
-        fit = ((uint64_t)T < kFitR && (uint64_t)D < kFitR && E < kFitR && S < kFitR && dl < kFitR &&
-               (eps == 0 || dl <= (kFitR - 1) / eps))
-                  ? 1u
-                  : 0u;
-        if (fit) rdivisor((uint32_t)T, tm2, mg, lg);
-        Dv = (uint32_t)D;
-        Ev = E;
-        Sv = S;
-        Emx = Emax;
-        Mv = M;
-        Amn = dl ? (Amin < kFitR ? Amin : 0u) : 0u;
-        dlv = (uint32_t)dl;
-        seg0 = (uint32_t)(q0 - seg_base);
     }
     if (lane == 0) {
         s.c0 = c0;
@@ -446,7 +482,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
 
 // BLOCKS resident blocks of 256 threads per SM: the register budget per thread.
 // Items are all of the launch (list == nullptr) or list[0 .. *count).
-template <int LG, int BLOCKS>
+template <int LG, int BLOCKS, bool REC>
 __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, AnalysisParams p, int64_t *R,
                                                                    uint8_t *st, uint8_t *verdict, const int32_t *list,
                                                                    const int32_t *count, int32_t *big_list,
@@ -468,11 +504,50 @@ __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, A
         if (!list && p.K == 0 && lane == 0 && i % kPrefetchSlice == 0)
             prefetch_systems(b, p.sys_order, i + kBinWindow, kPrefetchSlice);
         const int64_t item = list ? (int64_t)list[i] : i;
-        lazy_system<LG>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
+        lazy_system<LG, REC>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
     });
 }
 
+// one warp per system, one lane per chain: the records of chain_recs
+__global__ void __launch_bounds__(256) chain_records_kernel(BatchDev b, uint64_t kappa2, uint64_t eps, uint4 *recs)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t sys = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sys < b.n_sys; sys += nw) {
+        const int64_t c0 = b.sys_chain_off[sys];
+        const int n = (int)(b.sys_chain_off[sys + 1] - c0);
+        if (n <= 0) continue;
+        const int64_t seg_base = b.cb_seg_off[b.chain_cb_off[c0]];
+        const int64_t x0 = b.sys_exec_off[sys];
+        for (int j = lane; j < n; j += 32) {
+            const int64_t g = c0 + j;
+            ChainAgg a;
+            chain_aggregates(b, g, kappa2, eps, a);
+            const int32_t ex = b.exec[g];
+            const int32_t co = b.exec_core[x0 + ex];
+            const unsigned sp = b.spin[g] != 0 ? 1u : 0u;
+            uint4 *r = recs + g * 4;
+            r[0] = make_uint4(a.tm2, a.mg, a.lg, a.D);
+            r[1] = make_uint4(a.E, a.S, a.Emax, a.M);
+            r[2] = make_uint4(a.Amin, a.dl, (uint32_t)(a.q0 - seg_base), a.fit | (sp << 1));
+            r[3] = make_uint4((uint32_t)ex, (uint32_t)co, 0u, 0u);
+        }
+    }
+}
+
 } // namespace
+
+int paam_launch_chain_records(const paam_batch *bt, const AnalysisParams &p, uint4 *recs, cudaStream_t stream)
+{
+    if (bt->n_sys <= 0) return PAAM_OK;
+    int64_t blocks = (bt->n_sys + 7) / 8;
+    if (blocks > 16 * (int64_t)bt->ctx->n_sm) blocks = 16 * (int64_t)bt->ctx->n_sm;
+    chain_records_kernel<<<(unsigned)blocks, 256, 0, stream>>>(batch_dev(bt), 2 * (uint64_t)p.kappa,
+                                                               (uint64_t)p.eps, recs);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    paam_count_launch();
+    return PAAM_OK;
+}
 
 template <int LG, int BLOCKS>
 int launch_lazy_pass(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
@@ -481,7 +556,7 @@ int launch_lazy_pass(const paam_batch *bt, const AnalysisParams &p, int64_t *R, 
     if (threads % 32 != 0 || threads > 256) return PAAM_E_INVAL;
     const int groups = threads / LG;
     const size_t smem = sizeof(LazySmem<LG>) * groups;
-    auto kern = analyze_lazy_kernel<LG, BLOCKS>;
+    auto kern = p.chain_recs ? analyze_lazy_kernel<LG, BLOCKS, true> : analyze_lazy_kernel<LG, BLOCKS, false>;
     PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));

@@ -66,6 +66,10 @@ struct AnalysisParams {
     // Register-table kernels (analyze_reg.cu): skip systems with fewer chains (the
     // 64-chain pass after the 32-lane lazy pass over the same deferral list)
     int32_t min_chains;
+    // Candidate mode, optional (the 16- and 32-lane lazy kernels): each chain's
+    // aggregates computed once for all candidates (paam_launch_chain_records),
+    // four uint4 per chain
+    const uint4 *chain_recs;
 };
 
 // Item i of a launch: system index and candidate index (0 outside candidate mode).
@@ -268,6 +272,10 @@ int launch_lazy32(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uin
 // that are not narrow (a deadline at or above kLazyDeferWideD) go to b->list_wide.
 int launch_lazy64(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                   const int32_t *list, const int32_t *count, int64_t max_items, int threads, cudaStream_t stream);
+// The per-chain records of AnalysisParams::chain_recs for every chain of b
+// (analyze_lazy.cu): the aggregates the lazy kernels compute before the
+// relations, which do not depend on the priorities.
+int paam_launch_chain_records(const paam_batch *b, const AnalysisParams &p, uint4 *recs, cudaStream_t stream);
 // impl_big value of a launch configuration whose deferral list goes to the 32-lane
 // lazy kernel and then, for systems over 32 chains, to the 64-chain lazy kernel
 constexpr int kImplBigLazy32 = 9;

@@ -14,6 +14,10 @@
 
 namespace {
 
+// chains up to which the search keeps each chain's aggregates for all its
+// candidates (64 bytes per chain)
+constexpr int64_t kRecChains = (int64_t)1 << 22;
+
 __global__ void search_init(int32_t *first_ok, int64_t n_sys, int32_t K, uint8_t *cand_ok, int64_t n_cand)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -73,10 +77,14 @@ int search_ordered_impl(paam_ctx *ctx, const paam_batch *b, const paam_analysis_
     cudaStream_t stream = (cudaStream_t)stream_;
     const int64_t items = b->n_sys * (int64_t)K;
 
-    // per-call scratch: the two deferral lists over items, their counts, an error word
+    // per-call scratch: the two deferral lists over items, their counts, an error word,
+    // and (batches of up to kRecChains chains) each chain's aggregates, shared by
+    // all its candidates
     void *tmp = nullptr;
     const size_t list_bytes = 4 * (size_t)items;
-    if (cudaMallocAsync(&tmp, 2 * list_bytes + 64, stream) != cudaSuccess) {
+    const size_t rec_bytes = b->n_chain <= kRecChains ? 64 * (size_t)b->n_chain : 0;
+    const size_t rec_off = (2 * list_bytes + 64 + 255) & ~(size_t)255; // 16-byte aligned records
+    if (cudaMallocAsync(&tmp, rec_off + rec_bytes, stream) != cudaSuccess) {
         cudaGetLastError();
         return PAAM_E_NOMEM;
     }
@@ -123,6 +131,11 @@ int search_ordered_impl(paam_ctx *ctx, const paam_batch *b, const paam_analysis_
     p.first_ok = first_ok;
     p.err = err;
     int nk = 0;
+    if (rec_bytes && rc == PAAM_OK) {
+        p.chain_recs = (const uint4 *)((char *)tmp + rec_off);
+        rc = paam_launch_chain_records(b, p, (uint4 *)p.chain_recs, stream);
+        ++nk;
+    }
     if (rc == PAAM_OK) rc = paam_enqueue_analysis(&bs, p, kLaunchCfgs[b->cfg_index], nullptr, nullptr, nullptr,
                                                   stream, &nk);
     if (rc == PAAM_OK) {
