@@ -148,6 +148,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     bool sp = false;
     unsigned fit = 1, rank_ok = 1;
     Mask rbit = 0;
+    uint32_t rsx = 0, rco = 0; // same-executor and same-core chains, from the records
     const bool val = j < n;
     if (val) {
         const int64_t g = c0 + j;
@@ -166,6 +167,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             Ev = r1.x, Sv = r1.y, Emx = r1.z, Mv = r1.w;
             Amn = r2.x, dlv = r2.y, seg0 = r2.z, fit = r2.w & 1u, sp = (r2.w >> 1) & 1u;
             ex = (int32_t)r3.x, co = (int32_t)r3.y;
+            rsx = r3.z, rco = r3.w;
             if (xprio) ep = xprio[x0 + ex];
         } else {
             ex = b.exec[g];
@@ -229,9 +231,18 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     const bool counted = L > kIterCap;
 
     // ---- relations (Lemma 4, Theorem 1, Eq. 3), analysis order ---------------
-    const unsigned xm = __match_any_sync(gm, ex); // lanes of the same executor (unique keys past n)
+    // lanes of the same executor (unique keys past n) and of the same core: from the
+    // chain records (every lane of the group takes the same path), or matched here
+    unsigned xm;
+    Mask corem;
+    if constexpr (REC) {
+        xm = (val ? rsx : jbit) << sh;
+        corem = val ? rco : jbit;
+    } else {
+        xm = __match_any_sync(gm, ex);
+        corem = __match_any_sync(gm, co) >> sh;
+    }
     const Mask samex = xm >> sh;
-    const Mask corem = __match_any_sync(gm, co) >> sh;
     if (!xprio) ep = __reduce_max_sync(xm, pr); // criticality-as-priority: highest chain priority on the executor
     const bool one_bucket = p.n_buckets == 1;
     const Mask eqx = __match_any_sync(gm, ep) >> sh; // equal executor priority
@@ -526,11 +537,19 @@ __global__ void __launch_bounds__(256) chain_records_kernel(BatchDev b, uint64_t
             const int32_t ex = b.exec[g];
             const int32_t co = b.exec_core[x0 + ex];
             const unsigned sp = b.spin[g] != 0 ? 1u : 0u;
+            // the chains of the same executor and of the same core (systems of up to 32
+            // chains, the ones the lazy kernels read records for)
+            uint32_t sx = 0, sc = 0;
+            if (n <= 32) {
+                const unsigned act = n == 32 ? 0xffffffffu : (1u << n) - 1u; // lanes j < n
+                sx = __match_any_sync(act, ex);
+                sc = __match_any_sync(act, co);
+            }
             uint4 *r = recs + g * 4;
             r[0] = make_uint4(a.tm2, a.mg, a.lg, a.D);
             r[1] = make_uint4(a.E, a.S, a.Emax, a.M);
             r[2] = make_uint4(a.Amin, a.dl, (uint32_t)(a.q0 - seg_base), a.fit | (sp << 1));
-            r[3] = make_uint4((uint32_t)ex, (uint32_t)co, 0u, 0u);
+            r[3] = make_uint4((uint32_t)ex, (uint32_t)co, sx, sc);
         }
     }
 }
