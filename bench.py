@@ -149,6 +149,11 @@ def peaks() -> dict:
 
 
 # main kernel of each launch configuration (the table in csrc/analyze_fast.cu)
+# the passes over the first pass's deferral list, launched only for a batch with systems
+# above 16 chains (or deferred for their deadlines)
+_REG_BIG = "; analyze_reg_kernel<32, 2> for the deferred systems"
+_LAZY_BIG = ("; analyze_lazy_kernel<32, 6> for the deferred systems of up to 32 chains and "
+             "analyze_lazy64_kernel<3> for those above")
 CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>", 2: "analyze_fast_kernel<16, 32>",
                  3: "analyze_reg1_kernel<16>", 4: "analyze_reg_kernel<4, 4>", 5: "analyze_reg_kernel<16, 2>",
                  6: "analyze_reg1_kernel<32>", 7: "analyze_reg_kernel<8, 2>", 8: "analyze_fast_kernel<4, 16>",
@@ -158,13 +163,14 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
                  16: "analyze_reg1_kernel<32> (work queue)", 17: "analyze_reg1_kernel<16> (work queue, size-binned)",
                  18: "analyze_reg1_kernel<32> (work queue, size-binned)",
                  19: "analyze_reg_kernel<8, 2> (work queue, size-binned)",
-                 20: "analyze_lazy_kernel<4>", 21: "analyze_lazy_kernel<4> (work queue)",
-                 22: "analyze_lazy_kernel<4> (work queue, size-binned)",
-                 23: "analyze_lazy_kernel<5> (work queue, size-binned)",
-                 24: "analyze_lazy_kernel<6> (work queue, size-binned)", 25: "analyze_lazy_kernel<5> (work queue)",
-                 26: "analyze_lazy_kernel<16, 6> + analyze_lazy_kernel<32, 6> (work queue, size-binned)",
-                 27: "analyze_lazy_kernel<16, 4> + analyze_lazy_kernel<32, 6> (work queue, size-binned)",
-                 28: "analyze_lazy_kernel<16, 5> + analyze_lazy_kernel<32, 6> (work queue, size-binned)"}
+                 20: "analyze_lazy_kernel<16, 4>" + _REG_BIG, 21: "analyze_lazy_kernel<16, 4> (work queue)" + _REG_BIG,
+                 22: "analyze_lazy_kernel<16, 4> (work queue, size-binned)" + _REG_BIG,
+                 23: "analyze_lazy_kernel<16, 5> (work queue, size-binned)" + _REG_BIG,
+                 24: "analyze_lazy_kernel<16, 6> (work queue, size-binned)" + _REG_BIG,
+                 25: "analyze_lazy_kernel<16, 5> (work queue)" + _REG_BIG,
+                 26: "analyze_lazy_kernel<16, 6> (work queue, size-binned)" + _LAZY_BIG,
+                 27: "analyze_lazy_kernel<16, 4> (work queue, size-binned)" + _LAZY_BIG,
+                 28: "analyze_lazy_kernel<16, 5> (work queue, size-binned)" + _LAZY_BIG}
 
 
 # DRAM read + write per system of the analysis kernels, from ncu captures
