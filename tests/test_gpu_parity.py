@@ -165,14 +165,19 @@ def test_invalid_inputs_rejected():
 @pytest.mark.parametrize("p", PARAMS[:2])
 def test_safe_blocking_mode(p):
     """blocking_mode=1 (the safe reading of Lemma 4) on every shape: uneven
-    sizes up to 64 chains, spinning chains, overheads; bit-exact with the
-    oracle, and the search in the same mode."""
+    sizes up to 64 chains, spinning chains, overheads, callbacks with two
+    segments and systems of 40 to 192 segments (a quarter of them above 128,
+    the most the register-table kernel bounds with one segment per lane; it
+    takes those segment by segment); bit-exact with the oracle, and the search
+    in the same mode."""
     import torch
 
     import paper_2404_06452_gb300 as pkg
 
     for sy in (g.generate("cfg1", p_spin=0.5), g.generate("cfg3", n_sys=3000, seed=31),
-               g.generate("cfg2", n_sys=3000, p_spin=0.3, exec_prio_mode=1)):
+               g.generate("cfg2", n_sys=3000, p_spin=0.3, exec_prio_mode=1),
+               g.generate("cfg2", n_sys=3000, seed=77, n_min=8, n_max=16, cb_min=3, cb_max=12, seg_per_cb=2,
+                          p_acc=0.6, util_mode=0, util_lo=0.1, util_hi=0.5, a_min=10_000, a_max=200_000)):
         assert_same(gpu_analyze(sy, blocking_mode=1, **p), oracle.analyze(sy, blocking_mode=1, threads=8, **p))
     sy = g.generate("cfg4s", n_sys=200)
     ranks = g.candidate_ranks(sy, 24, 3)
