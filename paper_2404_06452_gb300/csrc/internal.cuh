@@ -30,7 +30,7 @@ struct AnalysisParams {
     int64_t kappa;
     // Candidate mode (priority-assignment search): work item i is system
     // i % n_sys under candidate i / n_sys (candidates in order, so that early
-    // exit prunes well); its chain priorities come from the rank row
+    // exit prunes well; sys_major below changes that); its chain priorities come from the rank row
     // ranks[(system * K + candidate) * nmax ..] (0 = highest), executor priorities derived
     // (criticality-as-priority).  A candidate stops at its first chain that is
     // not schedulable; results go to cand_ok[i] (optional) and to a running
@@ -44,6 +44,10 @@ struct AnalysisParams {
     int32_t Kc;           // candidates per system in ranks / cand_ok (K = slots visited)
     const int32_t *order; // optional [n_sys][K]: candidate visited in slot j (else slot j = candidate j)
     int32_t early;
+    // sys_major (the exhaustive search, no early exit): item i is instead candidate
+    // i % K of system i / K, so that a system's candidates run one after another and
+    // share its chain records in L1
+    int32_t sys_major;
     uint8_t *cand_ok;
     int32_t *first_ok;
     int32_t *err;
@@ -76,8 +80,14 @@ struct AnalysisParams {
 __device__ __forceinline__ void item_of(const AnalysisParams &p, int64_t i, int64_t &sys, int32_t &cand)
 {
     if (p.K > 0) {
-        cand = (int32_t)(i / p.n_sys);
-        sys = i - (int64_t)cand * p.n_sys;
+        if (p.sys_major) { // a 32-bit division where the index fits
+            const int64_t q = (uint64_t)i <= 0xffffffffu ? (int64_t)((uint32_t)i / (uint32_t)p.K) : i / p.K;
+            sys = q;
+            cand = (int32_t)(i - q * p.K);
+        } else {
+            cand = (int32_t)(i / p.n_sys);
+            sys = i - (int64_t)cand * p.n_sys;
+        }
     } else {
         sys = i;
         cand = 0;

@@ -127,6 +127,7 @@ int search_ordered_impl(paam_ctx *ctx, const paam_batch *b, const paam_analysis_
     p.n_sys = b->n_sys;
     p.nmax = nmax;
     p.early = stop_at_first ? 1 : 0;
+    p.sys_major = (!stop_at_first && !order) ? 1 : 0;
     p.cand_ok = cand_ok;
     p.first_ok = first_ok;
     p.err = err;
