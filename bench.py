@@ -180,10 +180,10 @@ CONFIG_KERNEL = {0: "analyze_reg_kernel<8, 2>", 1: "analyze_fast_kernel<8, 16>",
 # instruction-issue side, against the issue peak of 152 SMs x 4 schedulers x 1
 # per clock.  Valid only while the kernels and the order they visit are
 # unchanged since the capture; a configuration without an entry reports null.
-# 26: analyze_lazy_kernel<16, 6> (1,023.8 MB), 28: analyze_lazy_kernel<16, 5> (959.0 MB);
+# 26: analyze_lazy_kernel<16, 6> (1,022.1 MB), 28: analyze_lazy_kernel<16, 5> (959.0 MB);
 # neither defers a system of this workload, so configurations 24 and 23 run the
 # same kernels in the same order on it and take the same entries.
-_T26, _T28 = (951_578_112 + 72_256_512) / 500_000, (901_364_736 + 57_655_808) / 500_000
+_T26, _T28 = (949_534_464 + 72_603_904) / 500_000, (901_364_736 + 57_655_808) / 500_000
 TRAFFIC_PER_SYSTEM = {26: _T26, 24: _T26, 28: _T28, 23: _T28}
 # the same for the other workloads, keyed by (workload, launch configuration): the
 # uneven workload's step is the first pass, the 32-lane pass over the deferral list
@@ -198,7 +198,7 @@ def traffic_per_system(workload: str, cfg_index: int):
     return TRAFFIC_OTHER.get((workload, cfg_index))
 
 
-WARP_INST_PER_SYSTEM = {26: 550_822_977 / 500_000, 24: 550_822_977 / 500_000, 28: 531_338_213 / 500_000,
+WARP_INST_PER_SYSTEM = {26: 551_079_382 / 500_000, 24: 551_079_382 / 500_000, 28: 531_338_213 / 500_000,
                         23: 531_338_213 / 500_000}
 ISSUE_PEAK = 152 * 4 * 2.07e9  # warp-instructions / s at the 2070 MHz maximum SM clock
 
