@@ -20,10 +20,11 @@
 //    the eager order.
 //
 // Systems with more than 16 chains, or that fit the 32-bit bound but not the
-// narrow one, go to b.list_big (the 64-chain register-table kernel); systems
-// outside the 32-bit bound to b.list_wide (the int64 kernel).  One
-// accelerator, Lemma 4 as printed (blocking_mode 0), analysis and candidate
-// mode; the other modes keep their kernels.
+// narrow one, go to b.list_big (the 32-lane pass of this kernel over that list,
+// then analyze_lazy64.cu for those above 32 chains); systems outside the 32-bit
+// bound to b.list_wide (the int64 kernel).  One accelerator, Lemma 4 as printed
+// (blocking_mode 0): analysis, candidate and target mode; the other modes keep
+// their kernels.
 #include "reg_common.cuh"
 
 namespace {
@@ -113,8 +114,11 @@ __device__ __forceinline__ void chain_aggregates(const BatchDev &b, int64_t g, u
     a.q0 = q0;
 }
 
-// REC: the aggregates come from p.chain_recs (candidate mode)
-template <int LG, bool REC = false>
+// REC: the aggregates come from p.chain_recs (candidate mode).  TGT (target mode,
+// the Audsley-style seed; see AnalysisParams.target): candidate (system, c) is
+// decided by chain p.target[system * Kc + c] alone (-1: no trial in the slot), the
+// chains are analysed up to that one's step and no failure ends a candidate early.
+template <int LG, bool REC = false, bool TGT = false>
 __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t item, LazySmem<LG> &s, int lane,
                             unsigned gm, int64_t *__restrict__ R_out, uint8_t *__restrict__ st_out,
                             uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
@@ -130,6 +134,11 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     }
     const int64_t c0 = b.sys_chain_off[sys];
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
+    int tgt = -1;
+    if constexpr (TGT) {
+        tgt = p.target[sys * p.Kc + cand_of(p, sys, cand)];
+        if (tgt < 0 || tgt >= n) return; // no trial in this slot
+    }
     if (n > LG) { // the 64-chain kernel's; the first pass appends it to its list
         if (LG == 16 && lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
         return;
@@ -359,10 +368,12 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     const uint32_t k2 = (uint32_t)kappa2;
     auto chains = [&](auto counted_tag) {
     constexpr bool CNT = decltype(counted_tag)::value;
-    for (int step = 0; step < n; ++step) {
+    // target mode: up to the target chain's step
+    const int nsteps = TGT ? __shfl_sync(gm, pos, tgt, LG) + 1 : n;
+    for (int step = 0; step < nsteps; ++step) {
         const uint4 rl = s.rel[step];
         if (rl.w & ~sched) { // a needed H*_h is not available (the chain is DEP)
-            if (rank_row) break; // a candidate fails at its first unschedulable chain
+            if (rank_row && !TGT) break; // a candidate fails at its first unschedulable chain
             continue;
         }
         const uint4 rc = s.rec[step], sg = s.seg[step];
@@ -444,7 +455,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         }
         if (capped) { // no bound (PAAM_ST_ITERCAP)
             if (j == c) Rv = kCapR;
-            if (rank_row) break;
+            if (rank_row && !TGT) break;
             continue;
         }
         if (ok) {
@@ -456,7 +467,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             }
         } else {
             if (ev > kIterCap && j == c) Rv = kCapR; // the recurrence was cut short (PAAM_ST_ITERCAP)
-            if (rank_row) break;
+            if (rank_row && !TGT) break;
         }
     }
     };
@@ -469,6 +480,11 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     {
     const int64_t c0 = s.c0, sys = s.sys;
     const int32_t cand = s.cand;
+    if (TGT) { // the target chain's verdict; first_ok is not touched
+        if (lane == 0) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = ((sched >> tgt) & 1) ? 1 : 0;
+        __syncwarp(gm);
+        return;
+    }
     if (rank_row) {
         if (lane == 0) {
             const bool ok = sched == all;
@@ -493,7 +509,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
 
 // BLOCKS resident blocks of 256 threads per SM: the register budget per thread.
 // Items are all of the launch (list == nullptr) or list[0 .. *count).
-template <int LG, int BLOCKS, bool REC>
+template <int LG, int BLOCKS, bool REC, bool TGT = false>
 __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, AnalysisParams p, int64_t *R,
                                                                    uint8_t *st, uint8_t *verdict, const int32_t *list,
                                                                    const int32_t *count, int32_t *big_list,
@@ -515,7 +531,8 @@ __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, A
         if (!list && p.K == 0 && lane == 0 && i % kPrefetchSlice == 0)
             prefetch_systems(b, p.sys_order, i + kBinWindow, kPrefetchSlice);
         const int64_t item = list ? (int64_t)list[i] : i;
-        lazy_system<LG, REC>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
+        lazy_system<LG, REC, TGT>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list,
+                                  wide_count);
     });
 }
 
@@ -586,6 +603,28 @@ int launch_lazy_pass(const paam_batch *bt, const AnalysisParams &p, int64_t *R, 
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, list, count, bt->list_big,
                                                       bt->counts, bt->list_wide, bt->counts + 1);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    return PAAM_OK;
+}
+
+int paam_launch_lazy_target(const paam_batch *bt, const AnalysisParams &p, int32_t *list, int32_t *count,
+                            int64_t max_items, cudaStream_t stream)
+{
+    constexpr int LG = 16, threads = 256;
+    const int groups = threads / LG;
+    const size_t smem = sizeof(LazySmem<LG>) * groups;
+    auto kern = p.chain_recs ? analyze_lazy_kernel<LG, 5, true, true> : analyze_lazy_kernel<LG, 5, false, true>;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (max_items + groups - 1) / groups;
+    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    // every deferred trial (over 16 chains, not narrow, outside the 32-bit bound) to list
+    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                      list, count, list, count);
     PAAM_CUDA_TRY(cudaGetLastError());
     return PAAM_OK;
 }

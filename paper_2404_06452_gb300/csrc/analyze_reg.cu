@@ -54,15 +54,12 @@ constexpr uint64_t kSafeTermCap = 1ull << 40;
 // at or above it: every deadline is below it, so B + E > D either way
 constexpr uint32_t kHoldInf = (uint32_t)kFitR;
 
-// TARGET (a separate instantiation, used by the Audsley-style seed): the
-// candidate's verdict is the status of chain p.target[..] alone, the chains
-// are analysed until that one is done, and no candidate stops early.
 // SAFE (a separate instantiation, one chain per lane): the safe reading of
 // Lemma 4 (blocking_mode 1): every segment's Lemma 2 bound is computed, each
 // chain's longest callback hold E_i + sum over its segments of (bound + eps)
 // is kept in sx->hold, and B_c is the longest hold of a lower-priority chain on
 // c's executor.
-template <int G, int CPL, bool TARGET = false, bool SAFE = false>
+template <int G, int CPL, bool SAFE = false>
 __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t item, OwnSmem<G * CPL> &s,
                            SafeExt<G * CPL> *sx, int lane, unsigned gm, int64_t *__restrict__ R_out,
                            uint8_t *__restrict__ st_out,
@@ -82,11 +79,6 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     const int64_t c0 = b.sys_chain_off[sys];
     const int n = (int)(b.sys_chain_off[sys + 1] - c0);
     if (n < p.min_chains) return; // an earlier pass over the same list took it
-    int tgt = -1;
-    if constexpr (TARGET) {
-        tgt = p.target[sys * p.Kc + cand_of(p, sys, cand)];
-        if (tgt < 0 || tgt >= n) return; // no trial in this slot
-    }
     if (n > NMAX) {
         if (lane == 0) big_list[atomicAdd(big_count, 1)] = (int32_t)item;
         return;
@@ -530,7 +522,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         const Mask cbit = (Mask)1 << c;
         if ((hp | (hpp & spins)) & ~sched) { // a needed H*_h is not available
             dep |= cbit;
-            if (TARGET ? c == tgt : rank_row != nullptr) break; // a candidate fails at its first unschedulable chain
+            if (rank_row) break; // a candidate fails at its first unschedulable chain
             continue;
         }
         uint32_t ccoef[CPL], acoef[CPL];
@@ -545,7 +537,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
 #pragma unroll
             for (int k = 0; k < CPL; ++k)
                 if (lane + G * k == c) Rv[k] = kCapR;
-            if (TARGET ? c == tgt : rank_row != nullptr) break;
+            if (rank_row) break;
             continue;
         }
         const uint64_t Dc = rc.x, base = rc.y, own = rc.z, deps = rc.w, dl = sg.w;
@@ -628,9 +620,8 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
 #pragma unroll
                 for (int k = 0; k < CPL; ++k)
                     if (lane + G * k == c) Rv[k] = kCapR;
-            if (!TARGET && rank_row) break;
+            if (rank_row) break;
         }
-        if (TARGET && c == tgt) break; // chains after the target cannot change its result
     }
     };
     if (counted)
@@ -639,11 +630,6 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         fixed_points(std::false_type{});
 
     // ---- outputs --------------------------------------------------------------
-    if constexpr (TARGET) {
-        if (lane == 0) p.cand_ok[sys * p.Kc + cand_of(p, sys, cand)] = (uint8_t)((sched >> tgt) & 1);
-        __syncwarp(gm);
-        return;
-    }
     if (rank_row) {
         if (lane == 0) {
             const bool ok = sched == all;
@@ -667,7 +653,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     __syncwarp(gm);
 }
 
-template <int G, int CPL, bool TARGET = false, bool SAFE = false>
+template <int G, int CPL, bool SAFE = false>
 __device__ __forceinline__ void reg_items(const BatchDev &b, const AnalysisParams &p, int64_t *R, uint8_t *st,
                                           uint8_t *verdict, const int32_t *list, const int32_t *count,
                                           int32_t *big_list, int32_t *big_count, int32_t *wide_list,
@@ -685,7 +671,7 @@ __device__ __forceinline__ void reg_items(const BatchDev &b, const AnalysisParam
     const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for_each_item<G>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
         const int64_t item = list ? (int64_t)list[i] : i;
-        reg_system<G, CPL, TARGET, SAFE>(b, p, item, s, sx, lane, gm, R, st, verdict, big_list, big_count,
+        reg_system<G, CPL, SAFE>(b, p, item, s, sx, lane, gm, R, st, verdict, big_list, big_count,
                                          wide_list, wide_count);
     });
 }
@@ -719,18 +705,8 @@ __global__ void __launch_bounds__(256, 4) analyze_reg1_safe_kernel(BatchDev b, A
                                                                    uint8_t *st, uint8_t *verdict, int32_t *wide_list,
                                                                    int32_t *wide_count)
 {
-    reg_items<G, 1, false, true>(b, p, R, st, verdict, nullptr, nullptr, wide_list, wide_count, wide_list,
+    reg_items<G, 1, true>(b, p, R, st, verdict, nullptr, nullptr, wide_list, wide_count, wide_list,
                                  wide_count);
-}
-
-// Target mode for the Audsley-style seed: systems of up to G chains; larger
-// ones and those outside the 32-bit bound go to the wide list
-template <int G>
-__global__ void __launch_bounds__(256, 4) analyze_reg1_target_kernel(BatchDev b, AnalysisParams p,
-                                                                     int32_t *wide_list, int32_t *wide_count)
-{
-    reg_items<G, 1, true>(b, p, nullptr, nullptr, nullptr, nullptr, nullptr, wide_list, wide_count, wide_list,
-                          wide_count);
 }
 
 } // namespace
@@ -775,26 +751,6 @@ template int launch_reg<32, 1>(const paam_batch *, const AnalysisParams &, int64
                                const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
 template int launch_reg<32, 2>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
                                const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
-
-int paam_launch_reg_target(const paam_batch *bt, const AnalysisParams &p, int32_t *list, int32_t *count,
-                           int64_t max_items, cudaStream_t stream)
-{
-    constexpr int G = 16, threads = 256;
-    const int groups = threads / G;
-    const size_t smem = sizeof(OwnSmem<G>) * groups;
-    auto kern = analyze_reg1_target_kernel<G>;
-    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-    if (per_sm < 1) per_sm = 1;
-    int64_t blocks = (max_items + groups - 1) / groups;
-    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, list, count);
-    PAAM_CUDA_TRY(cudaGetLastError());
-    return PAAM_OK;
-}
 
 int paam_launch_reg_safe(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                          int64_t max_items, cudaStream_t stream)

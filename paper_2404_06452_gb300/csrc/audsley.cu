@@ -8,9 +8,10 @@
 // ranks 0 .. l-1 in deadline-monotonic order (D ascending, ties by index).
 // All trials of all systems are analysed at once in target mode, where a
 // trial's verdict is whether c itself is schedulable and the analysis stops
-// once c is done: the register-table kernel for systems of up to 16 chains
-// inside its 32-bit bound (one accelerator, Lemma 4 as printed), the exact
-// int64 kernel for the rest.  The first passing c
+// once c is done: the lazy kernel for systems of up to 16 chains inside its
+// narrow 32-bit bound (one accelerator, Lemma 4 as printed; each chain's
+// aggregates computed once per call for all its trials), the exact int64
+// kernel for the rest.  The first passing c
 // in index order takes level l; if none passes, the unassigned chain with the
 // largest D (ties: highest index) does.  The admission test is not
 // OPA-compatible (bucket ranks, blocking and the DEP rule depend on the whole
@@ -119,7 +120,12 @@ extern "C" int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *b, const 
     const size_t target_bytes = (size_t)chunk * Kc * sizeof(int16_t);
     const size_t ok_bytes = (size_t)chunk * Kc;
     const size_t list_bytes = 4 * (size_t)chunk * Kc; // trials deferred to the int64 kernel
-    if (cudaMallocAsync(&tmp, trial_bytes + target_bytes + ok_bytes + list_bytes + 512, stream) != cudaSuccess) {
+    // the lazy kernel serves one accelerator and Lemma 4 as printed; with up to
+    // kRecChains chains, each chain's aggregates are computed once for all trials
+    const bool lazy = !b->acc && o->blocking_mode == 0;
+    const size_t rec_bytes = lazy && b->n_chain <= kRecChains ? 64 * (size_t)b->n_chain : 0;
+    const size_t rec_off = (trial_bytes + target_bytes + ok_bytes + list_bytes + 512 + 255) & ~(size_t)255;
+    if (cudaMallocAsync(&tmp, rec_off + rec_bytes, stream) != cudaSuccess) {
         cudaGetLastError();
         return PAAM_E_NOMEM;
     }
@@ -129,14 +135,19 @@ extern "C" int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *b, const 
     int32_t *list = (int32_t *)(((uintptr_t)ok + ok_bytes + 15) & ~(uintptr_t)15);
     int32_t *err = (int32_t *)(((uintptr_t)(list + (size_t)chunk * Kc) + 15) & ~(uintptr_t)15);
     int32_t *count = err + 4;
-    // the register-table kernel serves one accelerator and Lemma 4 as printed
-    const bool reg = !b->acc && o->blocking_mode == 0;
+    uint4 *recs = rec_bytes ? (uint4 *)((char *)tmp + rec_off) : nullptr;
 
     int rc = PAAM_OK;
     unsigned launches = 0;
     const int threads = 256;
     const int cap = 8 * ctx->n_sm;
     if (cudaMemsetAsync(err, 0, sizeof(int32_t), stream) != cudaSuccess) rc = PAAM_E_CUDA;
+    if (recs && rc == PAAM_OK) {
+        AnalysisParams pr = {};
+        pr.eps = o->eps_ns;
+        pr.kappa = o->kappa_ns;
+        rc = paam_launch_chain_records(b, pr, recs, stream);
+    }
     {
         const int64_t n = b->n_sys * (int64_t)nmax;
         int blocks = (int)((n + threads - 1) / threads);
@@ -165,6 +176,7 @@ extern "C" int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *b, const 
         p.cand_ok = ok;
         p.err = err;
         p.target = target;
+        p.chain_recs = recs; // indexed by chain: the chunk's offsets are absolute
         const int64_t items = m * (int64_t)Kc;
         int tb = (int)((items + threads - 1) / threads);
         if (tb > cap) tb = cap;
@@ -173,9 +185,9 @@ extern "C" int paam_rta_audsley_order(paam_ctx *ctx, const paam_batch *b, const 
         for (int32_t j = 0; j < b->max_chains && rc == PAAM_OK; ++j) {
             audsley_trials<<<tb, threads, 0, stream>>>(bd, j, Kc, nmax, rank, trial, target);
             if (cudaGetLastError() != cudaSuccess) rc = PAAM_E_CUDA;
-            if (rc == PAAM_OK && reg) {
+            if (rc == PAAM_OK && lazy) {
                 if (cudaMemsetAsync(count, 0, sizeof(int32_t), stream) != cudaSuccess) rc = PAAM_E_CUDA;
-                if (rc == PAAM_OK) rc = paam_launch_reg_target(&sub, p, list, count, items, stream);
+                if (rc == PAAM_OK) rc = paam_launch_lazy_target(&sub, p, list, count, items, stream);
                 if (rc == PAAM_OK)
                     rc = paam_launch_wide(&sub, p, nullptr, nullptr, nullptr, list, count, items, stream);
                 launches += 1;

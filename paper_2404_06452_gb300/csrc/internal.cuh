@@ -61,7 +61,7 @@ struct AnalysisParams {
     // sys_order[k] (systems sorted by chain count), so the groups that share a
     // warp analyse systems of one size and stay converged longer.
     const int32_t *sys_order;
-    // Target mode (exact int64 kernel only; the Audsley-style seed): with
+    // Target mode (the Audsley-style seed; the int64 and lazy kernels): with
     // target set, candidate (system, c) is decided by one chain,
     // target[system * Kc + c] (-1: skip the item): cand_ok receives whether
     // that chain is schedulable, the analysis stops once it is done, and
@@ -347,12 +347,16 @@ int paam_launch_lazy_acc(const paam_batch *bt, const AnalysisParams &p, int64_t 
 int paam_launch_reg_safe(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                          int64_t max_items, cudaStream_t stream);
 
-// Target mode of the register-table kernel (analyze_reg.cu; see
-// AnalysisParams.target): candidates of systems with up to 16 chains inside
-// the 32-bit bound; the others are appended to list (count *count) for the
-// int64 kernel.
-int paam_launch_reg_target(const paam_batch *bt, const AnalysisParams &p, int32_t *list, int32_t *count,
-                           int64_t max_items, cudaStream_t stream);
+// Chains up to which a search (or the Audsley-style seed) keeps each chain's
+// aggregates for all its candidates (paam_launch_chain_records, 64 bytes per chain).
+constexpr int64_t kRecChains = (int64_t)1 << 22;
+
+// Target mode of the lazy kernel (analyze_lazy.cu), reading p.chain_recs when set:
+// candidates of systems with up to 16 chains inside the narrow 32-bit bound, one
+// accelerator, Lemma 4 as printed; the others are appended to list (count *count)
+// for the int64 kernel.
+int paam_launch_lazy_target(const paam_batch *bt, const AnalysisParams &p, int32_t *list, int32_t *count,
+                            int64_t max_items, cudaStream_t stream);
 
 // Exact int64 kernel (analyze_wide.cu) over list[0 .. *count) or, with
 // list == nullptr, over every system.

@@ -14,9 +14,6 @@
 
 namespace {
 
-// chains up to which the search keeps each chain's aggregates for all its
-// candidates (64 bytes per chain)
-constexpr int64_t kRecChains = (int64_t)1 << 22;
 
 __global__ void search_init(int32_t *first_ok, int64_t n_sys, int32_t K, uint8_t *cand_ok, int64_t n_cand)
 {
