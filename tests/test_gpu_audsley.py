@@ -46,6 +46,17 @@ def test_seed_uneven_sizes():
     assert counts.max() > 30 and counts.min() <= 3  # large and tiny systems in one batch
 
 
+def test_seed_deadlines_past_the_narrow_bound():
+    # periods up to 300 ms: a third of the systems keep every deadline below 2^27 ns
+    # (the lazy kernel's trials), the others reach past it (the int64 kernel's)
+    sy = g.generate("cfg1", n_sys=1500, t_min=1e7, t_max=3e8, seed=5)
+    dmax = np.maximum.reduceat(sy.D, sy.sys_chain_off[:-1])
+    assert 0.2 < (dmax < 2**27 - 16).mean() < 0.8
+    got = _seed(sy, 4, n_buckets=2, eps=391_000, kappa=129_180)
+    ref = oracle.audsley(sy, nmax=4, threads=8, n_buckets=2, eps=391_000, kappa=129_180)
+    np.testing.assert_array_equal(got, ref)
+
+
 @pytest.mark.parametrize("blocking_mode", [0, 1])
 def test_seed_several_accelerators_and_safe_blocking(blocking_mode):
     from paam_gen import tiny

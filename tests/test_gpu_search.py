@@ -38,6 +38,22 @@ def test_search_exhaustive_matches_oracle(cfg):
     assert np.array_equal(first, ref["first_ok"])
 
 
+@pytest.mark.parametrize("stop_at_first", [False, True])
+def test_search_deadlines_past_the_narrow_bound(stop_at_first):
+    # periods up to 300 ms: about a third of the systems stay below 2^27 ns (the lazy
+    # kernels, reading chain records), the others go to the int64 kernel
+    sy = g.generate("cfg1", n_sys=1500, t_min=1e7, t_max=3e8, seed=5)
+    ranks = g.candidate_ranks(sy, 24, 7)
+    p = dict(n_buckets=2, eps=391_000, kappa=129_180)
+    first, cand = _run(sy, ranks, stop_at_first=stop_at_first, **p)
+    ref = oracle.search(sy, ranks, threads=8, **p)
+    assert np.array_equal(first, ref["first_ok"])
+    if stop_at_first:
+        assert np.all(cand <= ref["cand_ok"])  # skipped candidates read 0
+    else:
+        assert np.array_equal(cand, ref["cand_ok"])
+
+
 def test_search_early_exit_same_first_candidate():
     sy = g.generate("cfg4s", n_sys=2000)
     ranks = g.candidate_ranks(sy, 128, 5)
