@@ -86,7 +86,7 @@ def bf16(x):
 
 def loss_and_grad_bf16(params, X, L):
     """The same masked MSE and gradient with the network's storage in
-    bfloat16, as the benchmark spec specifies it (BF16 weights, FP32
+    bfloat16, as the network is specified (BF16 weights, FP32
     accumulation): weights, each layer's pre-activation kept for the backward
     pass and its activation, the output gradient and each back-propagated
     gradient are rounded to bfloat16 where they are stored; every sum is
