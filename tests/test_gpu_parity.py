@@ -95,6 +95,17 @@ def test_cfg2_full_size():
     assert 0.05 < (out["status"] == 0).mean() < 0.95
 
 
+def test_safe_blocking_full_size():
+    """The 1,000,000-system workload under the safe reading of Lemma 4, with two
+    buckets and both overheads: every segment bounded one per lane (no system
+    has more than 128 segments), every chain compared bit-exactly."""
+    sy = g.generate("cfg2")
+    p = dict(n_buckets=2, eps=391_000, kappa=129_180)
+    out = gpu_analyze(sy, blocking_mode=1, **p)
+    assert_same(out, oracle.analyze(sy, blocking_mode=1, threads=os.cpu_count() or 8, **p))
+    assert 0.005 < (out["status"] == 0).mean() < 0.5
+
+
 def test_cfg3_full_size():
     """The 4,000,000-system uneven workload (2-64 chains), overheads on, every chain."""
     sy = g.generate("cfg3")
