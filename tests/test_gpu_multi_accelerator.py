@@ -24,6 +24,17 @@ def test_wfd_units_match_oracle(p):
         assert_same(gpu_analyze(sy, **p), oracle.analyze(sy, threads=8, **p))
 
 
+def test_three_accelerators_full_size():
+    """The 1,000,000-system workload with its segments spread over three
+    accelerator units by WFD (the benchmark's several-accelerator case), every
+    chain compared bit-exactly."""
+    import os
+
+    sy = g.assign_accelerators(g.generate("cfg2"), 3)
+    p = PARAMS[1]
+    assert_same(gpu_analyze(sy, **p), oracle.analyze(sy, threads=os.cpu_count() or 8, **p))
+
+
 def test_tiny_systems_four_accelerators():
     rng = random.Random(42)
     dicts = [tiny.tiny_system(rng, n_max=6, cb_max=3, x_max=3, n_acc=4, seg_max=2, p_seg=0.6,
