@@ -477,9 +477,10 @@ __device__ void lazy_acc_system(const BatchDev &b, const AnalysisParams &p, int6
     __syncwarp(gm);
 }
 
-// three resident blocks of 256 per SM for up to three accelerators, two for four
+// four resident blocks of 256 per SM (64 registers, no spills) for up to three
+// accelerators, two for four
 template <int NACC>
-__global__ void __launch_bounds__(256, NACC <= 3 ? 3 : 2) analyze_lazy_acc_kernel(BatchDev b, AnalysisParams p,
+__global__ void __launch_bounds__(256, NACC <= 3 ? 4 : 2) analyze_lazy_acc_kernel(BatchDev b, AnalysisParams p,
                                                                                 int64_t *R, uint8_t *st,
                                                                                 uint8_t *verdict, int32_t *wide_list,
                                                                                 int32_t *wide_count)
