@@ -651,7 +651,5 @@ template int launch_lazy<5>(const paam_batch *, const AnalysisParams &, int64_t 
                             const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
 template int launch_lazy<6>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
                             const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
-template int launch_lazy32<4>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
-                              const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
 template int launch_lazy32<6>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
                               const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
