@@ -188,8 +188,8 @@ TRAFFIC_PER_SYSTEM = {26: _T26, 24: _T26, 28: _T28, 23: _T28}
 # the same for the other workloads, keyed by (workload, launch configuration): the
 # uneven workload's step is the first pass, the 32-lane pass over the deferral list
 # and the 64-chain lazy kernel for the systems above 32 chains
-TRAFFIC_OTHER = {("cfg3", 26): (869_097_984 + 40_553_216 + 346_428_672 + 16_412_416 + 109_226_496 + 1_887_744) / 500_000,
-                 ("cfg3", 28): (850_265_600 + 32_014_592 + 346_421_248 + 16_240_128 + 109_251_840 + 1_920_000) / 500_000}
+TRAFFIC_OTHER = {("cfg3", 26): (867_346_688 + 40_391_936 + 346_479_616 + 16_131_584 + 109_261_824 + 1_899_520) / 500_000,
+                 ("cfg3", 28): (849_617_152 + 30_518_528 + 346_491_904 + 16_272_896 + 109_204_480 + 1_914_624) / 500_000}
 
 
 def traffic_per_system(workload: str, cfg_index: int):
