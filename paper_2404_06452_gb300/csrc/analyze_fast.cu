@@ -603,8 +603,8 @@ int paam_enqueue_analysis(const paam_batch *b, const AnalysisParams &p, const La
         pw.queue = b->queue + 2;
         pm.queue_batch = pb.queue_batch = pw.queue_batch = cfg.queue;
     }
-    if (p.blocking_mode == 1) { // the safe blocking term in register tables, the int64 kernel for the rest
-        int rc = paam_launch_reg_safe(b, pm, R, status, verdict, items, stream);
+    if (p.blocking_mode == 1) { // the safe blocking term in the lazy kernel, the int64 kernel for the rest
+        int rc = paam_launch_lazy_safe(b, pm, R, status, verdict, items, stream);
         if (rc == PAAM_OK) rc = paam_launch_wide(b, pw, R, status, verdict, b->list_wide, b->counts + 1, items, stream);
         if (n_kernels) *n_kernels = 2;
         return rc;

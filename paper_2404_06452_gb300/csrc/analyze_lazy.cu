@@ -22,9 +22,10 @@
 // Systems with more than 16 chains, or that fit the 32-bit bound but not the
 // narrow one, go to b.list_big (the 32-lane pass of this kernel over that list,
 // then analyze_lazy64.cu for those above 32 chains); systems outside the 32-bit
-// bound to b.list_wide (the int64 kernel).  One accelerator, Lemma 4 as printed
-// (blocking_mode 0): analysis, candidate and target mode; the other modes keep
-// their kernels.
+// bound to b.list_wide (the int64 kernel).  One accelerator: Lemma 4 as printed
+// (blocking_mode 0) in analysis, candidate and target mode, and the safe reading
+// (blocking_mode 1, 16 lanes; its larger systems go to the int64 kernel); several
+// accelerators keep their kernel (analyze_lazy_acc.cu).
 #include "reg_common.cuh"
 
 namespace {
@@ -55,6 +56,27 @@ struct LazySmem {
     int64_t c0, sys, seg_base; // kept here across the chain steps, not in registers
     int32_t cand;
 };
+
+// The safe reading of Lemma 4 (blocking_mode 1) also bounds every segment of the
+// system, one per lane, from these tables (systems of up to kSafeSegs segments).
+constexpr int kSafeSegs = 128;
+template <int LG>
+struct LazySafeExt {
+    uint4 dv[LG];             // by chain: {2 (T - 1), magic, l, S*} (the interferer's term)
+    uint4 ch[LG];             // by chain: {hps, D, blk, 0}
+    uint32_t hq[kSafeSegs];   // by segment (relative to the system's first): its bound; kInfR none, kCapR cut short
+    uint8_t segc[kSafeSegs];  // by segment: its chain
+};
+template <int LG>
+struct LazySafeSmem : LazySmem<LG> {
+    LazySafeExt<LG> x;
+};
+
+// a term of a segment's recurrence, capped: any term above every deadline (all
+// below 2^27 here) decides the comparison with D as the exact one does
+constexpr uint64_t kSafeTermCap = 1ull << 40;
+// a hold without a bound, and any hold at or above it: every deadline is below it
+constexpr uint32_t kHoldInf = (uint32_t)kFitR;
 
 // ceil(t / T) + 1 (Lemma 1) times c, capped at 2^27 - 1 so that 16 lanes' sum fits 32 bits
 __device__ __forceinline__ uint32_t capped_term(uint32_t t, uint32_t tm2, uint32_t mg, uint32_t lg, uint32_t c)
@@ -118,8 +140,15 @@ __device__ __forceinline__ void chain_aggregates(const BatchDev &b, int64_t g, u
 // the Audsley-style seed; see AnalysisParams.target): candidate (system, c) is
 // decided by chain p.target[system * Kc + c] alone (-1: no trial in the slot), the
 // chains are analysed up to that one's step and no failure ends a candidate early.
-template <int LG, bool REC = false, bool TGT = false>
-__device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t item, LazySmem<LG> &s, int lane,
+// SAFE (16 lanes, aggregates computed here): the safe reading of Lemma 4
+// (blocking_mode 1): every segment's Lemma 2 bound is computed (one segment per
+// lane), each chain's longest callback hold E_i + sum over its segments of (bound
+// + eps), B_c as the longest hold of a lower-priority chain on c's executor, and
+// Eq. 3's exact sum in every recurrence; systems of more than kSafeSegs segments
+// go to the int64 kernel's list.
+template <int LG, bool REC = false, bool TGT = false, bool SAFE = false>
+__device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t item, LazySmem<LG> &s,
+                            LazySafeExt<LG> *sx, int lane,
                             unsigned gm, int64_t *__restrict__ R_out, uint8_t *__restrict__ st_out,
                             uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
                             int32_t *wide_list, int32_t *wide_count)
@@ -230,6 +259,14 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         }
         return;
     }
+    uint32_t nseg = 0; // the system's segments (safe reading)
+    if constexpr (SAFE) {
+        nseg = __reduce_add_sync(gm, val ? dlv : 0u);
+        if (nseg > (uint32_t)kSafeSegs) {
+            if (lane == 0) wide_list[atomicAdd(wide_count, 1)] = (int32_t)item;
+            return;
+        }
+    }
     // The system's iteration bound: a recurrence of Eq. 3 or Eq. 6 rises strictly until
     // it converges or passes its deadline, and after its first step only when some
     // arrival count ceil(t / T_h) + 1 (Lemma 1) has grown, at most ceil(Dmax / T_h) times
@@ -318,8 +355,9 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
     sums = __shfl_up_sync(gm, sums, 1, LG);
     if (j == 0) sums = 0u;
     sums = __shfl_sync(gm, sums, prank < LG ? prank : 0, LG);
-    for (Mask lo = samex & ~higher & ~jbit & all; lo; lo &= lo - 1) // Lemma 4: one LP callback on the executor
-        Bv = umax(Bv, s.emax[__ffs(lo) - 1]);
+    if constexpr (!SAFE)
+        for (Mask lo = samex & ~higher & ~jbit & all; lo; lo &= lo - 1) // Lemma 4: one LP callback on the executor
+            Bv = umax(Bv, s.emax[__ffs(lo) - 1]);
     if (one_bucket) { // every user shares the bucket: the longest lower-priority request (R2-R3)
         // the largest M* over the users of rank > r: a suffix maximum in priority order
         uint32_t v = j < n ? s.msort[j] : 0u;
@@ -345,6 +383,84 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             }
     }
 
+    uint32_t hsum = 0; // safe reading: Eq. 3's exact sum over the chain's segments (kInfR none, kCapR cut short)
+    if constexpr (SAFE) {
+        // every segment's fixed point h = A* + blk + sum over hps(c) of (ceil(h / T_t)
+        // + 1) S*_t (Lemma 2), one segment per lane, each lane summing the terms of
+        // its chain's higher-priority users itself
+        if (val) {
+            sx->dv[j] = make_uint4(tm2, mg, lg, Sv);
+            sx->ch[j] = make_uint4(hps, Dv, blk, 0u);
+            for (uint32_t i = 0; i < dlv; ++i) sx->segc[seg0 + i] = (uint8_t)j;
+        }
+        __syncwarp(gm);
+        for (uint32_t k = j; k < nseg; k += LG) {
+            const int c = sx->segc[k];
+            const uint4 ch = sx->ch[c];
+            const uint64_t base = (uint64_t)b.A[seg_base + k] + kappa2 + ch.z;
+            uint64_t h = base; // the recurrence starts with the first two terms
+            uint32_t out, evs = 0;
+            for (;;) {
+                if (h > ch.y) {
+                    out = kInfR;
+                    break;
+                }
+                if (counted && evs++ == kIterCap) {
+                    out = kCapR;
+                    break;
+                }
+                uint64_t sum = 0;
+                for (Mask m = ch.x; m; m &= m - 1) {
+                    const uint4 dv = sx->dv[__ffs(m) - 1];
+                    const uint64_t term = (uint64_t)rarrivals((uint32_t)h, dv.x, dv.y, dv.z) * dv.w;
+                    sum += term < kSafeTermCap ? term : kSafeTermCap;
+                }
+                const uint64_t nh = base + sum;
+                if (nh == h) { // strictly increasing until here, bounded by D
+                    out = (uint32_t)h;
+                    break;
+                }
+                h = nh;
+            }
+            sx->hq[k] = out;
+        }
+        __syncwarp(gm);
+        // this lane's chain: its callbacks' holds E_i + sum over the callback's segments
+        // of (bound + eps), and Eq. 3's sum over all its segments; a chain without
+        // segments holds its executor for its longest callback
+        uint32_t hold = Emx;
+        if (val && dlv) {
+            const int64_t g = c0 + j;
+            const int64_t cb1 = b.chain_cb_off[g + 1];
+            uint64_t Hsum = 0, hl = 0;
+            bool seg_inf = false, hold_inf = false, capped = false;
+            for (int64_t cb = b.chain_cb_off[g]; cb < cb1; ++cb) {
+                uint64_t t = (uint64_t)b.E[cb];
+                bool t_inf = false;
+                const uint32_t k1 = (uint32_t)(b.cb_seg_off[cb + 1] - seg_base);
+                for (uint32_t k = (uint32_t)(b.cb_seg_off[cb] - seg_base); k < k1; ++k) {
+                    const uint32_t h = sx->hq[k];
+                    if (h >= kCapR) { // no bound
+                        seg_inf = t_inf = true;
+                        capped |= h == kCapR;
+                    } else {
+                        Hsum += h;
+                        t += h + eps;
+                    }
+                }
+                if (t_inf) hold_inf = true;
+                else if (t > hl) hl = t;
+            }
+            const uint64_t cap = (uint64_t)Dv + 1;
+            hsum = capped ? kCapR : seg_inf ? kInfR : (uint32_t)(Hsum < cap ? Hsum : cap);
+            hold = hold_inf || hl >= kHoldInf ? kHoldInf : (uint32_t)hl;
+        }
+        s.emax[j] = hold;
+        __syncwarp(gm);
+        for (Mask lo = samex & ~higher & ~jbit & all; lo; lo &= lo - 1) // safe Lemma 4: the longest LP hold
+            Bv = umax(Bv, s.emax[__ffs(lo) - 1]);
+    }
+
     // ---- own recurrence terms ------------------------------------------------
     if (val) {
         const uint64_t own = (uint64_t)Sv + (uint64_t)dlv * blk;
@@ -358,7 +474,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         // point is at least x + f sum_h S*_h with x = A* + blk, f = 2 if x >= 1, as mu >= 2
         // for t >= 1), kept capped at 2^27 like the interference sums it is compared with
         const uint64_t lb = (((uint64_t)Amn + blk) >= 1 ? 2 : 1) * (uint64_t)dlv * sums;
-        s.seg[pos] = make_uint4((uint32_t)j, lb < kNarrow ? (uint32_t)lb : kNarrow, blk, dlv);
+        s.seg[pos] = make_uint4((uint32_t)j, SAFE ? hsum : (lb < kNarrow ? (uint32_t)lb : kNarrow), blk, dlv);
     }
     __syncwarp(gm);
 
@@ -383,6 +499,11 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
         const uint32_t ccoef = ((rl.x >> j) & 1) ? Ehp : (((rl.y >> j) & 1) ? Ehpp : 0u);
         const uint32_t acoef = ((rl.z >> j) & 1) ? Sv : 0u;
         const uint32_t dl = sg.w;
+        if (SAFE && dl && sg.y == kCapR) { // a segment recurrence was cut short: no bound (PAAM_ST_ITERCAP)
+            if (j == c) Rv = kCapR;
+            if (rank_row && !TGT) break;
+            continue;
+        }
         // start: B + E + H* with the interference part of Eq. 4 empty; Lemma 2's sum is
         // never below own = S* + delta blk (each segment's fixed point is at least its
         // A* + blk), so H* starts at own + delta eps either way
@@ -393,8 +514,9 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
             // Lemma 2's sum is at least own + lb: while Eq. 4's interference part is at
             // most lb, the minimum of Eq. 3 and Eq. 4 is Eq. 4; the exact per-segment fixed
             // points are taken at the first evaluation where it is larger, if any
-            uint32_t lb = dl ? sg.y : kInfR; // kInfR once they are taken
-            uint32_t Hs = kInfR;             // Lemma 2's per-segment sum: unbounded, or not needed yet
+            // (safe reading: the exact sum is known from the start, and lb is not used)
+            uint32_t lb = (dl && !SAFE) ? sg.y : kInfR; // kInfR once they are taken
+            uint32_t Hs = (SAFE && dl) ? sg.y : kInfR;  // Lemma 2's per-segment sum: unbounded, or not needed yet
             // every deadline is below 2^27 - 16: in the loop base <= R <= D, each group
             // sum is capped at 2^27 where it is added (a capped term already exceeds D)
             for (;;) { // twice at most: before and after the fixed points are taken
@@ -509,7 +631,7 @@ __device__ void lazy_system(const BatchDev &b, const AnalysisParams &p, int64_t 
 
 // BLOCKS resident blocks of 256 threads per SM: the register budget per thread.
 // Items are all of the launch (list == nullptr) or list[0 .. *count).
-template <int LG, int BLOCKS, bool REC, bool TGT = false>
+template <int LG, int BLOCKS, bool REC, bool TGT = false, bool SAFE = false>
 __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, AnalysisParams p, int64_t *R,
                                                                    uint8_t *st, uint8_t *verdict, const int32_t *list,
                                                                    const int32_t *count, int32_t *big_list,
@@ -520,7 +642,10 @@ __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, A
     const int groups = blockDim.x / LG;
     const int grp = threadIdx.x / LG;
     const int lane = threadIdx.x % LG;
-    LazySmem<LG> &s = reinterpret_cast<LazySmem<LG> *>(smem_raw)[grp];
+    using SM = typename std::conditional<SAFE, LazySafeSmem<LG>, LazySmem<LG>>::type;
+    SM &s = reinterpret_cast<SM *>(smem_raw)[grp];
+    LazySafeExt<LG> *sx = nullptr;
+    if constexpr (SAFE) sx = &s.x;
     const unsigned gm = rgroup_mask<LG>();
     const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for_each_item<LG>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
@@ -531,8 +656,8 @@ __global__ void __launch_bounds__(256, BLOCKS) analyze_lazy_kernel(BatchDev b, A
         if (!list && p.K == 0 && lane == 0 && i % kPrefetchSlice == 0)
             prefetch_systems(b, p.sys_order, i + kBinWindow, kPrefetchSlice);
         const int64_t item = list ? (int64_t)list[i] : i;
-        lazy_system<LG, REC, TGT>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list,
-                                  wide_count);
+        lazy_system<LG, REC, TGT, SAFE>(b, p, item, s, sx, lane, gm, R, st, verdict, big_list, big_count, wide_list,
+                                        wide_count);
     });
 }
 
@@ -603,6 +728,29 @@ int launch_lazy_pass(const paam_batch *bt, const AnalysisParams &p, int64_t *R, 
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, list, count, bt->list_big,
                                                       bt->counts, bt->list_wide, bt->counts + 1);
+    PAAM_CUDA_TRY(cudaGetLastError());
+    return PAAM_OK;
+}
+
+int paam_launch_lazy_safe(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                          int64_t max_items, cudaStream_t stream)
+{
+    constexpr int LG = 16, threads = 256;
+    const int groups = threads / LG;
+    const size_t smem = sizeof(LazySafeSmem<LG>) * groups;
+    auto kern = analyze_lazy_kernel<LG, 5, false, false, true>;
+    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (max_items + groups - 1) / groups;
+    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    // every deferred system (over 16 chains or kSafeSegs segments, not narrow,
+    // outside the 32-bit bound) to the int64 kernel's list
+    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, nullptr, nullptr,
+                                                      bt->list_wide, bt->counts + 1, bt->list_wide, bt->counts + 1);
     PAAM_CUDA_TRY(cudaGetLastError());
     return PAAM_OK;
 }

@@ -32,42 +32,14 @@ struct OwnSmem {
     uint8_t order[NMAX];
 };
 
-// the safe blocking reading also keeps each chain's longest callback hold and,
-// for systems of up to kSafeSegs segments, each segment's Lemma 2 bound
-constexpr int kSafeSegs = 128;
-template <int NMAX>
-struct SafeExt {
-    uint32_t hold[NMAX];
-    uint32_t hq[kSafeSegs];  // by segment (relative to the system's first): its bound; kInfR none, kCapR cut short
-    uint8_t segc[kSafeSegs]; // by segment: its chain
-};
-template <int NMAX>
-struct SafeSmem : OwnSmem<NMAX> {
-    SafeExt<NMAX> x;
-};
 
-// a term of a segment's recurrence, capped: any term above every deadline (all
-// below 2^30) decides the comparison with D as the exact one does
-constexpr uint64_t kSafeTermCap = 1ull << 40;
-
-// a hold without a bound (a segment above its chain's deadline), and any hold
-// at or above it: every deadline is below it, so B + E > D either way
-constexpr uint32_t kHoldInf = (uint32_t)kFitR;
-
-// SAFE (a separate instantiation, one chain per lane): the safe reading of
-// Lemma 4 (blocking_mode 1): every segment's Lemma 2 bound is computed, each
-// chain's longest callback hold E_i + sum over its segments of (bound + eps)
-// is kept in sx->hold, and B_c is the longest hold of a lower-priority chain on
-// c's executor.
-template <int G, int CPL, bool SAFE = false>
-__device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t item, OwnSmem<G * CPL> &s,
-                           SafeExt<G * CPL> *sx, int lane, unsigned gm, int64_t *__restrict__ R_out,
+template <int G, int CPL>
+__device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t item, OwnSmem<G * CPL> &s, int lane, unsigned gm, int64_t *__restrict__ R_out,
                            uint8_t *__restrict__ st_out,
                            uint8_t *__restrict__ verdict, int32_t *big_list, int32_t *big_count,
                            int32_t *wide_list, int32_t *wide_count)
 {
     constexpr int NMAX = G * CPL;
-    static_assert(!SAFE || CPL == 1, "the safe reading runs one chain per lane");
     using Mask = typename RegMask<NMAX>::type;
     int64_t sys;
     int32_t cand;
@@ -294,7 +266,6 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
         // Eq. 4 is at most own + sum_h mu_h(D) S_h for every R <= D.  Exact sum only if it can win.
         const uint64_t f = ((uint64_t)Amn[k] + blk[k]) >= 1 ? 2 : 1;
         if (dl && f * dl * sums[k] < hchd[k]) need_exact |= (Mask)1 << j;
-        if constexpr (SAFE) sx->hold[j] = Emx[k]; // a chain without segments holds for its longest callback
     }
     need_exact = ror<G>(need_exact, gm);
     __syncwarp(gm);
@@ -310,140 +281,6 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     // the fixed points: counted loops only where the bound above exceeds kIterCap
     auto fixed_points = [&](auto counted_tag) {
     constexpr bool CNT = decltype(counted_tag)::value;
-    if constexpr (SAFE) {
-        // ---- every segment's Lemma 2 bound, the chains' sums (Eq. 3) and their
-        // longest holds; then B_c from the holds (safe Lemma 4)
-        const uint32_t nseg = __reduce_add_sync(gm, val[0] ? dlv[0] : 0u); // the system's segments
-        if (nseg <= (uint32_t)kSafeSegs) {
-            // one segment per lane: the fixed point h = A* + blk + sum over hps(c) of
-            // (ceil(h / T_t) + 1) S*_t of Lemma 2 for a segment of chain c, each lane
-            // summing the terms of c's higher-priority users itself
-            if (val[0])
-                for (uint32_t i = 0; i < dlv[0]; ++i) sx->segc[seg0[0] + i] = (uint8_t)lane;
-            __syncwarp(gm);
-            for (uint32_t k = lane; k < nseg; k += G) {
-                const int c = sx->segc[k];
-                const Mask hps = s.hps[c];
-                const uint32_t Dc = s.rec[c].x;
-                const uint64_t base = (uint64_t)b.A[seg_base + k] + kappa2 + s.seg[c].z;
-                uint64_t h = base; // the recurrence starts with the first two terms
-                uint32_t out, ev = 0;
-                for (;;) {
-                    if (h > Dc) {
-                        out = kInfR;
-                        break;
-                    }
-                    if (CNT && ev++ == kIterCap) {
-                        out = kCapR;
-                        break;
-                    }
-                    uint64_t sum = 0;
-                    for (Mask m = hps; m; m &= m - 1) {
-                        const int t = rlowest(m);
-                        const uint4 dv = s.dv[t];
-                        const uint64_t term = (uint64_t)rarrivals((uint32_t)h, dv.y, dv.z, dv.w) * s.sm[t].x;
-                        sum += term < kSafeTermCap ? term : kSafeTermCap;
-                    }
-                    const uint64_t nh = base + sum;
-                    if (nh == h) { // strictly increasing until here, bounded by D
-                        out = (uint32_t)h;
-                        break;
-                    }
-                    h = nh;
-                }
-                sx->hq[k] = out;
-            }
-            __syncwarp(gm);
-            // each user chain: its callbacks' holds E_i + sum over the callback's
-            // segments of (bound + eps), and Eq. 3's sum over all its segments
-            if (val[0] && dlv[0]) {
-                const int64_t g = c0 + lane;
-                const int64_t cb1 = b.chain_cb_off[g + 1];
-                uint64_t Hsum = 0, hold = 0;
-                bool seg_inf = false, hold_inf = false, capped = false;
-                for (int64_t cb = b.chain_cb_off[g]; cb < cb1; ++cb) {
-                    uint64_t t = (uint64_t)b.E[cb];
-                    bool t_inf = false;
-                    const uint32_t k1 = (uint32_t)(b.cb_seg_off[cb + 1] - seg_base);
-                    for (uint32_t k = (uint32_t)(b.cb_seg_off[cb] - seg_base); k < k1; ++k) {
-                        const uint32_t h = sx->hq[k];
-                        if (h >= kCapR) { // no bound
-                            seg_inf = t_inf = true;
-                            capped |= h == kCapR;
-                        } else {
-                            Hsum += h;
-                            t += h + eps;
-                        }
-                    }
-                    if (t_inf) hold_inf = true;
-                    else if (t > hold) hold = t;
-                }
-                const uint64_t cap = (uint64_t)Dv[0] + 1;
-                s.seg[lane].x = capped ? kCapR : seg_inf ? kInfR : (uint32_t)(Hsum < cap ? Hsum : cap);
-                sx->hold[lane] = hold_inf || hold >= kHoldInf ? kHoldInf : (uint32_t)hold;
-            }
-            __syncwarp(gm);
-        } else // larger systems: segment by segment, the lanes over the interfering chains
-        for (Mask nm = users; nm; nm &= nm - 1) {
-            const int c = rlowest(nm);
-            const Mask hps = s.hps[c];
-            const uint32_t Dc = s.rec[c].x, blkc = s.seg[c].z;
-            const uint32_t acoef = ((hps >> lane) & 1) ? Sv[0] : 0u;
-            const int64_t g = c0 + c;
-            const int64_t cb1 = b.chain_cb_off[g + 1];
-            uint64_t Hsum = 0, hold = 0;
-            bool seg_inf = false, hold_inf = false, capped = false;
-            for (int64_t cb = b.chain_cb_off[g]; cb < cb1; ++cb) {
-                uint64_t t = (uint64_t)b.E[cb];
-                bool t_inf = false;
-                const int64_t q1 = b.cb_seg_off[cb + 1];
-                for (int64_t q = b.cb_seg_off[cb]; q < q1; ++q) {
-                    const uint64_t base = (uint64_t)b.A[q] + kappa2 + blkc;
-                    uint64_t h = base; // the recurrence starts with the first two terms
-                    bool inf = false;
-                    uint32_t ev = 0;
-                    for (;;) {
-                        if (h > Dc) {
-                            inf = true;
-                            break;
-                        }
-                        if (CNT && ev++ == kIterCap) {
-                            inf = capped = true;
-                            break;
-                        }
-                        const uint64_t part = (uint64_t)rarrivals((uint32_t)h, tm2[0], mg[0], lg[0]) * acoef;
-                        const uint64_t nh = base + gsum<G>(part, narrow, gm);
-                        if (nh == h) break;
-                        h = nh;
-                    }
-                    if (inf) {
-                        seg_inf = t_inf = true;
-                    } else {
-                        Hsum += h;
-                        t += h + eps;
-                    }
-                }
-                if (t_inf) hold_inf = true;
-                else if (t > hold) hold = t;
-            }
-            if (lane == 0) {
-                const uint64_t cap = (uint64_t)Dc + 1;
-                s.seg[c].x = capped ? kCapR : seg_inf ? kInfR : (uint32_t)(Hsum < cap ? Hsum : cap);
-                sx->hold[c] = hold_inf || hold >= kHoldInf ? kHoldInf : (uint32_t)hold;
-            }
-            __syncwarp(gm);
-        }
-        if (val[0]) {
-            uint32_t Bs = 0;
-            for (int t = 0; t < n; ++t) {
-                const uint32_t ht = sx->hold[t];
-                if (((samex[0] >> t) & 1) && s.key[t].x < pr[0] && ht > Bs) Bs = ht;
-            }
-            s.rec[lane].y = Bs + Ev[0]; // below 2^31: both terms are below 2^30 + 1
-        }
-        need_exact = 0; // every sum is exact already
-        __syncwarp(gm);
-    }
 
     // ---- exact per-segment fixed points (Lemma 2), chains one at a time ------
     for (Mask nm = need_exact; nm; nm &= nm - 1) {
@@ -653,7 +490,7 @@ __device__ void reg_system(const BatchDev &b, const AnalysisParams &p, int64_t i
     __syncwarp(gm);
 }
 
-template <int G, int CPL, bool SAFE = false>
+template <int G, int CPL>
 __device__ __forceinline__ void reg_items(const BatchDev &b, const AnalysisParams &p, int64_t *R, uint8_t *st,
                                           uint8_t *verdict, const int32_t *list, const int32_t *count,
                                           int32_t *big_list, int32_t *big_count, int32_t *wide_list,
@@ -663,16 +500,12 @@ __device__ __forceinline__ void reg_items(const BatchDev &b, const AnalysisParam
     const int groups = blockDim.x / G;
     const int grp = threadIdx.x / G;
     const int lane = threadIdx.x % G;
-    using SM = typename std::conditional<SAFE, SafeSmem<G * CPL>, OwnSmem<G * CPL>>::type;
-    SM &s = reinterpret_cast<SM *>(smem_raw)[grp];
-    SafeExt<G * CPL> *sx = nullptr;
-    if constexpr (SAFE) sx = &s.x;
+    OwnSmem<G * CPL> &s = reinterpret_cast<OwnSmem<G * CPL> *>(smem_raw)[grp];
     const unsigned gm = rgroup_mask<G>();
     const int64_t n_items = list ? (int64_t)*count : (p.K > 0 ? b.n_sys * p.K : b.n_sys);
     for_each_item<G>(p, n_items, grp, groups, lane, gm, [&](int64_t i) {
         const int64_t item = list ? (int64_t)list[i] : i;
-        reg_system<G, CPL, SAFE>(b, p, item, s, sx, lane, gm, R, st, verdict, big_list, big_count,
-                                         wide_list, wide_count);
+        reg_system<G, CPL>(b, p, item, s, lane, gm, R, st, verdict, big_list, big_count, wide_list, wide_count);
     });
 }
 
@@ -696,17 +529,6 @@ __global__ void __launch_bounds__(256, 4) analyze_reg1_kernel(BatchDev b, Analys
                                                               int32_t *wide_count)
 {
     reg_items<G, 1>(b, p, R, st, verdict, list, count, big_list, big_count, wide_list, wide_count);
-}
-
-// The safe blocking reading: systems of up to G chains inside the 32-bit
-// bound; larger ones and the rest go to the wide list
-template <int G>
-__global__ void __launch_bounds__(256, 4) analyze_reg1_safe_kernel(BatchDev b, AnalysisParams p, int64_t *R,
-                                                                   uint8_t *st, uint8_t *verdict, int32_t *wide_list,
-                                                                   int32_t *wide_count)
-{
-    reg_items<G, 1, true>(b, p, R, st, verdict, nullptr, nullptr, wide_list, wide_count, wide_list,
-                                 wide_count);
 }
 
 } // namespace
@@ -751,26 +573,6 @@ template int launch_reg<32, 1>(const paam_batch *, const AnalysisParams &, int64
                                const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
 template int launch_reg<32, 2>(const paam_batch *, const AnalysisParams &, int64_t *, uint8_t *, uint8_t *,
                                const int32_t *, const int32_t *, int64_t, int, cudaStream_t);
-
-int paam_launch_reg_safe(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
-                         int64_t max_items, cudaStream_t stream)
-{
-    constexpr int G = 16, threads = 256;
-    const int groups = threads / G;
-    const size_t smem = sizeof(SafeSmem<G>) * groups;
-    auto kern = analyze_reg1_safe_kernel<G>;
-    PAAM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    PAAM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-    if (per_sm < 1) per_sm = 1;
-    int64_t blocks = (max_items + groups - 1) / groups;
-    const int64_t cap = (int64_t)per_sm * bt->ctx->n_sm;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, threads, smem, stream>>>(batch_dev(bt), p, R, st, verdict, bt->list_wide, bt->counts + 1);
-    PAAM_CUDA_TRY(cudaGetLastError());
-    return PAAM_OK;
-}
 
 namespace {
 __global__ void diag_divisor_kernel(const uint32_t *T, uint32_t *m, uint32_t *l, int64_t n)

@@ -341,15 +341,16 @@ int paam_launch_validate_range(const paam_batch *b, const int32_t *acc, const Va
 int paam_launch_lazy_acc(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
                          int64_t max_items, cudaStream_t stream);
 
-// The safe blocking reading (blocking_mode 1) in the register-table kernel
-// (analyze_reg.cu): systems of up to 16 chains inside the 32-bit bound; the
-// others go to b->list_wide (count b->counts[1]) for the int64 kernel.
-int paam_launch_reg_safe(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
-                         int64_t max_items, cudaStream_t stream);
 
 // Chains up to which a search (or the Audsley-style seed) keeps each chain's
 // aggregates for all its candidates (paam_launch_chain_records, 64 bytes per chain).
 constexpr int64_t kRecChains = (int64_t)1 << 22;
+
+// The safe reading of Lemma 4 (blocking_mode 1) in the lazy kernel (analyze_lazy.cu):
+// systems of up to 16 chains and 128 segments inside the narrow 32-bit bound, one
+// accelerator; the others are appended to b->list_wide (count b->counts[1]).
+int paam_launch_lazy_safe(const paam_batch *bt, const AnalysisParams &p, int64_t *R, uint8_t *st, uint8_t *verdict,
+                          int64_t max_items, cudaStream_t stream);
 
 // Target mode of the lazy kernel (analyze_lazy.cu), reading p.chain_recs when set:
 // candidates of systems with up to 16 chains inside the narrow 32-bit bound, one
