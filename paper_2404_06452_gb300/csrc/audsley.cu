@@ -11,9 +11,9 @@
 // once c is done: the lazy kernel for systems of up to 16 chains inside its
 // narrow 32-bit bound (one accelerator, Lemma 4 as printed; each chain's
 // aggregates computed once per call for all its trials), the exact int64
-// kernel for the rest.  The first passing c
-// in index order takes level l; if none passes, the unassigned chain with the
-// largest D (ties: highest index) does.  The admission test is not
+// kernel for the rest.  The first passing c in index order takes level l; if
+// none passes, the unassigned chain with the largest D (ties: highest index)
+// does.  The admission test is not
 // OPA-compatible (bucket ranks, blocking and the DEP rule depend on the whole
 // order), so the result is a seed for the exact search, not an optimum.
 #include "internal.cuh"
